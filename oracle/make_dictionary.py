@@ -1,0 +1,46 @@
+"""Writes the frozen default dictionary with the oracle's Algorithm 1 (Sec. IV-C).
+
+Training set: the 100,000-line seed-1 synthetic stream, pre-processed by the oracle (Sec. IV-A), with the
+SMILES-alphabet pre-population (Sec. IV-B), L_min = 2 (Sec. IV-C), L_max = 8 (the middle of the paper's
+{5, 8, 15} sweep, Sec. V-C) and T = 146 (every free symbol byte). Only ``oracle`` and the seeded input
+generator are used.
+
+    python -m oracle.make_dictionary [--lmax 8] [--out paper_2404_19391_gb300/data/zs_default.zsd]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import os
+import sys
+
+_ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if _ROOT not in sys.path:
+    sys.path.insert(0, _ROOT)
+
+import oracle  # noqa: E402
+from oracle import dictgen  # noqa: E402
+import synth  # noqa: E402
+
+
+def build_default(lmax: int = 8, lmin: int = 2, T: int = 146, lines: int = synth.TRAIN_LINES,
+                  alphabet: bytes = dictgen.SMILES_ALPHABET, preprocess: bool = True) -> bytes:
+    raw = synth.generate(synth.TRAIN, 0, lines)
+    pre = oracle.preprocess_stream(raw) if preprocess else raw
+    return dictgen.generate(pre, T=T, lmin=lmin, lmax=lmax, alphabet=alphabet)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--lmax", type=int, default=8)
+    ap.add_argument("--T", type=int, default=146)
+    ap.add_argument("--out", default=os.path.join(_ROOT, "paper_2404_19391_gb300", "data", "zs_default.zsd"))
+    args = ap.parse_args()
+    text = build_default(lmax=args.lmax, T=args.T)
+    with open(args.out, "wb") as f:
+        f.write(text)
+    print(args.out, len(text), hashlib.sha256(text).hexdigest())
+
+
+if __name__ == "__main__":
+    main()
