@@ -1,0 +1,169 @@
+/*
+ * zsmiles.h - C ABI of the GB300 ZSMILES codec (libzsmiles.so).
+ *
+ * ZSMILES (arXiv 2404.19391) stores SMILES libraries one molecule per line. Each line is optionally
+ * pre-processed (ring-ID renumbering, Sec. IV-A), then encoded against one fixed, input-independent
+ * dictionary D (Sec. I, IV-B, IV-C) by the parse of minimum output length (a shortest path where a
+ * dictionary match costs 1 byte and an escaped character 2, Sec. IV-D1). Decoding replaces each symbol
+ * by its pattern and copies the byte after a space verbatim (Sec. IV-D2). The output stays readable and
+ * keeps every molecule on its own line, so any line can be cut out and decoded alone (Sec. I).
+ *
+ * Conventions for every call below:
+ *   - Pointers named d_* are DEVICE pointers on the device that was current when the dictionary was
+ *     loaded (for calls without a dictionary: the current device). The caller owns every buffer; the
+ *     library owns only the zs_dict handle and the scratch it caches per (dictionary, stream) pair.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
+ *     stream-ordered. Calls that fill a zs_result wait for their own work on `stream` before returning,
+ *     so *res is valid on return.
+ *   - Streams: a stream is a sequence of lines separated by '\n'. A trailing '\n' does not open an
+ *     extra, empty line; whether the last line ends with '\n' is preserved by every call. A line
+ *     index has n_lines + 1 uint64 entries: the byte offset where each line starts, then the total
+ *     length.
+ *   - Errors never abort, trap or print. The return value says what went wrong, zs_last_error()
+ *     gives a message. On ZS_ERR_CAPACITY the output buffers may have been partly written and
+ *     res->out_len holds the size that would have been needed.
+ *   - The library never falls back to a CPU path: without a usable CUDA device every call returns
+ *     ZS_ERR_CUDA.
+ */
+#ifndef ZSMILES_H
+#define ZSMILES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct zs_dict zs_dict; /* opaque, library-owned */
+
+typedef enum {
+    ZS_OK = 0,
+    ZS_ERR_INVALID_ARG = 1, /* NULL where a pointer is required, wrong device, size out of range */
+    ZS_ERR_BAD_DICT = 2,    /* dictionary file does not parse (format below) */
+    ZS_ERR_CAPACITY = 3,    /* an output buffer is too small; res->out_len / *n_lines say how large */
+    ZS_ERR_MALFORMED = 4,   /* compressed input is not a valid ZSMILES stream; see res->err_offset */
+    ZS_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    ZS_ERR_TIMEOUT = 6,     /* a device-side wait ran past its limit; the call's output is invalid */
+    ZS_ERR_OOM = 7          /* the library could not allocate its scratch */
+} zs_status;
+
+/* zs_compress flags */
+enum { ZS_PREPROCESS = 1u }; /* renumber ring IDs before encoding (Sec. IV-A); "optionally", Sec. IV-D */
+
+typedef struct {
+    uint64_t out_len;    /* bytes written to the output (or needed, on ZS_ERR_CAPACITY) */
+    uint64_t n_lines;    /* lines (compress/decompress) or requests (decompress_lines) processed */
+    uint64_t err_offset; /* ZS_ERR_MALFORMED: offset of the first bad byte, or index of the bad request */
+} zs_result;
+
+/*
+ * zs_load_dictionary - parse a dictionary file and build its device tables.
+ *
+ * D maps a symbol byte to a pattern (Sec. IV: "a dictionary that associates a common string pattern to
+ * an ASCII character"); it is fixed and input-independent (Sec. I), pre-populated with single
+ * characters (Sec. IV-B) and filled with learned patterns by Algorithm 1 (Sec. IV-C). The paper compiles
+ * D into its executable (Sec. IV-D); here it is loaded at run time from this text format:
+ *
+ *     ZSDICT 1
+ *     <lmin> <lmax> <T>
+ *     alphabet <hex of the pre-populated characters, or ->
+ *     T lines of: <symbol as 2 hex digits> <pattern as hex>
+ *
+ * Each alphabet character c is the entry c -> "c". Symbols and patterns must be unique, may not hold
+ * '\n' or ' ' (the line separator and the escape), and patterns are 1..lmax bytes, lmax <= 16.
+ *
+ * file_bytes: host memory, len bytes, read during the call only. *out: receives a handle owned by the
+ * caller until zs_free_dictionary. The device tables live on the current device. Returns ZS_OK,
+ * ZS_ERR_INVALID_ARG, ZS_ERR_BAD_DICT, ZS_ERR_CUDA or ZS_ERR_OOM.
+ */
+zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, zs_dict **out);
+
+/* Releases the handle, its device tables and every scratch buffer cached for it. The caller must not
+ * have work in flight that uses the handle. NULL is ignored. */
+void zs_free_dictionary(zs_dict *d);
+
+/* Longest pattern of D (the most bytes one symbol can expand to). */
+int zs_dictionary_lmax(const zs_dict *d);
+
+/* Output capacity that always suffices for zs_compress of in_len bytes: 3 * in_len + 16. Escaping
+ * doubles a byte (Sec. IV-B) and renumbering can turn a 1-byte ring label into a 3-byte %nn label. */
+size_t zs_compress_bound(size_t in_len);
+
+/* Output capacity that always suffices for zs_decompress of in_len bytes under d: lmax * in_len. */
+size_t zs_decompress_bound(const zs_dict *d, size_t in_len);
+
+/*
+ * zs_compress - encode every line of a stream (Sec. IV-D1).
+ *
+ * Per line: if flags has ZS_PREPROCESS, renumber ring IDs (Sec. IV-A: IDs restart at 0, are reused once
+ * a ring closes, and among overlapping rings the one that closes first - the innermost - gets the lower
+ * ID; only the first space/tab-free field is touched; a line with an unclosed ring or bracket, a bad %
+ * label, or one needing an ID above 99 is left as is). Then write the minimum-length sequence of
+ * dictionary symbols (cost 1) and escapes (' ' + raw byte, cost 2) that spells the line (Sec. IV-D1);
+ * among equally short encodings the one taking the longest piece at each step, front to back. Each
+ * output line ends with '\n' exactly when its input line did.
+ *
+ * d_in:  device, in_len bytes (any alignment; 16-byte alignment is faster).
+ * d_out: device, out_cap bytes; zs_compress_bound(in_len) always suffices.
+ * d_line_index: device, nullable; if given, receives n_lines + 1 offsets into d_out (index_cap entries
+ *        available; ZS_ERR_CAPACITY if fewer are needed than given).
+ * res:   host; out_len = compressed bytes, n_lines = lines.
+ * Returns ZS_OK, ZS_ERR_INVALID_ARG, ZS_ERR_CAPACITY, ZS_ERR_CUDA, ZS_ERR_TIMEOUT or ZS_ERR_OOM.
+ */
+zs_status zs_compress(const zs_dict *d, const uint8_t *d_in, size_t in_len, unsigned flags, uint8_t *d_out,
+                      size_t out_cap, uint64_t *d_line_index, size_t index_cap, zs_result *res, void *stream);
+
+/*
+ * zs_decompress - decode every line of a compressed stream (Sec. IV-D2).
+ *
+ * Each byte b of a line: ' ' -> output the next byte verbatim (escape); any other b -> output D[b].
+ * '\n' separates lines and is copied. An undefined symbol, or a line ending in an unpaired ' ', is
+ * ZS_ERR_MALFORMED with res->err_offset = offset of the first bad byte in d_in.
+ *
+ * d_in: device, in_len bytes. d_out: device, out_cap bytes (zs_decompress_bound suffices).
+ * res: host; out_len = decoded bytes, n_lines = lines.
+ * Returns ZS_OK, ZS_ERR_INVALID_ARG, ZS_ERR_CAPACITY, ZS_ERR_MALFORMED, ZS_ERR_CUDA, ZS_ERR_TIMEOUT, ZS_ERR_OOM.
+ */
+zs_status zs_decompress(const zs_dict *d, const uint8_t *d_in, size_t in_len, uint8_t *d_out, size_t out_cap,
+                        zs_result *res, void *stream);
+
+/*
+ * zs_build_line_index - line-start offsets of any '\n'-separated stream (Sec. I: every molecule keeps
+ * its own line, which is what makes random access possible).
+ *
+ * d_in: device, in_len bytes. d_index: device, index_cap uint64 entries; receives n_lines + 1 offsets.
+ * *n_lines: host, receives the line count (also on ZS_ERR_CAPACITY, so the caller can size d_index).
+ * Returns ZS_OK, ZS_ERR_INVALID_ARG, ZS_ERR_CAPACITY, ZS_ERR_CUDA, ZS_ERR_TIMEOUT or ZS_ERR_OOM.
+ */
+zs_status zs_build_line_index(const uint8_t *d_in, size_t in_len, uint64_t *d_index, size_t index_cap,
+                              size_t *n_lines, void *stream);
+
+/*
+ * zs_decompress_lines - random access: decode the requested lines of a compressed stream (Sec. I:
+ * "random access" = lines keep their order and stay separable, so one line can be decoded alone with
+ * the shared dictionary).
+ *
+ * d_comp, comp_len: device, the compressed stream. d_index: device, its n_lines + 1 line offsets (from
+ * zs_compress or zs_build_line_index). d_ids: device, k line numbers, any order, repeats allowed.
+ * d_out: device, out_cap bytes; receives the decoded lines in request order, each followed by '\n'.
+ * d_out_off: device, k + 1 entries; the offset of each decoded line in d_out, then the total.
+ * res: host; out_len = total bytes, n_lines = k. An id >= n_lines, or a malformed line, is
+ * ZS_ERR_MALFORMED with res->err_offset = the position of the first bad request in d_ids.
+ * Returns ZS_OK, ZS_ERR_INVALID_ARG, ZS_ERR_CAPACITY, ZS_ERR_MALFORMED, ZS_ERR_CUDA, ZS_ERR_TIMEOUT, ZS_ERR_OOM.
+ */
+zs_status zs_decompress_lines(const zs_dict *d, const uint8_t *d_comp, size_t comp_len, const uint64_t *d_index,
+                              size_t n_lines, const uint64_t *d_ids, size_t k, uint8_t *d_out, size_t out_cap,
+                              uint64_t *d_out_off, zs_result *res, void *stream);
+
+/* Message for the last failing call on this thread ("" if none). Valid until the next call. */
+const char *zs_last_error(void);
+
+/* Library version string. */
+const char *zs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZSMILES_H */

@@ -1,0 +1,677 @@
+// zs_decompress (Sec. IV-D2), zs_build_line_index and zs_decompress_lines (random access, Sec. I).
+//
+// Escapes without a sequential scan: a byte is a verbatim (escaped) byte exactly when the run of ' '
+// bytes just before it has odd length - each ' ' that is not itself escaped escapes the byte after it,
+// and a run always starts unescaped (the byte before a run is never an unescaped ' '). So every thread
+// can decode its own slice after counting the spaces in front of it.
+#include <algorithm>
+
+#include "zs_common.cuh"
+
+namespace zs {
+namespace {
+
+// ------------------------------------------------------------------------------------------------
+// Full-stream decompression: tiles of kDT compressed bytes, kPerT per thread, single pass with decoupled
+// look-back; the tile's output is assembled in a shared buffer aligned to the output's 16-byte grid and
+// written with coalesced 16-byte stores (direct stores when a tile expands past the buffer).
+// ------------------------------------------------------------------------------------------------
+constexpr int kDNT = 256;
+constexpr int kDT = 8192;
+constexpr int kPerT = kDT / kDNT;  // 32
+constexpr int kDOutCap = 40960;
+
+struct DecArgs {
+    const uint8_t *in;
+    uint64_t n;
+    uint8_t *out;
+    uint64_t out_cap;
+    uint32_t in_aligned;
+    uint64_t ntiles;
+    const uint8_t *dec;  // plen[256], pat[256][16]
+    DevResult *res;
+    TileState *tiles;
+    uint64_t limit_ns;
+    int64_t stall_tile;
+};
+
+constexpr int kDOffStage = 0;
+constexpr int kDOffOut = kDOffStage + kDT + 16;
+constexpr int kDOffDec = kDOffOut + kDOutCap + 32;
+constexpr int kDOffScan = kDOffDec + kDecBytes;
+constexpr int kDOffVars = kDOffScan + 16 * (kDNT / 32 + 1) + 16;
+constexpr int kDOffBar = kDOffVars + 64;
+constexpr int kDSmem = kDOffBar + 16;
+
+struct DVars {
+    uint64_t tile;
+    uint64_t E_a, E_b;
+    uint32_t carry;  // spaces immediately before the tile
+    uint32_t staged;
+    uint32_t so;
+    uint32_t pad;
+};
+
+__global__ void __launch_bounds__(kDNT) decompress_kernel(DecArgs A)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t *st = smem + kDOffStage;
+    uint8_t *ost = smem + kDOffOut;
+    uint8_t *dec = smem + kDOffDec;
+    uint64_t *scan = reinterpret_cast<uint64_t *>(smem + kDOffScan);
+    DVars *V = reinterpret_cast<DVars *>(smem + kDOffVars);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kDOffBar);
+    const int tid = threadIdx.x;
+    uint32_t *status = &A.res->status;
+    const uint8_t *plen = dec;
+    const uint8_t *pat = dec + 256;
+
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    if (tid == 0) {
+        mbar_arrive_tx(bar, kDecBytes);
+        bulk_g2s(dec, A.dec, kDecBytes, bar);
+    }
+    if (!mbar_wait_bounded(bar, phase, A.limit_ns, status)) {
+        mbar_wait_bounded(bar, phase, A.limit_ns, status);
+        return;
+    }
+    phase ^= 1u;
+
+    for (;;) {
+        if (tid == 0) V->tile = atomicAdd(&A.res->tile_counter, 1ull);
+        __syncthreads();
+        const uint64_t t = V->tile;
+        if (t >= A.ntiles) break;
+        const uint64_t base = t * (uint64_t)kDT;
+        const uint32_t nown = (uint32_t)(min(A.n, base + kDT) - base);
+        const uint32_t nbulk = A.in_aligned ? (nown & ~15u) : 0u;
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_tx(bar, nbulk);
+            if (nbulk) bulk_g2s(st, A.in + base, nbulk, bar);
+            uint32_t c = 0;
+            while (base > c && A.in[base - 1 - c] == kEsc) ++c;  // space run ending just before the tile
+            V->carry = c;
+        }
+        for (uint32_t j = nbulk + tid; j < nown; j += kDNT) st[j] = A.in[base + j];
+        if (!mbar_wait_bounded(bar, phase, A.limit_ns, status)) {
+            mbar_wait_bounded(bar, phase, A.limit_ns, status);
+            return;
+        }
+        phase ^= 1u;
+        __syncthreads();
+
+        // ---- sizes of this thread's slice ----
+        const uint32_t p0 = min(nown, (uint32_t)tid * kPerT);
+        const uint32_t p1 = min(nown, p0 + kPerT);
+        uint32_t run = 0;
+        {
+            int q = (int)p0 - 1;
+            while (q >= 0 && st[q] == kEsc) {
+                ++run;
+                --q;
+            }
+            if (q < 0) run += V->carry;
+        }
+        const bool lit0 = (run & 1u) != 0;
+        bool lit = lit0;
+        uint32_t outb = 0, nls = 0;
+        for (uint32_t p = p0; p < p1; ++p) {
+            const uint8_t b = st[p];
+            if (lit) {
+                if (b == kNl) {  // a line ending in an unpaired escape
+                    note_error_offset(A.res, base + p - 1);
+                    atomicOr(status, kStMalformed);
+                }
+                outb += 1;
+                nls += (b == kNl);
+                lit = false;
+            } else if (b == kEsc) {
+                lit = true;
+            } else if (b == kNl) {
+                outb += 1;
+                nls += 1;
+            } else {
+                const uint32_t l = plen[b];
+                if (l == 0) {
+                    note_error_offset(A.res, base + p);
+                    atomicOr(status, kStMalformed);
+                }
+                outb += l;
+            }
+        }
+        if (lit && p1 > p0 && base + p1 == A.n) {
+            note_error_offset(A.res, A.n - 1);
+            atomicOr(status, kStMalformed);
+        }
+
+        uint64_t xa, xb, ta, tb;
+        block_excl2_u64<kDNT>(outb, nls, scan, &xa, &xb, &ta, &tb);
+        if (tid == 0) {
+            const bool stall = (int64_t)t == A.stall_tile;
+            if (!stall) publish(&A.tiles[t], t == 0 ? 2u : 1u, ta, tb);
+            uint64_t ea = 0, eb = 0;
+            if (t > 0) lookback(A.tiles, t, &ea, &eb, A.limit_ns, status);
+            if (t > 0 && !stall) publish(&A.tiles[t], 2u, ea + ta, eb + tb);
+            V->E_a = ea;
+            V->E_b = eb;
+            V->so = (uint32_t)(((uint64_t)(uintptr_t)A.out + ea) & 15u);
+            V->staged = (ta + 32 <= (uint64_t)kDOutCap) ? 1u : 0u;
+            if (t == A.ntiles - 1) {
+                A.res->out_len = ea + ta;
+                A.res->n_lines = eb + tb + ((A.in[A.n - 1] != kNl) ? 1u : 0u);
+            }
+        }
+        __syncthreads();
+
+        // ---- emit ----
+        const uint64_t E_a = V->E_a;
+        const bool staged = V->staged != 0;
+        const uint32_t so = V->so;
+        uint64_t pos = xa;
+        lit = lit0;
+        for (uint32_t p = p0; p < p1; ++p) {
+            const uint8_t b = st[p];
+            if (!lit && b == kEsc) {
+                lit = true;
+                continue;
+            }
+            if (lit || b == kNl) {
+                lit = false;
+                if (staged) ost[so + pos] = b;
+                else if (E_a + pos < A.out_cap) A.out[E_a + pos] = b;
+                pos += 1;
+                continue;
+            }
+            const uint32_t l = plen[b];
+            const uint8_t *src = pat + 16u * b;
+            if (staged) {
+                uint8_t *d = ost + so + pos;
+                for (uint32_t k = 0; k < l; ++k) d[k] = src[k];
+            } else {
+                for (uint32_t k = 0; k < l; ++k)
+                    if (E_a + pos + k < A.out_cap) A.out[E_a + pos + k] = src[k];
+            }
+            pos += l;
+        }
+        __syncthreads();
+        if (staged) {
+            uint8_t *gdst = A.out + E_a - so;
+            const uint32_t nchunks = (uint32_t)((so + ta + 15) >> 4);
+            for (uint32_t c = tid; c < nchunks; c += kDNT) {
+                const uint32_t lo = c * 16u, hi = lo + 16u;
+                if (lo >= so && hi <= so + ta && E_a - so + hi <= A.out_cap) {
+                    *reinterpret_cast<uint4 *>(gdst + lo) = *reinterpret_cast<const uint4 *>(ost + lo);
+                } else {
+                    for (uint32_t k = lo; k < hi; ++k)
+                        if (k >= so && k < so + ta && E_a - so + k < A.out_cap) gdst[k] = ost[k];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Line index: newline ranks via warp-segmented 16-byte loads, block scan, decoupled look-back.
+// ------------------------------------------------------------------------------------------------
+constexpr int kINT = 256;
+constexpr int kIT = 16384;  // bytes per tile: each warp 2 KiB = 4 x 512
+
+struct IdxArgs {
+    const uint8_t *in;
+    uint64_t n;
+    uint64_t *index;
+    uint64_t index_cap;
+    uint32_t in_aligned;
+    uint64_t ntiles;
+    DevResult *res;
+    TileState *tiles;
+    uint64_t limit_ns;
+    int64_t stall_tile;
+};
+
+__device__ __forceinline__ uint32_t zero_bits4(uint32_t t)
+{
+    uint32_t z = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t | 0x7F7F7F7Fu);
+    return ((z >> 7) & 1u) | ((z >> 14) & 2u) | ((z >> 21) & 4u) | ((z >> 28) & 8u);
+}
+
+__device__ __forceinline__ uint32_t nl_bits(const uint8_t *in, uint64_t n, uint64_t p, bool aligned)
+{
+    if (p >= n) return 0;
+    if (aligned && p + 16 <= n) {
+        uint4 v = __ldg(reinterpret_cast<const uint4 *>(in + p));
+        const uint32_t k = 0x0A0A0A0Au;
+        return zero_bits4(v.x ^ k) | (zero_bits4(v.y ^ k) << 4) | (zero_bits4(v.z ^ k) << 8) |
+               (zero_bits4(v.w ^ k) << 12);
+    }
+    uint32_t bits = 0;
+    for (uint32_t q = 0; q < 16 && p + q < n; ++q)
+        if (in[p + q] == kNl) bits |= 1u << q;
+    return bits;
+}
+
+__global__ void __launch_bounds__(kINT) line_index_kernel(IdxArgs A)
+{
+    __shared__ uint64_t scan[2 * (kINT / 32 + 1)];
+    __shared__ uint64_t s_tile, s_E;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *status = &A.res->status;
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&A.res->tile_counter, 1ull);
+        __syncthreads();
+        const uint64_t t = s_tile;
+        if (t >= A.ntiles) break;
+        const uint64_t wbase = t * (uint64_t)kIT + (uint64_t)warp * 2048u;
+        uint32_t bits[4];
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            bits[it] = nl_bits(A.in, A.n, wbase + (uint64_t)it * 512u + (uint64_t)lane * 16u, A.in_aligned != 0);
+            cnt += __popc(bits[it]);
+        }
+        uint64_t xa, xb, ta, tb;
+        block_excl2_u64<kINT>(cnt, 0, scan, &xa, &xb, &ta, &tb);
+        if (tid == 0) {
+            const bool stall = (int64_t)t == A.stall_tile;
+            if (!stall) publish(&A.tiles[t], t == 0 ? 2u : 1u, ta, 0);
+            uint64_t ea = 0, eb = 0;
+            if (t > 0) lookback(A.tiles, t, &ea, &eb, A.limit_ns, status);
+            if (t > 0 && !stall) publish(&A.tiles[t], 2u, ea + ta, 0);
+            s_E = ea;
+            if (t == 0 && A.index_cap > 0) A.index[0] = 0;
+            if (t == A.ntiles - 1) {
+                const uint64_t nl = ea + ta;
+                const bool open_last = A.in[A.n - 1] != kNl;
+                const uint64_t lines = nl + (open_last ? 1u : 0u);
+                A.res->n_lines = lines;
+                if (open_last && lines < A.index_cap) A.index[lines] = A.n;
+            }
+        }
+        __syncthreads();
+        // each newline at p ends line k and starts line k+1 at p+1 (the last one marks the end)
+        uint64_t rank = s_E + xa;
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            uint32_t b = bits[it];
+            const uint32_t c = __popc(b);
+            const uint32_t inc = warp_incl_u32(c);
+            uint64_t rk = rank + inc - c;
+            const uint64_t p0 = wbase + (uint64_t)it * 512u + (uint64_t)lane * 16u;
+            while (b) {
+                const int q = __ffs(b) - 1;
+                b &= b - 1;
+                if (rk + 1 < A.index_cap) A.index[rk + 1] = p0 + (uint64_t)q + 1u;
+                ++rk;
+            }
+            rank += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Random access: one request per thread; decoded sizes, block scan + look-back over request tiles for
+// the output offsets, then each thread decodes its line.
+// ------------------------------------------------------------------------------------------------
+constexpr int kRNT = 256;
+
+struct LinesArgs {
+    const uint8_t *comp;
+    uint64_t comp_len;
+    const uint64_t *index;
+    uint64_t n_lines;
+    const uint64_t *ids;
+    uint64_t k;
+    uint8_t *out;
+    uint64_t out_cap;
+    uint64_t *out_off;
+    uint64_t ntiles;
+    const uint8_t *dec;
+    DevResult *res;
+    TileState *tiles;
+    uint64_t limit_ns;
+    int64_t stall_tile;
+};
+
+__global__ void __launch_bounds__(kRNT) lines_kernel(LinesArgs A)
+{
+    __shared__ __align__(16) uint8_t dec[kDecBytes];
+    __shared__ uint64_t scan[2 * (kRNT / 32 + 1)];
+    __shared__ uint64_t s_tile, s_E;
+    const int tid = threadIdx.x;
+    uint32_t *status = &A.res->status;
+    for (uint32_t j = tid; j < kDecBytes / 16; j += kRNT)
+        reinterpret_cast<uint4 *>(dec)[j] = __ldg(reinterpret_cast<const uint4 *>(A.dec) + j);
+    __syncthreads();
+    const uint8_t *plen = dec;
+    const uint8_t *pat = dec + 256;
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&A.res->tile_counter, 1ull);
+        __syncthreads();
+        const uint64_t t = s_tile;
+        if (t >= A.ntiles) break;
+        const uint64_t r = t * (uint64_t)kRNT + (uint64_t)tid;
+        uint64_t a = 0, b = 0, olen = 0;
+        bool ok = false;
+        if (r < A.k) {
+            const uint64_t id = A.ids[r];
+            ok = id < A.n_lines;
+            if (ok) {
+                a = A.index[id];
+                b = A.index[id + 1];
+                ok = a <= b && b <= A.comp_len;
+            }
+            if (ok && b > a && A.comp[b - 1] == kNl) --b;
+            bool lit = false;
+            for (uint64_t p = a; ok && p < b; ++p) {
+                const uint8_t c = A.comp[p];
+                if (lit) {
+                    olen += 1;
+                    lit = false;
+                } else if (c == kEsc) {
+                    lit = true;
+                } else {
+                    const uint32_t l = plen[c];
+                    if (l == 0) ok = false;  // unknown symbol or a '\n' inside the line
+                    olen += l;
+                }
+            }
+            if (lit) ok = false;
+            if (!ok) {
+                note_error_offset(A.res, r);
+                atomicOr(status, kStMalformed);
+                olen = 0;
+            } else {
+                olen += 1;  // '\n'
+            }
+        }
+        uint64_t xa, xb, ta, tb;
+        block_excl2_u64<kRNT>(olen, 0, scan, &xa, &xb, &ta, &tb);
+        if (tid == 0) {
+            const bool stall = (int64_t)t == A.stall_tile;
+            if (!stall) publish(&A.tiles[t], t == 0 ? 2u : 1u, ta, 0);
+            uint64_t ea = 0, eb = 0;
+            if (t > 0) lookback(A.tiles, t, &ea, &eb, A.limit_ns, status);
+            if (t > 0 && !stall) publish(&A.tiles[t], 2u, ea + ta, 0);
+            s_E = ea;
+            if (t == A.ntiles - 1) {
+                A.res->out_len = ea + ta;
+                A.out_off[A.k] = ea + ta;
+            }
+        }
+        __syncthreads();
+        if (r < A.k) {
+            uint64_t pos = s_E + xa;
+            A.out_off[r] = pos;
+            if (ok) {
+                bool lit = false;
+                for (uint64_t p = a; p < b; ++p) {
+                    const uint8_t c = A.comp[p];
+                    if (!lit && c == kEsc) {
+                        lit = true;
+                        continue;
+                    }
+                    if (lit) {
+                        if (pos < A.out_cap) A.out[pos] = c;
+                        ++pos;
+                        lit = false;
+                        continue;
+                    }
+                    const uint32_t l = plen[c];
+                    const uint8_t *src = pat + 16u * c;
+                    for (uint32_t q = 0; q < l; ++q, ++pos)
+                        if (pos < A.out_cap) A.out[pos] = src[q];
+                }
+                if (pos < A.out_cap) A.out[pos] = kNl;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+template <class K>
+int blocks_per_sm(K kernel, int nt, int smem)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, nt, smem);
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace
+
+uint64_t decompress_tiles(uint64_t n) { return (n + kDT - 1) / kDT; }
+uint64_t index_tiles(uint64_t n) { return (n + kIT - 1) / kIT; }
+uint64_t lines_tiles(uint64_t k) { return (k + kRNT - 1) / kRNT; }
+
+cudaError_t launch_decompress(const zs_dict *d, const uint8_t *in, uint64_t n, uint8_t *out, uint64_t out_cap,
+                              DevResult *res, TileState *tiles, cudaStream_t s)
+{
+    DecArgs a{};
+    a.in = in;
+    a.n = n;
+    a.out = out;
+    a.out_cap = out_cap;
+    a.in_aligned = (((uintptr_t)in) & 15u) == 0;
+    a.ntiles = decompress_tiles(n);
+    a.dec = d->d_dec;
+    a.res = res;
+    a.tiles = tiles;
+    a.limit_ns = wait_limit_ns();
+    a.stall_tile = injected_stall_tile();
+    static int per = -1;
+    if (per < 0) {
+        cudaFuncSetAttribute(decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDSmem);
+        per = blocks_per_sm(decompress_kernel, kDNT, kDSmem);
+    }
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.ntiles, (uint64_t)per * sm_count()));
+    decompress_kernel<<<(unsigned)grid, kDNT, kDSmem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_index(const uint8_t *in, uint64_t n, uint64_t *index, uint64_t index_cap, DevResult *res,
+                              TileState *tiles, cudaStream_t s)
+{
+    IdxArgs a{};
+    a.in = in;
+    a.n = n;
+    a.index = index;
+    a.index_cap = index_cap;
+    a.in_aligned = (((uintptr_t)in) & 15u) == 0;
+    a.ntiles = index_tiles(n);
+    a.res = res;
+    a.tiles = tiles;
+    a.limit_ns = wait_limit_ns();
+    a.stall_tile = injected_stall_tile();
+    static int per = -1;
+    if (per < 0) per = blocks_per_sm(line_index_kernel, kINT, 0);
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.ntiles, (uint64_t)per * sm_count()));
+    line_index_kernel<<<(unsigned)grid, kINT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lines(const zs_dict *d, const uint8_t *comp, uint64_t comp_len, const uint64_t *index,
+                         uint64_t n_lines, const uint64_t *ids, uint64_t k, uint8_t *out, uint64_t out_cap,
+                         uint64_t *out_off, DevResult *res, TileState *tiles, cudaStream_t s)
+{
+    LinesArgs a{};
+    a.comp = comp;
+    a.comp_len = comp_len;
+    a.index = index;
+    a.n_lines = n_lines;
+    a.ids = ids;
+    a.k = k;
+    a.out = out;
+    a.out_cap = out_cap;
+    a.out_off = out_off;
+    a.ntiles = lines_tiles(k);
+    a.dec = d->d_dec;
+    a.res = res;
+    a.tiles = tiles;
+    a.limit_ns = wait_limit_ns();
+    a.stall_tile = injected_stall_tile();
+    static int per = -1;
+    if (per < 0) per = blocks_per_sm(lines_kernel, kRNT, 0);
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.ntiles, (uint64_t)per * sm_count()));
+    lines_kernel<<<(unsigned)grid, kRNT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace zs
+
+namespace {
+
+zs_status check_dict_device(const zs_dict *d, const char *what)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return zs::cuda_fail(e, what);
+    if (dev != d->device) {
+        zs::set_error(std::string(what) + ": dictionary was loaded on another device");
+        return ZS_ERR_INVALID_ARG;
+    }
+    return ZS_OK;
+}
+
+// Zero the call's scratch, run `launch`, read the result back. *r receives the device result.
+template <class F>
+zs_status run(zs::ScratchPool &pool, void *stream, uint64_t ntiles, const char *what, F launch, zs::DevResult *r)
+{
+    zs::Scratch *sc = nullptr;
+    zs_status st = pool.get(stream, ntiles, 0, &sc);
+    if (st != ZS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    zs::DevResult *dr = reinterpret_cast<zs::DevResult *>(sc->dev);
+    zs::TileState *tiles = reinterpret_cast<zs::TileState *>(dr + 1);
+    cudaError_t e = cudaMemsetAsync(sc->dev, 0, sizeof(zs::DevResult) + ntiles * sizeof(zs::TileState), s);
+    if (e == cudaSuccess) e = launch(dr, tiles, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc->host, dr, sizeof(zs::DevResult), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return zs::cuda_fail(e, what);
+    *r = *sc->host;
+    if (r->status & zs::kStTimeout) {
+        zs::set_error(std::string(what) + ": a device-side wait expired");
+        return ZS_ERR_TIMEOUT;
+    }
+    return ZS_OK;
+}
+
+}  // namespace
+
+extern "C" zs_status zs_decompress(const zs_dict *d, const uint8_t *d_in, size_t in_len, uint8_t *d_out,
+                                   size_t out_cap, zs_result *res, void *stream)
+{
+    zs::clear_error();
+    if (!d || !res || (!d_in && in_len) || (!d_out && out_cap)) {
+        zs::set_error("zs_decompress: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    zs_status st = check_dict_device(d, "zs_decompress");
+    if (st != ZS_OK) return st;
+    res->out_len = res->n_lines = res->err_offset = 0;
+    if (in_len == 0) return ZS_OK;
+    zs::DevResult r{};
+    st = run(const_cast<zs_dict *>(d)->pool, stream, zs::decompress_tiles(in_len), "zs_decompress",
+             [&](zs::DevResult *dr, zs::TileState *tiles, cudaStream_t s) {
+                 return zs::launch_decompress(d, d_in, in_len, d_out, out_cap, dr, tiles, s);
+             },
+             &r);
+    if (st != ZS_OK) return st;
+    res->out_len = r.out_len;
+    res->n_lines = r.n_lines;
+    if (r.status & zs::kStMalformed) {
+        res->err_offset = ~r.err_key;
+        zs::set_error("zs_decompress: malformed input at byte " + std::to_string(res->err_offset));
+        return ZS_ERR_MALFORMED;
+    }
+    if (r.out_len > out_cap) {
+        zs::set_error("zs_decompress: output buffer too small");
+        return ZS_ERR_CAPACITY;
+    }
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_build_line_index(const uint8_t *d_in, size_t in_len, uint64_t *d_index, size_t index_cap,
+                                         size_t *n_lines, void *stream)
+{
+    zs::clear_error();
+    if (!n_lines || (!d_in && in_len) || (!d_index && index_cap)) {
+        zs::set_error("zs_build_line_index: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    *n_lines = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (in_len == 0) {
+        if (index_cap < 1) {
+            zs::set_error("zs_build_line_index: index buffer too small");
+            return ZS_ERR_CAPACITY;
+        }
+        cudaError_t e = cudaMemsetAsync(d_index, 0, sizeof(uint64_t), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? ZS_OK : zs::cuda_fail(e, "zs_build_line_index");
+    }
+    zs::DevResult r{};
+    zs_status st = run(zs::global_pool(), stream, zs::index_tiles(in_len), "zs_build_line_index",
+                       [&](zs::DevResult *dr, zs::TileState *tiles, cudaStream_t s2) {
+                           return zs::launch_line_index(d_in, in_len, d_index, index_cap, dr, tiles, s2);
+                       },
+                       &r);
+    if (st != ZS_OK) return st;
+    *n_lines = r.n_lines;
+    if (r.n_lines + 1 > index_cap) {
+        zs::set_error("zs_build_line_index: index buffer too small");
+        return ZS_ERR_CAPACITY;
+    }
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_decompress_lines(const zs_dict *d, const uint8_t *d_comp, size_t comp_len,
+                                         const uint64_t *d_index, size_t n_lines, const uint64_t *d_ids, size_t k,
+                                         uint8_t *d_out, size_t out_cap, uint64_t *d_out_off, zs_result *res,
+                                         void *stream)
+{
+    zs::clear_error();
+    if (!d || !res || !d_out_off || (!d_comp && comp_len) || !d_index || (!d_ids && k) || (!d_out && out_cap)) {
+        zs::set_error("zs_decompress_lines: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    zs_status st = check_dict_device(d, "zs_decompress_lines");
+    if (st != ZS_OK) return st;
+    res->out_len = res->n_lines = res->err_offset = 0;
+    if (k == 0) {
+        cudaError_t e = cudaMemsetAsync(d_out_off, 0, sizeof(uint64_t), (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+        return e == cudaSuccess ? ZS_OK : zs::cuda_fail(e, "zs_decompress_lines");
+    }
+    zs::DevResult r{};
+    st = run(const_cast<zs_dict *>(d)->pool, stream, zs::lines_tiles(k), "zs_decompress_lines",
+             [&](zs::DevResult *dr, zs::TileState *tiles, cudaStream_t s) {
+                 return zs::launch_lines(d, d_comp, comp_len, d_index, n_lines, d_ids, k, d_out, out_cap, d_out_off,
+                                         dr, tiles, s);
+             },
+             &r);
+    if (st != ZS_OK) return st;
+    res->out_len = r.out_len;
+    res->n_lines = k;
+    if (r.status & zs::kStMalformed) {
+        res->err_offset = ~r.err_key;
+        zs::set_error("zs_decompress_lines: bad request at position " + std::to_string(res->err_offset));
+        return ZS_ERR_MALFORMED;
+    }
+    if (r.out_len > out_cap) {
+        zs::set_error("zs_decompress_lines: output buffer too small");
+        return ZS_ERR_CAPACITY;
+    }
+    return ZS_OK;
+}

@@ -1,0 +1,306 @@
+// zs_load_dictionary: parse the dictionary file and build the encoder automaton and decoder tables.
+#include <string.h>
+
+#include <algorithm>
+#include <deque>
+#include <string>
+#include <vector>
+
+#include "zs_common.cuh"
+
+namespace {
+
+struct Entry {
+    uint8_t sym;
+    std::string pat;
+};
+
+int hexv(int c)
+{
+    if (c >= '0' && c <= '9') return c - '0';
+    if (c >= 'a' && c <= 'f') return c - 'a' + 10;
+    if (c >= 'A' && c <= 'F') return c - 'A' + 10;
+    return -1;
+}
+
+bool unhex(const std::string &h, std::string *out)
+{
+    if (h.size() % 2) return false;
+    out->clear();
+    for (size_t i = 0; i < h.size(); i += 2) {
+        int a = hexv((unsigned char)h[i]), b = hexv((unsigned char)h[i + 1]);
+        if (a < 0 || b < 0) return false;
+        out->push_back((char)(a * 16 + b));
+    }
+    return true;
+}
+
+bool parse_uint(const std::string &s, size_t *pos, long *v)
+{
+    while (*pos < s.size() && s[*pos] == ' ') ++*pos;
+    if (*pos >= s.size() || s[*pos] < '0' || s[*pos] > '9') return false;
+    long x = 0;
+    while (*pos < s.size() && s[*pos] >= '0' && s[*pos] <= '9') {
+        x = x * 10 + (s[*pos] - '0');
+        if (x > 1000000) return false;
+        ++*pos;
+    }
+    *v = x;
+    return true;
+}
+
+// Parse the text format documented in zsmiles.h. Returns "" on success, else a message.
+std::string parse(const uint8_t *bytes, size_t len, int *lmax_out, std::vector<Entry> *entries)
+{
+    std::vector<std::string> lines;
+    size_t i = 0;
+    while (i < len) {
+        size_t j = i;
+        while (j < len && bytes[j] != '\n') ++j;
+        lines.emplace_back((const char *)bytes + i, j - i);
+        i = j + 1;
+    }
+    if (lines.size() < 3 || lines[0] != "ZSDICT 1") return "missing 'ZSDICT 1' header";
+    size_t p = 0;
+    long lmin, lmax, T;
+    if (!parse_uint(lines[1], &p, &lmin) || !parse_uint(lines[1], &p, &lmax) || !parse_uint(lines[1], &p, &T))
+        return "bad '<lmin> <lmax> <T>' line";
+    while (p < lines[1].size() && lines[1][p] == ' ') ++p;
+    if (p != lines[1].size()) return "trailing characters after '<lmin> <lmax> <T>'";
+    if (lmin < 1 || lmax < lmin || lmax > zs::kMaxPat) return "lmin/lmax out of range (1 <= lmin <= lmax <= 16)";
+    if (T > 254) return "too many patterns";
+    const std::string &al = lines[2];
+    if (al.compare(0, 9, "alphabet ") != 0 || al.size() < 10) return "bad 'alphabet' line";
+    std::string alpha;
+    if (al.substr(9) != "-" && !unhex(al.substr(9), &alpha)) return "alphabet is not hex";
+    bool sym_used[256] = {false};
+    std::vector<std::string> pats;
+    auto add = [&](uint8_t sym, const std::string &pat) -> std::string {
+        if (sym == zs::kNl || sym == zs::kEsc) return "symbol is '\\n' or ' '";
+        if (sym_used[sym]) return "duplicate symbol";
+        if (pat.empty() || (long)pat.size() > lmax) return "pattern length outside 1..lmax";
+        for (unsigned char c : pat)
+            if (c == zs::kNl || c == zs::kEsc) return "pattern holds '\\n' or ' '";
+        for (const auto &q : pats)
+            if (q == pat) return "duplicate pattern";
+        sym_used[sym] = true;
+        pats.push_back(pat);
+        entries->push_back({sym, pat});
+        return "";
+    };
+    for (unsigned char c : alpha) {
+        std::string err = add(c, std::string(1, (char)c));
+        if (!err.empty()) return "alphabet: " + err;
+    }
+    if ((long)lines.size() < 3 + T) return "fewer pattern lines than T";
+    for (long t = 0; t < T; ++t) {
+        const std::string &l = lines[3 + t];
+        size_t sp = l.find(' ');
+        std::string s, pat;
+        if (sp != 2 || !unhex(l.substr(0, 2), &s) || !unhex(l.substr(3), &pat)) return "bad pattern line";
+        std::string err = add((uint8_t)s[0], pat);
+        if (!err.empty()) return "pattern line " + std::to_string(t) + ": " + err;
+    }
+    for (size_t k = 3 + T; k < lines.size(); ++k)
+        if (!lines[k].empty()) return "extra lines after the T pattern lines";
+    *lmax_out = (int)lmax;
+    return "";
+}
+
+struct Node {
+    int child[256];
+    int fail = 0;
+    int term_len = 0;
+    int term_sym = -1;
+    Node() { std::fill(child, child + 256, -1); }
+};
+
+}  // namespace
+
+extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, zs_dict **out)
+{
+    zs::clear_error();
+    if (!out || (!file_bytes && len)) {
+        zs::set_error("zs_load_dictionary: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int lmax = 0;
+    std::vector<Entry> entries;
+    std::string err = parse(file_bytes, len, &lmax, &entries);
+    if (!err.empty()) {
+        zs::set_error("dictionary: " + err);
+        return ZS_ERR_BAD_DICT;
+    }
+
+    // character classes: bytes that occur in some pattern, ascending
+    uint8_t cls[256] = {0};
+    int n_classes = 1;
+    {
+        bool seen[256] = {false};
+        for (auto &e : entries)
+            for (unsigned char c : e.pat) seen[c] = true;
+        for (int b = 0; b < 256; ++b)
+            if (seen[b]) cls[b] = (uint8_t)n_classes++;
+    }
+
+    // trie of reversed patterns
+    std::vector<Node> nodes(1);
+    for (auto &e : entries) {
+        int u = 0;
+        for (int k = (int)e.pat.size() - 1; k >= 0; --k) {
+            int c = cls[(unsigned char)e.pat[k]];
+            if (nodes[u].child[c] < 0) {
+                nodes[u].child[c] = (int)nodes.size();
+                nodes.emplace_back();
+            }
+            u = nodes[u].child[c];
+        }
+        nodes[u].term_len = (int)e.pat.size();
+        nodes[u].term_sym = e.sym;
+    }
+    const int S = (int)nodes.size();
+    if (S > 65535) {
+        zs::set_error("dictionary: automaton has too many states");
+        return ZS_ERR_BAD_DICT;
+    }
+
+    // failure links and the complete transition function, breadth first
+    std::vector<int> order;
+    std::vector<std::vector<int>> delta(S, std::vector<int>(n_classes, 0));
+    {
+        std::deque<int> q;
+        for (int c = 0; c < n_classes; ++c) {
+            int v = nodes[0].child[c];
+            if (v >= 0) {
+                nodes[v].fail = 0;
+                delta[0][c] = v;
+                q.push_back(v);
+            } else {
+                delta[0][c] = 0;
+            }
+        }
+        while (!q.empty()) {
+            int u = q.front();
+            q.pop_front();
+            order.push_back(u);
+            for (int c = 0; c < n_classes; ++c) {
+                int v = nodes[u].child[c];
+                if (v >= 0) {
+                    nodes[v].fail = delta[nodes[u].fail][c];
+                    delta[u][c] = v;
+                    q.push_back(v);
+                } else {
+                    delta[u][c] = delta[nodes[u].fail][c];
+                }
+            }
+        }
+    }
+    // match sets and symbols along each failure chain
+    std::vector<uint32_t> mask(S, 0);
+    std::vector<std::vector<uint8_t>> sym(S, std::vector<uint8_t>(zs::kMaxPat, 0));
+    auto fill = [&](int u) {
+        int f = nodes[u].fail;
+        mask[u] = (u == 0) ? 0u : mask[f];
+        if (u != 0) sym[u] = sym[f];
+        if (nodes[u].term_len) {
+            mask[u] |= 1u << (nodes[u].term_len - 1);
+            sym[u][nodes[u].term_len - 1] = (uint8_t)nodes[u].term_sym;
+        }
+    };
+    fill(0);
+    for (int u : order) fill(u);
+
+    std::vector<uint32_t> distinct;
+    for (int u = 0; u < S; ++u)
+        if (std::find(distinct.begin(), distinct.end(), mask[u]) == distinct.end()) distinct.push_back(mask[u]);
+    const bool compact = S <= 2048 && distinct.size() <= 32;
+
+    zs::EncLayout L{};
+    L.n_states = (uint32_t)S;
+    L.n_classes = (uint32_t)n_classes;
+    L.compact = compact ? 1u : 0u;
+    L.lmax = (uint32_t)lmax;
+    L.off_trans = zs::kOffTrans;
+    uint32_t trans_bytes = (uint32_t)S * (uint32_t)n_classes * (compact ? 2u : 4u);
+    trans_bytes = (trans_bytes + 15u) & ~15u;
+    L.off_sym = L.off_trans + trans_bytes;
+    L.img_bytes = L.off_sym + (uint32_t)S * 16u;
+    const uint32_t kMaxImg = 150u * 1024u;
+    if (L.img_bytes > kMaxImg) {
+        zs::set_error("dictionary: encoder automaton (" + std::to_string(L.img_bytes) +
+                      " bytes) exceeds the 150 KiB shared-memory budget");
+        return ZS_ERR_BAD_DICT;
+    }
+
+    std::vector<uint8_t> img(L.img_bytes, 0);
+    memcpy(img.data() + zs::kOffCls, cls, 256);
+    uint8_t plen[256] = {0};
+    uint8_t pat[256][zs::kMaxPat];
+    memset(pat, 0, sizeof pat);
+    for (auto &e : entries) {
+        plen[e.sym] = (uint8_t)e.pat.size();
+        memcpy(pat[e.sym], e.pat.data(), e.pat.size());
+    }
+    memcpy(img.data() + zs::kOffPlen, plen, 256);
+    if (compact) {
+        uint32_t *m = (uint32_t *)(img.data() + zs::kOffMasks);
+        for (size_t k = 0; k < distinct.size(); ++k) m[k] = distinct[k];
+        uint16_t *t = (uint16_t *)(img.data() + L.off_trans);
+        for (int u = 0; u < S; ++u)
+            for (int c = 0; c < n_classes; ++c) {
+                int v = delta[u][c];
+                uint32_t id = (uint32_t)(std::find(distinct.begin(), distinct.end(), mask[v]) - distinct.begin());
+                t[u * n_classes + c] = (uint16_t)(v | (id << 11));
+            }
+    } else {
+        uint32_t *t = (uint32_t *)(img.data() + L.off_trans);
+        for (int u = 0; u < S; ++u)
+            for (int c = 0; c < n_classes; ++c) {
+                int v = delta[u][c];
+                t[u * n_classes + c] = (uint32_t)v | (mask[v] << 16);
+            }
+    }
+    for (int u = 0; u < S; ++u) memcpy(img.data() + L.off_sym + 16 * u, sym[u].data(), 16);
+
+    std::vector<uint8_t> dec(zs::kDecBytes, 0);
+    memcpy(dec.data(), plen, 256);
+    memcpy(dec.data() + 256, pat, sizeof pat);
+
+    zs_dict *d = new zs_dict();
+    cudaError_t e = cudaGetDevice(&d->device);
+    if (e != cudaSuccess) {
+        delete d;
+        return zs::cuda_fail(e, "cudaGetDevice");
+    }
+    d->lmax = lmax;
+    d->layout = L;
+    memcpy(d->plen, plen, 256);
+    memcpy(d->pat, pat, sizeof pat);
+    e = cudaMalloc((void **)&d->d_enc, L.img_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d->d_dec, zs::kDecBytes);
+    if (e == cudaSuccess) e = cudaMemcpy(d->d_enc, img.data(), L.img_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d->d_dec, dec.data(), zs::kDecBytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (d->d_enc) cudaFree(d->d_enc);
+        if (d->d_dec) cudaFree(d->d_dec);
+        delete d;
+        return zs::cuda_fail(e, "uploading dictionary tables");
+    }
+    *out = d;
+    return ZS_OK;
+}
+
+extern "C" void zs_free_dictionary(zs_dict *d)
+{
+    if (!d) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    cudaSetDevice(d->device);
+    d->pool.release_all();
+    if (d->d_enc) cudaFree(d->d_enc);
+    if (d->d_dec) cudaFree(d->d_dec);
+    if (cur >= 0) cudaSetDevice(cur);
+    delete d;
+}

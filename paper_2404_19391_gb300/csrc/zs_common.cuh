@@ -1,0 +1,363 @@
+// Internal declarations shared by the ZSMILES CUDA translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "../../include/zsmiles.h"
+
+namespace zs {
+
+constexpr int kMaxPat = 16;       // longest pattern a dictionary may hold
+constexpr uint8_t kEsc = ' ';     // escape byte (Sec. IV-D1/IV-D2)
+constexpr uint8_t kNl = '\n';     // line separator
+
+// ------------------------------------------------------------------------------------------------
+// Encoder tables. The host builds one contiguous image that each compress CTA copies into shared
+// memory with a single bulk (TMA) copy. Offsets are 16-byte aligned.
+//
+//   [0, 256)                  cls[256]    byte -> character class (0: the byte occurs in no pattern)
+//   [256, 512)                plen[256]   symbol -> pattern length (0: not a symbol)
+//   [512, 640)                masks[32]   compact layout: mask id -> set of match lengths
+//   [off_trans, +trans_bytes) trans       reverse Aho-Corasick automaton, next state + match set
+//   [off_sym, +S*16)          sym[S][16]  symbol of the pattern of length l+1 that starts at the
+//                                          byte just read
+//
+// The automaton reads a line from its last byte to its first; after reading byte i its state is the
+// longest suffix of (s[n-1] ... s[i]) that is a prefix of some reversed pattern, so the match set of
+// the state is exactly {l : s[i..i+l) is a pattern of D} - the out-edges of node i in the paper's
+// graph G (Sec. IV-D1), in the order the backward shortest-path scan needs them.
+//
+// Transition entry: compact (u16) = next state (bits 0-10) | mask id (bits 11-15), used when the
+// automaton has <= 2048 states and <= 32 distinct match sets; wide (u32) = next state (bits 0-15) |
+// match set (bits 16-31).
+// ------------------------------------------------------------------------------------------------
+struct EncLayout {
+    uint32_t n_states;
+    uint32_t n_classes;
+    uint32_t compact;
+    uint32_t lmax;
+    uint32_t off_trans;
+    uint32_t off_sym;
+    uint32_t img_bytes;
+    uint32_t _pad;
+};
+
+constexpr uint32_t kOffCls = 0, kOffPlen = 256, kOffMasks = 512, kOffTrans = 640;
+
+// Decoder tables (global, staged per CTA): plen[256] then pat[256][16].
+constexpr uint32_t kDecBytes = 256 + 256 * kMaxPat;
+
+// ------------------------------------------------------------------------------------------------
+// Per-call device scratch
+// ------------------------------------------------------------------------------------------------
+struct alignas(16) TileState {
+    uint32_t flag;   // 0: nothing yet, 1: aggregate published, 2: inclusive prefix published
+    uint32_t _pad;
+    uint64_t agg_a, agg_b;  // this tile's totals (a: bytes, b: lines)
+    uint64_t inc_a, inc_b;  // totals of tiles [0, this] (valid when flag == 2)
+    uint64_t _pad2;
+};
+
+enum : uint32_t {
+    kStTimeout = 1u,       // a bounded wait expired
+    kStMalformed = 2u,     // bad compressed byte / request
+    kStSlowOverflow = 4u,  // the long/irregular-line scratch was too small (host retries larger)
+    kStTooBig = 8u,        // a single line needs more than 4 GiB of work space
+};
+
+struct alignas(16) DevResult {
+    unsigned long long tile_counter;  // dynamic tile ids, claimed in launch order
+    uint32_t status;                  // kSt* bits
+    uint32_t _pad;
+    unsigned long long out_len;       // total output bytes (written by the last tile)
+    unsigned long long n_lines;       // total lines / requests
+    unsigned long long err_key;       // max of (~offset): the smallest bad offset, 0 = none
+    unsigned long long slow_used;     // bytes of long-line scratch claimed
+    unsigned long long _pad2[2];
+};
+
+// Host-side scratch cached per (device, stream).
+struct Scratch {
+    int device = -1;
+    void *dev = nullptr;            // DevResult + TileState[cap_tiles]
+    size_t cap_tiles = 0;
+    uint8_t *slow = nullptr;        // long/irregular-line work space
+    size_t slow_cap = 0;
+    DevResult *host = nullptr;      // pinned mirror of DevResult
+};
+
+class ScratchPool {
+   public:
+    ~ScratchPool();
+    // Returns the scratch of `stream`, grown to hold `tiles` tile states and `slow` long-line bytes.
+    zs_status get(void *stream, size_t tiles, size_t slow, Scratch **out);
+    void release_all();
+
+   private:
+    std::mutex mu_;
+    std::map<void *, Scratch> map_;
+};
+
+ScratchPool &global_pool();
+
+// Thread-local error message.
+void set_error(const std::string &msg);
+void clear_error();
+zs_status cuda_fail(cudaError_t e, const char *what);
+
+// Bounded-wait default (device waits give up after this many nanoseconds).
+uint64_t wait_limit_ns();
+// Debug/fault-injection knobs, set from the environment of the calling process (tests only):
+//   ZS_WAIT_LIMIT_MS    overrides the wait limit
+//   ZS_INJECT_STALL     tile index whose look-back record is never published
+int64_t injected_stall_tile();
+
+}  // namespace zs
+
+// The dictionary handle.
+struct zs_dict {
+    int device = -1;
+    int lmax = 0;
+    zs::EncLayout layout{};
+    uint8_t *d_enc = nullptr;  // encoder image (layout.img_bytes)
+    uint8_t *d_dec = nullptr;  // decoder tables (kDecBytes)
+    uint8_t plen[256];
+    uint8_t pat[256][zs::kMaxPat];
+    zs::ScratchPool pool;
+};
+
+// ------------------------------------------------------------------------------------------------
+// Device helpers
+// ------------------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace zs {
+
+__device__ __forceinline__ uint64_t gtime()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Make generic-proxy writes to shared memory visible to a following bulk copy into the same bytes.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One-dimensional bulk copy global -> shared (cp.async.bulk): src, dst 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Waits for phase `phase` of `bar`; gives up after `limit_ns` (sets kStTimeout). Returns false on
+// timeout. A timed-out copy may still be in flight: the caller stops issuing new ones and the kernel
+// only finishes after the copy lands (see drain_bulk), so no write hits shared memory after exit.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint64_t limit_ns,
+                                                  uint32_t *status)
+{
+    if (mbar_try_wait(bar, phase)) return true;
+    uint64_t t0 = gtime();
+    for (;;) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (gtime() - t0 > limit_ns) {
+            atomicOr(status, kStTimeout);
+            return false;
+        }
+    }
+}
+
+// Warp-level inclusive sum.
+__device__ __forceinline__ uint32_t warp_incl_u32(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Block-wide exclusive sum of one value per thread; `tmp` holds NT/32 + 1 words. Returns the
+// exclusive prefix; *total gets the block total. Contains __syncthreads().
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_u32(uint32_t v, uint32_t *tmp, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = warp_incl_u32(v);
+    if (lane == 31) tmp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NT / 32 ? tmp[lane] : 0u;
+        uint32_t wi = warp_incl_u32(w);
+        if (lane < NT / 32) tmp[lane] = wi - w;
+        if (lane == NT / 32 - 1) tmp[NT / 32] = wi;
+    }
+    __syncthreads();
+    uint32_t r = tmp[warp] + inc - v;
+    *total = tmp[NT / 32];
+    __syncthreads();
+    return r;
+}
+
+// Block-wide exclusive sums of two 64-bit values per thread (NT threads, NT/32 <= 32). `tmp` holds
+// 2 * (NT/32 + 1) words. Returns the exclusive prefixes in *xa, *xb and the block totals in *ta, *tb.
+// Contains __syncthreads().
+template <int NT>
+__device__ __forceinline__ void block_excl2_u64(uint64_t a, uint64_t b, uint64_t *tmp, uint64_t *xa, uint64_t *xb,
+                                                uint64_t *ta, uint64_t *tb)
+{
+    constexpr int W = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t ua = __shfl_up_sync(0xffffffffu, ia, o);
+        uint64_t ub = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += ua;
+            ib += ub;
+        }
+    }
+    if (lane == 31) {
+        tmp[warp] = ia;
+        tmp[W + 1 + warp] = ib;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t wa = lane < W ? tmp[lane] : 0ull, wb = lane < W ? tmp[W + 1 + lane] : 0ull;
+        uint64_t sa = wa, sb = wb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t ua = __shfl_up_sync(0xffffffffu, sa, o);
+            uint64_t ub = __shfl_up_sync(0xffffffffu, sb, o);
+            if (lane >= o) {
+                sa += ua;
+                sb += ub;
+            }
+        }
+        if (lane < W) {
+            tmp[lane] = sa - wa;
+            tmp[W + 1 + lane] = sb - wb;
+        }
+        if (lane == W - 1) {
+            tmp[W] = sa;
+            tmp[2 * W + 1] = sb;
+        }
+    }
+    __syncthreads();
+    *xa = tmp[warp] + ia - a;
+    *xb = tmp[W + 1 + warp] + ib - b;
+    *ta = tmp[W];
+    *tb = tmp[2 * W + 1];
+    __syncthreads();
+}
+
+// Decoupled look-back (single thread): publish-free part. Sums the aggregates of tiles t-1, t-2, ...
+// until one has published its inclusive prefix. Waits are bounded; on expiry kStTimeout is set and
+// the sums so far are returned.
+__device__ __forceinline__ void lookback(TileState *tiles, uint64_t t, uint64_t *ea, uint64_t *eb,
+                                         uint64_t limit_ns, uint32_t *status)
+{
+    uint64_t a = 0, b = 0;
+    int64_t p = (int64_t)t - 1;
+    uint64_t t0 = 0;
+    bool timed = false;
+    while (p >= 0) {
+        uint32_t f = ld_acquire(&tiles[p].flag);
+        if (f == 0) {
+            if (*((volatile uint32_t *)status) & kStTimeout) break;
+            if (!timed) {
+                t0 = gtime();
+                timed = true;
+            } else if (gtime() - t0 > limit_ns) {
+                atomicOr(status, kStTimeout);
+                break;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        if (f == 2) {
+            a += tiles[p].inc_a;
+            b += tiles[p].inc_b;
+            break;
+        }
+        a += tiles[p].agg_a;
+        b += tiles[p].agg_b;
+        --p;
+        timed = false;
+    }
+    *ea = a;
+    *eb = b;
+}
+
+__device__ __forceinline__ void publish(TileState *ts, uint32_t flag, uint64_t a, uint64_t b)
+{
+    if (flag == 1) {
+        ts->agg_a = a;
+        ts->agg_b = b;
+    } else {
+        ts->inc_a = a;
+        ts->inc_b = b;
+    }
+    st_release(&ts->flag, flag);
+}
+
+__device__ __forceinline__ void note_error_offset(DevResult *r, uint64_t off)
+{
+    atomicMax(&r->err_key, ~(unsigned long long)off);
+}
+
+}  // namespace zs
+#endif

@@ -1,0 +1,219 @@
+"""Python binding of libzsmiles.so (the ZSMILES C ABI, include/zsmiles.h).
+
+Argument marshalling only: every step of compression, decompression, indexing and random access runs in
+the library's CUDA kernels. Device buffers are torch CUDA tensors (uint8 / int64 views of uint64 data);
+streams are torch.cuda streams (default: the current stream). There is no CPU fallback: importing this
+module on a machine where the library cannot be loaded raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+OK, ERR_INVALID_ARG, ERR_BAD_DICT, ERR_CAPACITY, ERR_MALFORMED, ERR_CUDA, ERR_TIMEOUT, ERR_OOM = range(8)
+STATUS_NAMES = ["ZS_OK", "ZS_ERR_INVALID_ARG", "ZS_ERR_BAD_DICT", "ZS_ERR_CAPACITY", "ZS_ERR_MALFORMED",
+                "ZS_ERR_CUDA", "ZS_ERR_TIMEOUT", "ZS_ERR_OOM"]
+PREPROCESS = 1
+
+DEFAULT_DICTIONARY = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "zs_default.zsd")
+
+
+class ZsError(RuntimeError):
+    def __init__(self, status: int, message: str, result: "Result | None" = None):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {message}")
+        self.status = status
+        self.result = result
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("out_len", ctypes.c_uint64), ("n_lines", ctypes.c_uint64), ("err_offset", ctypes.c_uint64)]
+
+
+@dataclass
+class Result:
+    out_len: int
+    n_lines: int
+    err_offset: int
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(rebuild: bool = False) -> ctypes.CDLL:
+    """Load (building first if needed) the in-tree libzsmiles.so."""
+    global _lib
+    if _lib is not None and not rebuild:
+        return _lib
+    path = _build.build() if (rebuild or not os.path.exists(_build.LIB)) else _build.LIB
+    lib = ctypes.CDLL(path)
+    vp, sz, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64
+    pres = ctypes.POINTER(_Result)
+    sig = {
+        "zs_load_dictionary": (ctypes.c_int, [vp, sz, ctypes.POINTER(vp)]),
+        "zs_free_dictionary": (None, [vp]),
+        "zs_dictionary_lmax": (ctypes.c_int, [vp]),
+        "zs_compress_bound": (sz, [sz]),
+        "zs_decompress_bound": (sz, [vp, sz]),
+        "zs_compress": (ctypes.c_int, [vp, vp, sz, ctypes.c_uint, vp, sz, vp, sz, pres, vp]),
+        "zs_decompress": (ctypes.c_int, [vp, vp, sz, vp, sz, pres, vp]),
+        "zs_build_line_index": (ctypes.c_int, [vp, sz, vp, sz, ctypes.POINTER(sz), vp]),
+        "zs_decompress_lines": (ctypes.c_int, [vp, vp, sz, vp, sz, vp, sz, vp, sz, vp, pres, vp]),
+        "zs_last_error": (ctypes.c_char_p, []),
+        "zs_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _L():
+    return _lib if _lib is not None else load_library()
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr() if t.numel() else None
+
+
+def _stream(stream) -> int | None:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+def _check(st: int, res: _Result | None = None):
+    if st != OK:
+        r = Result(res.out_len, res.n_lines, res.err_offset) if res is not None else None
+        raise ZsError(st, _L().zs_last_error().decode(), r)
+
+
+def zs_version() -> str:
+    return _L().zs_version().decode()
+
+
+def zs_compress_bound(in_len: int) -> int:
+    return int(_L().zs_compress_bound(in_len))
+
+
+class Dictionary:
+    """A loaded dictionary (zs_load_dictionary / zs_free_dictionary)."""
+
+    def __init__(self, file_bytes: bytes | None = None, path: str | None = None):
+        if file_bytes is None:
+            with open(path or DEFAULT_DICTIONARY, "rb") as f:
+                file_bytes = f.read()
+        self._bytes = bytes(file_bytes)
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(self._bytes, len(self._bytes))
+        _check(_L().zs_load_dictionary(buf, len(self._bytes), ctypes.byref(h)))
+        self.handle = h
+        self.lmax = int(_L().zs_dictionary_lmax(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _L().zs_free_dictionary(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decompress_bound(self, in_len: int) -> int:
+        return int(_L().zs_decompress_bound(self.handle, in_len))
+
+
+def zs_load_dictionary(file_bytes: bytes) -> Dictionary:
+    return Dictionary(file_bytes)
+
+
+def zs_compress(d: Dictionary, d_in: torch.Tensor, flags: int, d_out: torch.Tensor,
+                d_line_index: torch.Tensor | None = None, stream=None) -> Result:
+    res = _Result()
+    st = _L().zs_compress(d.handle, _ptr(d_in), d_in.numel(), flags, _ptr(d_out), d_out.numel(),
+                          _ptr(d_line_index), 0 if d_line_index is None else d_line_index.numel(),
+                          ctypes.byref(res), _stream(stream))
+    _check(st, res)
+    return Result(res.out_len, res.n_lines, res.err_offset)
+
+
+def zs_decompress(d: Dictionary, d_in: torch.Tensor, d_out: torch.Tensor, stream=None) -> Result:
+    res = _Result()
+    st = _L().zs_decompress(d.handle, _ptr(d_in), d_in.numel(), _ptr(d_out), d_out.numel(), ctypes.byref(res),
+                            _stream(stream))
+    _check(st, res)
+    return Result(res.out_len, res.n_lines, res.err_offset)
+
+
+def zs_build_line_index(d_in: torch.Tensor, d_index: torch.Tensor, stream=None) -> int:
+    n = ctypes.c_size_t(0)
+    st = _L().zs_build_line_index(_ptr(d_in), d_in.numel(), _ptr(d_index), d_index.numel(), ctypes.byref(n),
+                                  _stream(stream))
+    if st != OK:
+        raise ZsError(st, _L().zs_last_error().decode(), Result(0, n.value, 0))
+    return int(n.value)
+
+
+def zs_decompress_lines(d: Dictionary, d_comp: torch.Tensor, d_index: torch.Tensor, d_ids: torch.Tensor,
+                        d_out: torch.Tensor, d_out_off: torch.Tensor, stream=None) -> Result:
+    res = _Result()
+    st = _L().zs_decompress_lines(d.handle, _ptr(d_comp), d_comp.numel(), _ptr(d_index), d_index.numel() - 1,
+                                  _ptr(d_ids), d_ids.numel(), _ptr(d_out), d_out.numel(), _ptr(d_out_off),
+                                  ctypes.byref(res), _stream(stream))
+    _check(st, res)
+    return Result(res.out_len, res.n_lines, res.err_offset)
+
+
+# ---- conveniences built only from the calls above ----------------------------------------------------
+
+def compress(d: Dictionary, d_in: torch.Tensor, flags: int = PREPROCESS, with_index: bool = True, stream=None):
+    """Compress a device byte tensor; returns (compressed bytes, line index or None, Result)."""
+    out = torch.empty(zs_compress_bound(d_in.numel()), dtype=torch.uint8, device=d_in.device)
+    idx = None
+    if with_index:
+        n_lines = int(torch.count_nonzero(d_in == 10).item()) + 1
+        idx = torch.empty(n_lines + 1, dtype=torch.int64, device=d_in.device)
+    r = zs_compress(d, d_in, flags, out, idx, stream)
+    return out[: r.out_len], (idx[: r.n_lines + 1] if idx is not None else None), r
+
+
+def decompress(d: Dictionary, d_in: torch.Tensor, stream=None):
+    out = torch.empty(max(1, d.decompress_bound(d_in.numel())), dtype=torch.uint8, device=d_in.device)
+    r = zs_decompress(d, d_in, out, stream)
+    return out[: r.out_len], r
+
+
+def line_index(d_in: torch.Tensor, stream=None) -> torch.Tensor:
+    cap = int(torch.count_nonzero(d_in == 10).item()) + 2
+    idx = torch.empty(cap, dtype=torch.int64, device=d_in.device)
+    n = zs_build_line_index(d_in, idx, stream)
+    return idx[: n + 1]
+
+
+def decompress_lines(d: Dictionary, d_comp: torch.Tensor, d_index: torch.Tensor, d_ids: torch.Tensor,
+                     out_cap: int | None = None, stream=None):
+    if out_cap is None:
+        spans = (d_index[d_ids.clamp(max=d_index.numel() - 2) + 1] - d_index[d_ids.clamp(max=d_index.numel() - 2)])
+        out_cap = int(spans.sum().item()) * d.lmax + d_ids.numel() + 16
+    out = torch.empty(max(1, out_cap), dtype=torch.uint8, device=d_comp.device)
+    off = torch.empty(d_ids.numel() + 1, dtype=torch.int64, device=d_comp.device)
+    r = zs_decompress_lines(d, d_comp, d_index, d_ids, out, off, stream)
+    return out[: r.out_len], off, r
