@@ -292,8 +292,9 @@ __global__ void __launch_bounds__(kINT) line_index_kernel(IdxArgs A)
             }
         }
         __syncthreads();
-        // each newline at p ends line k and starts line k+1 at p+1 (the last one marks the end)
-        uint64_t rank = s_E + xa;
+        // each newline at p ends line k and starts line k+1 at p+1 (the last one marks the end); chunks of
+        // a warp interleave (iteration-major), so ranks come from the warp's base plus per-iteration scans
+        uint64_t rank = s_E + __shfl_sync(0xffffffffu, xa, 0);
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             uint32_t b = bits[it];
