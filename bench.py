@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the ZSMILES codec hot path on GB300.
+
+Workload (N=1): the large single-stream configuration - 10,000,000 seeded synthetic SMILES lines
+(drug-like, mean ~49 bytes, ~490 MB), one shard per launch, the frozen default dictionary.
+
+One step = the whole hot path over that stream, through the C ABI on device-resident data:
+    zs_compress (pre-processing + shortest-output parse + line index)
+    -> zs_decompress of the result
+    -> zs_decompress_lines of 100,000 random line ids (random access).
+value = uncompressed bytes per second of step (GB/s, 1e9). Inputs (490 MB) are larger than the 129 MB L2,
+so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--lines L]
+
+Under torchrun (N > 1) every rank runs its own replica on its own 10M-line range (weak scaling, no
+collective on the data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = None
+RA_IDS = 100_000
+HBM_FALLBACK_GBS = 6800.0
+
+
+def baseline_metric() -> str:
+    try:
+        with open(os.path.join(ROOT, "BASELINE.json")) as f:
+            return json.load(f)["metric"]
+    except Exception:
+        return "compress/decompress input GB/s (frac. of HBM peak); random-access p99 latency"
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch for `kernel` from the committed ncu summary, if the kernel source is unchanged
+    since the counters were taken (the summary records the sha256 of its source file); else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    for line in text.splitlines():
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel:
+            src, sha, traffic = parts[1], parts[2], float(parts[3])
+            cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+            return traffic if cur == sha else None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                rows.append((t, float(f[2]), float(f[3]), f[6:10]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if self.t0 is not None and self.t0 - 0.15 <= r[0] <= (self.t1 or r[0]) + 0.15]
+        use = inside or rows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in use for k in range(4) if r[3][k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples": len(use), "in_region": bool(inside)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_desc(lines: int, nbytes: int) -> str:
+    return (f"plain codec, large single stream: {lines:,} synthetic drug-like SMILES lines "
+            f"({nbytes / 1e6:.1f} MB, mean {nbytes / max(1, lines):.1f} B/line incl. newline), one shard per launch")
+
+
+# ---------------------------------------------------------------------------------------------------------
+# CPU oracle (the reported baseline; also the reference arm)
+# ---------------------------------------------------------------------------------------------------------
+
+def oracle_round_trip(raw: np.ndarray, threads: int):
+    import oracle
+    d = oracle.Dict(open(os.path.join(ROOT, "paper_2404_19391_gb300", "data", "zs_default.zsd"), "rb").read())
+    t0 = time.perf_counter()
+    comp, idx = oracle.compress_stream_parallel(d, raw, oracle.PREPROCESS, threads=threads)
+    t1 = time.perf_counter()
+    oracle.decompress_stream_parallel(d, comp, threads=threads)
+    t2 = time.perf_counter()
+    rng = np.random.default_rng(1)
+    ids = rng.integers(0, idx.size - 1, size=min(RA_IDS, idx.size - 1)).astype(np.uint64)
+    oracle.decompress_lines(d, comp, idx, ids)
+    t3 = time.perf_counter()
+    return t1 - t0, t2 - t1, t3 - t2
+
+
+def cpu_baseline(sample_lines: int, shape, threads: int | None = None):
+    threads = threads or (os.cpu_count() or 1)
+    raw = synth.generate(shape, 0, sample_lines)
+    tc, td, tr = oracle_round_trip(raw, threads)
+    total = tc + td + tr
+    return {"value": raw.size / total / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {sample_lines:,} lines ({raw.size / 1e6:.1f} MB) of the same stream; compress + "
+                      f"decompress line-partitioned over {threads} threads, then {RA_IDS:,}-id random access "
+                      f"(single thread)",
+            "seconds": round(total, 3), "compress_s": round(tc, 3), "decompress_s": round(td, 3),
+            "random_access_s": round(tr, 3)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    shape = synth.CFG1
+    sample = args.ref_sample_lines
+    raw = synth.generate(shape, 0, sample)
+    for _ in range(args.warmup):
+        oracle_round_trip(raw, threads)
+    times = []
+    for _ in range(args.steps):
+        tc, td, tr = oracle_round_trip(raw, threads)
+        times.append(tc + td + tr)
+    t = float(np.mean(times))
+    value = raw.size / t / 1e9
+    line = {"impl": "reference", "metric": baseline_metric(), "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": workload_desc(args.lines, synth.lines_size(shape, 0, args.lines)),
+                       "step": "CPU oracle round trip (compress + decompress + random access) over a bounded "
+                               "sample of the workload"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                             "sample": f"first {sample:,} lines ({raw.size / 1e6:.1f} MB) per step"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# GPU path
+# ---------------------------------------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    from paper_2404_19391_gb300 import zsmiles as zs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    zs.load_library()
+    d = zs.Dictionary()
+
+    shape = synth.CFG1
+    lines = args.lines
+    first = rank * lines
+    nbytes = synth.lines_size(shape, first, lines)
+    host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    synth.generate_into(shape, first, lines, host_in.data_ptr(), nbytes)
+    x = host_in.to(dev)
+
+    comp = torch.empty(zs.zs_compress_bound(nbytes), dtype=torch.uint8, device=dev)
+    idx = torch.empty(lines + 2, dtype=torch.int64, device=dev)
+    dec = torch.empty(d.decompress_bound(nbytes) // 2 + nbytes, dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(1000 + rank)
+    ids_host = torch.from_numpy(rng.integers(0, lines, size=RA_IDS).astype(np.int64)).pin_memory()
+    ids = ids_host.to(dev)
+    ra_out = torch.empty(RA_IDS * 256, dtype=torch.uint8, device=dev)
+    ra_off = torch.empty(RA_IDS + 1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    kms = {"compress": [], "decompress": [], "lines": []}
+    sizes = {}
+
+    def step(record=True):
+        r = zs.zs_compress(d, x, zs.PREPROCESS, comp, idx)
+        kc = zs.zs_last_kernel_ms()
+        c = comp[: r.out_len]
+        rd = zs.zs_decompress(d, c, dec)
+        kd = zs.zs_last_kernel_ms()
+        rl = zs.zs_decompress_lines(d, c, idx[: r.n_lines + 1], ids, ra_out, ra_off)
+        kl = zs.zs_last_kernel_ms()
+        if record:
+            kms["compress"].append(kc)
+            kms["decompress"].append(kd)
+            kms["lines"].append(kl)
+        sizes.update(comp=r.out_len, n_lines=r.n_lines, dec=rd.out_len, ra=rl.out_len)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step(record=False)
+    assert sizes["n_lines"] == lines and sizes["dec"] >= nbytes * 0.9
+
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = int(visible[local]) if len(visible) > local and visible[local].strip().isdigit() else local
+    clocks = ClockSampler(smi_index)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.mark(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks.mark(False)
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+
+    # ---- end to end: pinned host input -> device -> codec -> pinned host outputs, every step ----
+    host_comp = torch.empty(comp.numel(), dtype=torch.uint8, pin_memory=True)
+    host_idx = torch.empty(idx.numel(), dtype=torch.int64, pin_memory=True)
+    host_dec = torch.empty(sizes["dec"] + 16, dtype=torch.uint8, pin_memory=True)
+    host_ra = torch.empty(ra_out.numel(), dtype=torch.uint8, pin_memory=True)
+    host_off = torch.empty(ra_off.numel(), dtype=torch.int64, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    h2d = nbytes + ids_host.numel() * 8
+    d2h = 0
+
+    def e2e_step():
+        nonlocal d2h
+        x.copy_(host_in, non_blocking=True)
+        ids.copy_(ids_host, non_blocking=True)
+        r = zs.zs_compress(d, x, zs.PREPROCESS, comp, idx)
+        c = comp[: r.out_len]
+        rd = zs.zs_decompress(d, c, dec)
+        rl = zs.zs_decompress_lines(d, c, idx[: r.n_lines + 1], ids, ra_out, ra_off)
+        host_comp[: r.out_len].copy_(c, non_blocking=True)
+        host_idx[: r.n_lines + 1].copy_(idx[: r.n_lines + 1], non_blocking=True)
+        host_dec[: rd.out_len].copy_(dec[: rd.out_len], non_blocking=True)
+        host_ra[: rl.out_len].copy_(ra_out[: rl.out_len], non_blocking=True)
+        host_off.copy_(ra_off, non_blocking=True)
+        d2h = r.out_len + (r.n_lines + 1) * 8 + rd.out_len + rl.out_len + ra_off.numel() * 8
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks.stop()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+
+    ms_step = ms_total / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, e2e_ms = float(t[0]), float(t[1])
+        nb = torch.tensor([float(nbytes)], dtype=torch.float64, device=dev)
+        dist.all_reduce(nb, op=dist.ReduceOp.SUM)
+        total_bytes = float(nb[0])
+    else:
+        total_bytes = float(nbytes)
+
+    value = total_bytes / (ms_step * 1e-3) / 1e9
+    peak, peak_kind = hbm_peak()
+    kc = float(np.mean(kms["compress"]))
+    kd = float(np.mean(kms["decompress"]))
+    kl = float(np.mean(kms["lines"]))
+    comp_bytes = nbytes + sizes["comp"] + 8 * (sizes["n_lines"] + 1)   # read input, write output + index
+    dec_bytes = sizes["comp"] + sizes["dec"]                            # read compressed, write decoded
+    achieved_c = comp_bytes / (kc * 1e-3) / 1e9
+    achieved_d = dec_bytes / (kd * 1e-3) / 1e9
+    traffic = kernel_traffic("compress_kernel")
+
+    if rank == 0:
+        line = {
+            "metric": baseline_metric(), "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(lines, nbytes), "lines_per_rank": lines,
+                       "bytes_per_rank": nbytes, "dictionary": "frozen default (Algorithm 1, seed-1 100k-line "
+                                                               "training set, L_max 8, T 146)",
+                       "step": f"zs_compress + zs_decompress + zs_decompress_lines({RA_IDS:,} random ids)",
+                       "l2": "inputs (and outputs) larger than the 129 MB L2; no flush",
+                       "parallelism": f"{world} independent replica(s)"},
+            "clocks": clocks.summary(),
+            "e2e": {"value": total_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "how": "pinned host input H2D, the three C-ABI calls, D2H of compressed stream, index, "
+                           "decoded stream and random-access output, every step"},
+            "gpu_launches": 3 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved_c, "peak": peak, "unit": "GB/s",
+                         "frac": achieved_c / peak, "traffic": traffic, "kernel": "compress_kernel",
+                         "peak_kind": f"{peak_kind} (copy, MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": comp_bytes, "kernel_ms": kc},
+            "compress": {"kernel_ms": kc, "gbps_in": nbytes / (kc * 1e-3) / 1e9,
+                         "lines_per_s": lines / (kc * 1e-3), "hbm_gbps": achieved_c, "hbm_frac": achieved_c / peak,
+                         "ratio": sizes["comp"] / nbytes},
+            "decompress": {"kernel_ms": kd, "gbps_in": sizes["comp"] / (kd * 1e-3) / 1e9,
+                           "gbps_out": sizes["dec"] / (kd * 1e-3) / 1e9, "hbm_gbps": achieved_d,
+                           "hbm_frac": achieved_d / peak},
+            "random_access": {"ids": RA_IDS, "kernel_ms": kl, "lines_per_s": RA_IDS / (kl * 1e-3),
+                              "p99_ms": float(np.percentile(kms["lines"], 99))},
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_sample_lines, shape)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lines", type=int, default=synth.CFG1_LINES)
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--cpu-sample-lines", type=int, default=1_000_000)
+    ap.add_argument("--ref-sample-lines", type=int, default=400_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

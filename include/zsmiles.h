@@ -156,6 +156,11 @@ zs_status zs_decompress_lines(const zs_dict *d, const uint8_t *d_comp, size_t co
                               size_t n_lines, const uint64_t *d_ids, size_t k, uint8_t *d_out, size_t out_cap,
                               uint64_t *d_out_off, zs_result *res, void *stream);
 
+/* Device time, in milliseconds, of the main kernel of the last successful zs_compress, zs_decompress,
+ * zs_build_line_index or zs_decompress_lines on this thread, measured with CUDA events recorded on the
+ * call's stream just before and just after the kernel launch (no paper counterpart: instrumentation). */
+double zs_last_kernel_ms(void);
+
 /* Message for the last failing call on this thread ("" if none). Valid until the next call. */
 const char *zs_last_error(void);
 

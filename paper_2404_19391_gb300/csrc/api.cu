@@ -7,6 +7,23 @@
 namespace zs {
 
 static thread_local std::string t_error;
+static thread_local double t_kernel_ms = 0.0;
+
+void mark_kernel_start(Scratch *sc, cudaStream_t s)
+{
+    if (!sc->ev0) cudaEventCreate(&sc->ev0);
+    if (!sc->ev1) cudaEventCreate(&sc->ev1);
+    cudaEventRecord(sc->ev0, s);
+}
+
+void mark_kernel_end(Scratch *sc, cudaStream_t s) { cudaEventRecord(sc->ev1, s); }
+
+void note_kernel_time(Scratch *sc)
+{
+    float ms = 0.f;
+    if (sc->ev0 && sc->ev1 && cudaEventElapsedTime(&ms, sc->ev0, sc->ev1) == cudaSuccess) t_kernel_ms = ms;
+    else cudaGetLastError();
+}
 
 void set_error(const std::string &msg) { t_error = msg; }
 void clear_error() { t_error.clear(); }
@@ -47,6 +64,8 @@ void ScratchPool::release_all()
         if (s.dev) cudaFree(s.dev);
         if (s.slow) cudaFree(s.slow);
         if (s.host) cudaFreeHost(s.host);
+        if (s.ev0) cudaEventDestroy(s.ev0);
+        if (s.ev1) cudaEventDestroy(s.ev1);
     }
     map_.clear();
     if (cur >= 0) cudaSetDevice(cur);
@@ -120,6 +139,8 @@ ScratchPool &global_pool()
 }  // namespace zs
 
 extern "C" const char *zs_last_error(void) { return zs::t_error.c_str(); }
+
+extern "C" double zs_last_kernel_ms(void) { return zs::t_kernel_ms; }
 
 extern "C" const char *zs_version(void) { return "zsmiles-gb300 0.1 (sm_103a)"; }
 

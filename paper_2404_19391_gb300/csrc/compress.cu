@@ -989,13 +989,16 @@ extern "C" zs_status zs_compress(const zs_dict *d, const uint8_t *d_in, size_t i
         zs::TileState *tiles = reinterpret_cast<zs::TileState *>(dr + 1);
         e = cudaMemsetAsync(sc->dev, 0, sizeof(zs::DevResult) + ntiles * sizeof(zs::TileState), s);
         if (e != cudaSuccess) return zs::cuda_fail(e, "zs_compress: memset");
+        zs::mark_kernel_start(sc, s);
         e = zs::launch_compress(d, d_in, in_len, flags, d_out, out_cap, d_line_index, d_line_index ? index_cap : 0,
                                 dr, tiles, sc->slow, sc->slow_cap, s);
         if (e != cudaSuccess) return zs::cuda_fail(e, "zs_compress: launch");
+        zs::mark_kernel_end(sc, s);
         e = cudaMemcpyAsync(sc->host, dr, sizeof(zs::DevResult), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return zs::cuda_fail(e, "zs_compress");
         const zs::DevResult r = *sc->host;
+        zs::note_kernel_time(sc);
         if (r.status & zs::kStSlowOverflow) {
             slow_need = (size_t)r.slow_used + ((size_t)r.slow_used >> 2) + (1u << 20);
             continue;

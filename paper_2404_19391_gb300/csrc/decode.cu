@@ -556,11 +556,16 @@ zs_status run(zs::ScratchPool &pool, void *stream, uint64_t ntiles, const char *
     zs::DevResult *dr = reinterpret_cast<zs::DevResult *>(sc->dev);
     zs::TileState *tiles = reinterpret_cast<zs::TileState *>(dr + 1);
     cudaError_t e = cudaMemsetAsync(sc->dev, 0, sizeof(zs::DevResult) + ntiles * sizeof(zs::TileState), s);
-    if (e == cudaSuccess) e = launch(dr, tiles, s);
+    if (e == cudaSuccess) {
+        zs::mark_kernel_start(sc, s);
+        e = launch(dr, tiles, s);
+        zs::mark_kernel_end(sc, s);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(sc->host, dr, sizeof(zs::DevResult), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return zs::cuda_fail(e, what);
     *r = *sc->host;
+    zs::note_kernel_time(sc);
     if (r->status & zs::kStTimeout) {
         zs::set_error(std::string(what) + ": a device-side wait expired");
         return ZS_ERR_TIMEOUT;

@@ -89,6 +89,7 @@ struct Scratch {
     uint8_t *slow = nullptr;        // long/irregular-line work space
     size_t slow_cap = 0;
     DevResult *host = nullptr;      // pinned mirror of DevResult
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the call's main kernel (zs_last_kernel_ms)
 };
 
 class ScratchPool {
@@ -104,6 +105,12 @@ class ScratchPool {
 };
 
 ScratchPool &global_pool();
+
+// Kernel timing: record ev0/ev1 of `sc` around a launch on `s`; after the stream is synchronised,
+// note_kernel_time() stores the elapsed milliseconds for zs_last_kernel_ms().
+void mark_kernel_start(Scratch *sc, cudaStream_t s);
+void mark_kernel_end(Scratch *sc, cudaStream_t s);
+void note_kernel_time(Scratch *sc);
 
 // Thread-local error message.
 void set_error(const std::string &msg);

@@ -69,6 +69,7 @@ def load_library(rebuild: bool = False) -> ctypes.CDLL:
         "zs_decompress_lines": (ctypes.c_int, [vp, vp, sz, vp, sz, vp, sz, vp, sz, vp, pres, vp]),
         "zs_last_error": (ctypes.c_char_p, []),
         "zs_version": (ctypes.c_char_p, []),
+        "zs_last_kernel_ms": (ctypes.c_double, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -105,6 +106,10 @@ def _check(st: int, res: _Result | None = None):
 
 def zs_version() -> str:
     return _L().zs_version().decode()
+
+
+def zs_last_kernel_ms() -> float:
+    return float(_L().zs_last_kernel_ms())
 
 
 def zs_compress_bound(in_len: int) -> int:
