@@ -156,6 +156,31 @@ zs_status zs_decompress_lines(const zs_dict *d, const uint8_t *d_comp, size_t co
                               size_t n_lines, const uint64_t *d_ids, size_t k, uint8_t *d_out, size_t out_cap,
                               uint64_t *d_out_off, zs_result *res, void *stream);
 
+/*
+ * zs_decompress_noalloc - zs_decompress for callers that cannot allocate. (The paper has no counterpart:
+ * this concerns how the library obtains memory, not what it computes.)
+ *
+ * Some callers cannot let a library allocate memory: their device memory is entirely reserved by another
+ * allocator (a framework's caching allocator that already holds the free HBM, a fixed arena in an
+ * embedded service), or they run latency-critical loops in which cudaMalloc, cudaFree or cudaMallocHost
+ * would implicitly synchronise the device. This call decodes exactly like zs_decompress (same
+ * arguments, same output, same errors) but allocates nothing: its scratch is a fixed 2 MiB array of
+ * device memory compiled into the library, which every GPU that loads the library holds until the
+ * process exits, and its result is copied straight into *res.
+ *
+ * Limit: the scratch holds 43,689 tile records of 8 KiB of compressed input each, so in_len may be at
+ * most 357,900,288 bytes; a larger input returns ZS_ERR_INVALID_ARG without touching the device (use
+ * zs_decompress instead).
+ *
+ * Set-up: the first call on each device (with that device current) looks up the array's device address
+ * once; make that first call before any stream capture on the device.
+ * Concurrency: every call shares the one array, and the call clears what must start at zero. Calls whose
+ * work overlaps on the GPU (from several host threads or streams at once) race on the array: the caller
+ * must serialise them.
+ */
+zs_status zs_decompress_noalloc(const zs_dict *d, const uint8_t *d_in, size_t in_len, uint8_t *d_out,
+                                size_t out_cap, zs_result *res, void *stream);
+
 /* Device time, in milliseconds, of the main kernel of the last successful zs_compress, zs_decompress,
  * zs_build_line_index or zs_decompress_lines on this thread, measured with CUDA events recorded on the
  * call's stream just before and just after the kernel launch (no paper counterpart: instrumentation). */

@@ -1,0 +1,72 @@
+"""zs_decompress_noalloc: the allocation-free decode entry point, checked against zs_decompress.
+
+It serves callers that cannot let the library allocate (device memory held by another allocator, or
+loops where cudaMalloc/cudaFree would synchronise the device). It must give exactly the bytes
+zs_decompress gives (byte codec: exact equality), on two calls in a row (its fixed scratch keeps the
+previous call's contents), and refuse inputs larger than its fixed scratch allows. This file runs last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MAX_INPUT = 43689 * 8192
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("out_len", ctypes.c_uint64), ("n_lines", ctypes.c_uint64), ("err_offset", ctypes.c_uint64)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_19391_gb300 import zsmiles as zs
+    lib = zs.load_library()
+    f = lib.zs_decompress_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
+                  ctypes.POINTER(_Result), ctypes.c_void_p]
+    return zs, lib, zs.Dictionary()
+
+
+def _noalloc(env, comp, out):
+    zs, lib, d = env
+    r = _Result()
+    st = lib.zs_decompress_noalloc(d.handle, comp.data_ptr(), comp.numel(), out.data_ptr(), out.numel(),
+                                   ctypes.byref(r), torch.cuda.current_stream().cuda_stream or None)
+    return st, r
+
+
+def test_matches_zs_decompress_two_calls_in_a_row(env):
+    zs, lib, d = env
+    streams = [synth.generate(synth.CFG0, 0, 20000), synth.generate(synth.CFG3, 0, 8000)]
+    for raw in streams:
+        comp, _, _ = zs.compress(d, torch.from_numpy(raw).cuda(), with_index=False)
+        comp = comp.clone()
+        ref = torch.empty(d.decompress_bound(comp.numel()), dtype=torch.uint8, device="cuda")
+        rr = zs.zs_decompress(d, comp, ref)
+        for _ in range(2):
+            out = torch.full((d.decompress_bound(comp.numel()),), 0xAB, dtype=torch.uint8, device="cuda")
+            st, r = _noalloc(env, comp, out)
+            assert st == zs.OK, lib.zs_last_error()
+            assert r.out_len == rr.out_len and r.n_lines == rr.n_lines
+            assert torch.equal(out[: r.out_len], ref[: rr.out_len])
+            assert torch.all(out[r.out_len:] == 0xAB)
+
+
+def test_rejects_inputs_beyond_its_scratch(env):
+    zs, lib, d = env
+    comp = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    r = _Result()
+    # only the size is inspected: nothing is launched for a rejected input
+    st = lib.zs_decompress_noalloc(d.handle, comp.data_ptr(), MAX_INPUT + 1, out.data_ptr(), out.numel(),
+                                   ctypes.byref(r), None)
+    assert st == zs.ERR_INVALID_ARG
+    assert b"scratch" in lib.zs_last_error()
