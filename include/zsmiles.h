@@ -83,6 +83,12 @@ zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, zs_dict **ou
  * have work in flight that uses the handle. NULL is ignored. */
 void zs_free_dictionary(zs_dict *d);
 
+/* 1 if zs_compress with this dictionary runs the parse-transducer kernel on the current device (the
+ * shortest-path scan of Sec. IV-D1 compiled into one table lookup per byte, built at load time), 0 if it
+ * runs the generic kernel (automaton walk plus window scan per byte) because the transducer's state space
+ * or table does not fit. Both produce identical output. (Informational; the paper has no counterpart.) */
+int zs_dictionary_uses_transducer(const zs_dict *d);
+
 /* Longest pattern of D (the most bytes one symbol can expand to). */
 int zs_dictionary_lmax(const zs_dict *d);
 

@@ -22,10 +22,11 @@
 //     scratch.
 #include <algorithm>
 
-#include "zs_common.cuh"
+#include "compress_shared.cuh"
 
 namespace zs {
 namespace {
+using namespace cx;
 
 constexpr int kNT = 256;                  // threads per CTA
 constexpr int kTB = 16384;                // owned bytes per tile
@@ -97,20 +98,6 @@ struct Vars {
     uint32_t halo_hit;
     uint32_t pad;
 };
-
-__device__ __forceinline__ uint32_t zero_byte_bits(uint32_t t)
-{
-    uint32_t z = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t | 0x7F7F7F7Fu);
-    return ((z >> 7) & 1u) | ((z >> 14) & 2u) | ((z >> 21) & 4u) | ((z >> 28) & 8u);
-}
-
-// bit i set iff byte i of the 16-byte chunk is '\n'
-__device__ __forceinline__ uint32_t nl_bits16(uint4 v)
-{
-    const uint32_t k = 0x0A0A0A0Au;
-    return zero_byte_bits(v.x ^ k) | (zero_byte_bits(v.y ^ k) << 4) | (zero_byte_bits(v.z ^ k) << 8) |
-           (zero_byte_bits(v.w ^ k) << 12);
-}
 
 // Block exclusive scan of 64-bit values (NT threads).
 __device__ __forceinline__ uint64_t block_excl_u64(uint64_t v, uint64_t *tmp, uint64_t *total)
@@ -247,109 +234,6 @@ __device__ __forceinline__ int preprocess_inplace(uint8_t *st, int a, int n, con
 }
 
 // ------------------------------------------------------------------------------------------------
-// Pre-processing, slow path: any line, work space in global memory. Two passes: label every ring
-// token (same streaming rule, labels up to 99), then write the relabelled line (1- or 3-byte labels).
-// tok: one byte per ring token; lcv/open_tok: 100 ints each. Returns the new length.
-// ------------------------------------------------------------------------------------------------
-__device__ uint32_t preprocess_slow(const uint8_t *s, uint32_t n, uint8_t *out, uint8_t *tok, int32_t *lcv,
-                                    int32_t *open_tok)
-{
-    for (int k = 0; k < 100; ++k) {
-        lcv[k] = 0;
-        open_tok[k] = -1;
-    }
-    uint32_t f = 0;
-    while (f < n && s[f] != ' ' && s[f] != '\t') ++f;
-    bool ok = true, in_br = false;
-    int32_t ord = 0;
-    for (uint32_t r = 0; r < f && ok;) {
-        uint8_t c = s[r];
-        if (in_br) {
-            if (c == ']') in_br = false;
-            ++r;
-            continue;
-        }
-        if (c == '[') {
-            in_br = true;
-            ++r;
-            continue;
-        }
-        int lab = -1, tl = 1;
-        if (c == '%') {
-            if (r + 2 < f && s[r + 1] >= '0' && s[r + 1] <= '9' && s[r + 2] >= '0' && s[r + 2] <= '9') {
-                lab = (s[r + 1] - '0') * 10 + (s[r + 2] - '0');
-                tl = 3;
-            } else {
-                ok = false;
-                break;
-            }
-        } else if (c >= '0' && c <= '9') {
-            lab = c - '0';
-        }
-        if (lab >= 0) {
-            if (open_tok[lab] < 0) {
-                open_tok[lab] = ord;
-            } else {
-                int32_t o = open_tok[lab];
-                int nl = 0;
-                while (nl < 100 && lcv[nl] > o + 1) ++nl;
-                if (nl > 99) {
-                    ok = false;
-                    break;
-                }
-                tok[o] = (uint8_t)nl;
-                tok[ord] = (uint8_t)nl;
-                lcv[nl] = ord + 1;
-                open_tok[lab] = -1;
-            }
-            ++ord;
-        }
-        r += tl;
-    }
-    if (in_br) ok = false;
-    for (int k = 0; k < 100 && ok; ++k)
-        if (open_tok[k] >= 0) ok = false;
-    if (!ok) {
-        for (uint32_t i = 0; i < n; ++i) out[i] = s[i];
-        return n;
-    }
-    uint32_t w = 0;
-    ord = 0;
-    in_br = false;
-    for (uint32_t r = 0; r < f;) {
-        uint8_t c = s[r];
-        if (in_br) {
-            if (c == ']') in_br = false;
-            out[w++] = c;
-            ++r;
-            continue;
-        }
-        if (c == '[') {
-            in_br = true;
-            out[w++] = c;
-            ++r;
-            continue;
-        }
-        if (c == '%' || (c >= '0' && c <= '9')) {
-            int nl = tok[ord++];
-            if (nl < 10) {
-                out[w++] = (uint8_t)('0' + nl);
-            } else {
-                out[w++] = '%';
-                out[w++] = (uint8_t)('0' + nl / 10);
-                out[w++] = (uint8_t)('0' + nl % 10);
-            }
-            r += (c == '%') ? 3 : 1;
-            continue;
-        }
-        out[w++] = c;
-        ++r;
-    }
-    for (uint32_t r = f; r < n; ++r) out[w++] = s[r];
-    return w;
-}
-
-// ------------------------------------------------------------------------------------------------
 // Backward shortest-path scan (Sec. IV-D1). best[i] = min(best[i+1] + (s[i] in D ? 1 : 2),
 // min over matches l >= 2 at i of best[i+l] + 1); ties go to the longest piece (an escape loses to
 // everything). Writes at choice[i] the symbol chosen at i (kEsc for an escape); text and choice may
@@ -407,56 +291,6 @@ __device__ __forceinline__ uint32_t parse_backward(TP text, CP choice, uint32_t 
     }
     *esc = e;
     return w[0];
-}
-
-// Emission of one line: walk the choices front to back.
-template <class CP, class TP, class Sink>
-__device__ __forceinline__ void emit_line(CP choice, TP raw, uint32_t n, const uint8_t *plen, Sink &out)
-{
-    for (uint32_t i = 0; i < n;) {
-        uint8_t s = choice[i];
-        if (s == kEsc) {
-            out.put(kEsc);
-            out.put(raw[i]);
-            i += 1;
-        } else {
-            out.put(s);
-            i += plen[s];
-        }
-    }
-}
-
-struct SmemSink {
-    uint8_t *p;
-    __device__ __forceinline__ void put(uint8_t b) { *p++ = b; }
-};
-
-struct GlobalSink {
-    uint8_t *out;
-    uint64_t pos, cap;
-    __device__ __forceinline__ void put(uint8_t b)
-    {
-        if (pos < cap) out[pos] = b;
-        ++pos;
-    }
-};
-
-// Work space of one slow line of n input bytes: a 16-byte header {n, pre-processed length}, the
-// pre-processed text (<= 3n bytes: a 1-byte label can become %nn), the chosen symbols, one label byte per
-// ring token, and the 2 x 100 ints of the relabelling tables.
-struct SlowLayout {
-    uint64_t text, chs, tok, tables, need;
-};
-
-__device__ __forceinline__ SlowLayout slow_layout(uint32_t n)
-{
-    SlowLayout s;
-    s.text = 16;
-    s.chs = s.text + 3ull * n + 16;
-    s.tok = s.chs + 3ull * n + 16;
-    s.tables = (s.tok + n + 16 + 15) & ~15ull;
-    s.need = (s.tables + 800 + 15) & ~15ull;
-    return s;
 }
 
 template <int LMAX, bool COMPACT>
@@ -917,6 +751,43 @@ cudaError_t launch_compress(const zs_dict *d, const uint8_t *in, uint64_t n, uns
 
 uint64_t compress_tiles(uint64_t n) { return (n + kTB - 1) / kTB; }
 
+uint64_t compress_warp_tiles(uint64_t n);
+size_t compress_warp_smem(const zs_dict *d);
+cudaError_t launch_compress_warp(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,
+                                 uint64_t out_cap, uint64_t *index, uint64_t index_cap, DevResult *res,
+                                 TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s);
+
+// The transducer kernel runs when the dictionary has a transducer and its tables fit in shared memory;
+// otherwise the generic kernel (automaton + window scan per byte) runs.
+bool use_transducer(const zs_dict *d)
+{
+    if (!d->has_machine) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return compress_warp_smem(d) <= (size_t)optin;
+}
+
+}  // namespace zs
+
+extern "C" int zs_dictionary_uses_transducer(const zs_dict *d) { return d && zs::use_transducer(d) ? 1 : 0; }
+
+namespace zs {
+
+uint64_t compress_scratch_tiles(const zs_dict *d, uint64_t n)
+{
+    return use_transducer(d) ? compress_warp_tiles(n) : compress_tiles(n);
+}
+
+cudaError_t launch_compress_any(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,
+                                uint64_t out_cap, uint64_t *index, uint64_t index_cap, DevResult *res,
+                                TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s)
+{
+    if (use_transducer(d))
+        return launch_compress_warp(d, in, n, flags, out, out_cap, index, index_cap, res, tiles, slow, slow_cap, s);
+    return launch_compress(d, in, n, flags, out, out_cap, index, index_cap, res, tiles, slow, slow_cap, s);
+}
+
 }  // namespace zs
 
 namespace {
@@ -979,7 +850,7 @@ extern "C" zs_status zs_compress(const zs_dict *d, const uint8_t *d_in, size_t i
         }
         return ZS_OK;
     }
-    const uint64_t ntiles = zs::compress_tiles(in_len);
+    const uint64_t ntiles = zs::compress_scratch_tiles(d, in_len);
     size_t slow_need = 16u << 20;
     for (int attempt = 0; attempt < 3; ++attempt) {
         zs::Scratch *sc = nullptr;
@@ -990,8 +861,8 @@ extern "C" zs_status zs_compress(const zs_dict *d, const uint8_t *d_in, size_t i
         e = cudaMemsetAsync(sc->dev, 0, sizeof(zs::DevResult) + ntiles * sizeof(zs::TileState), s);
         if (e != cudaSuccess) return zs::cuda_fail(e, "zs_compress: memset");
         zs::mark_kernel_start(sc, s);
-        e = zs::launch_compress(d, d_in, in_len, flags, d_out, out_cap, d_line_index, d_line_index ? index_cap : 0,
-                                dr, tiles, sc->slow, sc->slow_cap, s);
+        e = zs::launch_compress_any(d, d_in, in_len, flags, d_out, out_cap, d_line_index,
+                                    d_line_index ? index_cap : 0, dr, tiles, sc->slow, sc->slow_cap, s);
         if (e != cudaSuccess) return zs::cuda_fail(e, "zs_compress: launch");
         zs::mark_kernel_end(sc, s);
         e = cudaMemcpyAsync(sc->host, dr, sizeof(zs::DevResult), cudaMemcpyDeviceToHost, s);

@@ -1,9 +1,13 @@
 // zs_load_dictionary: parse the dictionary file and build the encoder automaton and decoder tables.
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <deque>
+#include <map>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "zs_common.cuh"
@@ -117,6 +121,138 @@ struct Node {
 
 }  // namespace
 
+// ------------------------------------------------------------------------------------------------
+// Parse transducer.
+//
+// The backward shortest-path scan (Sec. IV-D1) needs, at position i, the match set of i (a function of
+// the automaton state after reading s[i]) and best[i+1 .. i+Lp] for the longest pattern length Lp. The
+// choice at i and the increment best[i] - best[i+1] depend on those values only through their
+// differences, and with match cost 1 and escape cost 2 the differences stay bounded. So the pair
+// (automaton state, window of best values relative to best[i]) ranges over a finite set, and the
+// whole scan is a finite-state transducer: per byte class it moves to a next state and outputs the
+// increment of best and the symbol chosen at that byte (' ' for an escape). Its reachable states are
+// enumerated breadth-first and then merged by Moore partition refinement (states with identical output
+// sequences for every input are equivalent); the minimal table is what the kernel walks, one lookup
+// per byte. Returns false when the state space or the table exceeds the given limits.
+// ------------------------------------------------------------------------------------------------
+struct Machine {
+    std::vector<uint32_t> table;  // [states][classes]: next | (delta + 16) << 16 | symbol << 24
+    int states = 0;
+    int start = 0;
+};
+
+bool build_machine(const std::vector<std::vector<int>> &delta, const std::vector<uint32_t> &mask,
+                   const std::vector<std::vector<uint8_t>> &sym, int n_classes, int Lp, size_t max_states,
+                   size_t max_table_bytes, Machine *out)
+{
+    const int W = Lp > 1 ? Lp - 1 : 0;  // window: best[i+1..i+Lp-1] - best[i]
+    const int8_t INF = 127;
+    struct Entry {
+        int next;
+        int delta;
+        uint8_t sym;
+    };
+    std::unordered_map<std::string, int> id;
+    std::vector<std::string> keys;
+    auto key_of = [&](int ac, const int8_t *w) {
+        std::string k(2 + W, '\0');
+        k[0] = (char)(ac & 0xFF);
+        k[1] = (char)(ac >> 8);
+        for (int j = 0; j < W; ++j) k[2 + j] = (char)w[j];
+        return k;
+    };
+    std::vector<int8_t> w0(W > 0 ? W : 1, INF);
+    std::string k0 = key_of(0, w0.data());
+    id[k0] = 0;
+    keys.push_back(k0);
+    std::vector<std::vector<Entry>> rows;
+    for (size_t qi = 0; qi < keys.size(); ++qi) {
+        const std::string cur = keys[qi];
+        const int ac = (uint8_t)cur[0] | ((uint8_t)cur[1] << 8);
+        const int8_t *w = reinterpret_cast<const int8_t *>(cur.data() + 2);
+        std::vector<Entry> row(n_classes);
+        for (int c = 0; c < n_classes; ++c) {
+            const int a2 = delta[ac][c];
+            const uint32_t m = mask[a2];
+            int best = (m & 1u) ? 1 : 2, pick = 1;
+            for (int l = 2; l <= Lp; ++l) {
+                if (!((m >> (l - 1)) & 1u)) continue;
+                const int v = w[l - 2];
+                if (v == INF) return false;  // cannot happen: matches never reach past the line end
+                if (1 + v <= best) {
+                    best = 1 + v;
+                    pick = l;
+                }
+            }
+            const uint8_t sy = (pick == 1 && !(m & 1u)) ? (uint8_t)' ' : sym[a2][pick - 1];
+            std::vector<int8_t> nw(W > 0 ? W : 1, INF);
+            if (W > 0) {
+                nw[0] = (int8_t)(-best);
+                for (int j = 1; j < W; ++j) nw[j] = (w[j - 1] == INF) ? INF : (int8_t)(w[j - 1] - best);
+            }
+            std::string nk = key_of(a2, nw.data());
+            auto it = id.find(nk);
+            int nid;
+            if (it == id.end()) {
+                if (keys.size() >= max_states) return false;
+                nid = (int)keys.size();
+                id.emplace(nk, nid);
+                keys.push_back(nk);
+            } else {
+                nid = it->second;
+            }
+            row[c] = {nid, best, sy};
+        }
+        rows.push_back(std::move(row));
+    }
+    const int N = (int)rows.size();
+
+    // Moore refinement: start from the partition by output rows, split by successor classes
+    std::vector<int> part(N), np(N);
+    {
+        std::map<std::vector<int>, int> sig;
+        for (int i = 0; i < N; ++i) {
+            std::vector<int> v(2 * n_classes);
+            for (int c = 0; c < n_classes; ++c) {
+                v[2 * c] = rows[i][c].delta;
+                v[2 * c + 1] = rows[i][c].sym;
+            }
+            auto it = sig.emplace(std::move(v), (int)sig.size()).first;
+            part[i] = it->second;
+        }
+    }
+    int nparts = 0;
+    for (int i = 0; i < N; ++i) nparts = std::max(nparts, part[i] + 1);
+    for (;;) {
+        std::map<std::vector<int>, int> sig;
+        for (int i = 0; i < N; ++i) {
+            std::vector<int> v(n_classes + 1);
+            v[0] = part[i];
+            for (int c = 0; c < n_classes; ++c) v[c + 1] = part[rows[i][c].next];
+            auto it = sig.emplace(std::move(v), (int)sig.size()).first;
+            np[i] = it->second;
+        }
+        const int n2 = (int)sig.size();
+        part.swap(np);
+        if (n2 == nparts) break;
+        nparts = n2;
+    }
+    if (nparts > 65535 || (size_t)nparts * n_classes * 4 > max_table_bytes) return false;
+    std::vector<int> rep(nparts, -1);
+    for (int i = 0; i < N; ++i)
+        if (rep[part[i]] < 0) rep[part[i]] = i;
+    out->states = nparts;
+    out->start = part[0];
+    out->table.assign((size_t)nparts * n_classes, 0);
+    for (int p2 = 0; p2 < nparts; ++p2)
+        for (int c = 0; c < n_classes; ++c) {
+            const Entry &e = rows[rep[p2]][c];
+            out->table[(size_t)p2 * n_classes + c] =
+                (uint32_t)part[e.next] | ((uint32_t)(e.delta + 16) << 16) | ((uint32_t)e.sym << 24);
+        }
+    return true;
+}
+
 extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, zs_dict **out)
 {
     zs::clear_error();
@@ -133,15 +269,26 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
         return ZS_ERR_BAD_DICT;
     }
 
-    // character classes: bytes that occur in some pattern, ascending
-    uint8_t cls[256] = {0};
-    int n_classes = 1;
+    // Character classes. The bytes that pre-processing and segmentation look at get fixed classes:
+    // digit d -> d, '%' -> 10, '[' -> 11, ']' -> 12, ' ' -> 13, '\t' -> 14, '\n' -> 15. Every other byte
+    // that occurs in some pattern gets its own class from 17 up (ascending byte order); all remaining
+    // bytes share class 16.
+    uint8_t cls[256];
+    int n_classes = zs::kClsFirstFree;
     {
         bool seen[256] = {false};
         for (auto &e : entries)
             for (unsigned char c : e.pat) seen[c] = true;
+        for (int b = 0; b < 256; ++b) cls[b] = zs::kClsOther;
+        for (int dg = 0; dg < 10; ++dg) cls['0' + dg] = (uint8_t)dg;
+        cls['%'] = zs::kClsPct;
+        cls['['] = zs::kClsLbr;
+        cls[']'] = zs::kClsRbr;
+        cls[' '] = zs::kClsSpace;
+        cls['\t'] = zs::kClsTab;
+        cls['\n'] = zs::kClsNl;
         for (int b = 0; b < 256; ++b)
-            if (seen[b]) cls[b] = (uint8_t)n_classes++;
+            if (seen[b] && cls[b] == zs::kClsOther) cls[b] = (uint8_t)n_classes++;
     }
 
     // trie of reversed patterns
@@ -263,6 +410,29 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
     }
     for (int u = 0; u < S; ++u) memcpy(img.data() + L.off_sym + 16 * u, sym[u].data(), 16);
 
+    // parse transducer image: replicated class table, pattern lengths, transition table
+    int Lp = 1;
+    for (auto &en : entries) Lp = std::max(Lp, (int)en.pat.size());
+    Machine mach;
+    const char *force_generic = getenv("ZS_FORCE_GENERIC");
+    const bool use_machine = !(force_generic && *force_generic && *force_generic != '0') &&
+                             build_machine(delta, mask, sym, n_classes, Lp, 1u << 20, zs::kMaxMachineBytes, &mach);
+    std::vector<uint8_t> mimg;
+    zs::MachineLayout ML{};
+    if (use_machine) {
+        ML.n_states = (uint32_t)mach.states;
+        ML.n_classes = (uint32_t)n_classes;
+        ML.start = (uint32_t)mach.start;
+        ML.off_table = zs::kMOffTable;
+        ML.img_bytes = zs::kMOffTable + (uint32_t)(mach.table.size() * 4);
+        ML.img_bytes = (ML.img_bytes + 15u) & ~15u;
+        mimg.assign(ML.img_bytes, 0);
+        for (int c = 0; c < 256; ++c)
+            for (int ln = 0; ln < 32; ++ln) mimg[zs::kMOffClsRep + ((c >> 2) * 32 + ln) * 4 + (c & 3)] = cls[c];
+        for (auto &en : entries) mimg[zs::kMOffPlen + en.sym] = (uint8_t)en.pat.size();
+        memcpy(mimg.data() + zs::kMOffTable, mach.table.data(), mach.table.size() * 4);
+    }
+
     std::vector<uint8_t> dec(zs::kDecBytes, 0);
     memcpy(dec.data(), plen, 256);
     memcpy(dec.data() + 256, pat, sizeof pat);
@@ -275,16 +445,23 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
     }
     d->lmax = lmax;
     d->layout = L;
+    d->mlayout = ML;
+    d->has_machine = use_machine;
     memcpy(d->plen, plen, 256);
     memcpy(d->pat, pat, sizeof pat);
     e = cudaMalloc((void **)&d->d_enc, L.img_bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d->d_dec, zs::kDecBytes);
     if (e == cudaSuccess) e = cudaMemcpy(d->d_enc, img.data(), L.img_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d->d_dec, dec.data(), zs::kDecBytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && use_machine) {
+        e = cudaMalloc((void **)&d->d_mimg, ML.img_bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(d->d_mimg, mimg.data(), ML.img_bytes, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (d->d_enc) cudaFree(d->d_enc);
         if (d->d_dec) cudaFree(d->d_dec);
+        if (d->d_mimg) cudaFree(d->d_mimg);
         delete d;
         return zs::cuda_fail(e, "uploading dictionary tables");
     }
@@ -301,6 +478,7 @@ extern "C" void zs_free_dictionary(zs_dict *d)
     d->pool.release_all();
     if (d->d_enc) cudaFree(d->d_enc);
     if (d->d_dec) cudaFree(d->d_dec);
+    if (d->d_mimg) cudaFree(d->d_mimg);
     if (cur >= 0) cudaSetDevice(cur);
     delete d;
 }

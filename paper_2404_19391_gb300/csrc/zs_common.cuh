@@ -49,6 +49,27 @@ struct EncLayout {
 
 constexpr uint32_t kOffCls = 0, kOffPlen = 256, kOffMasks = 512, kOffTrans = 640;
 
+// Fixed byte classes (the automaton's input alphabet): pre-processing and segmentation read these
+// directly from class-coded text. Interesting bytes for pre-processing have classes below kClsNl.
+constexpr uint8_t kClsPct = 10, kClsLbr = 11, kClsRbr = 12, kClsSpace = 13, kClsTab = 14, kClsNl = 15,
+                  kClsOther = 16, kClsFirstFree = 17;
+
+// Parse-transducer image (shared memory of the compress kernel):
+//   [0, 8192)          class of each byte, replicated for the 32 lanes: byte c of lane l is at
+//                      ((c >> 2) * 32 + l) * 4 + (c & 3), so a warp-wide lookup never conflicts on a bank
+//   [8192, 8448)       plen[256]: symbol -> pattern length
+//   [8448, ...)        table[states][classes] (u32): next state | (delta + 16) << 16 | symbol << 24
+struct MachineLayout {
+    uint32_t n_states;
+    uint32_t n_classes;
+    uint32_t start;
+    uint32_t off_table;
+    uint32_t img_bytes;
+    uint32_t _pad[3];
+};
+constexpr uint32_t kMOffClsRep = 0, kMOffPlen = 8192, kMOffTable = 8448;
+constexpr uint32_t kMaxMachineBytes = 64u * 1024u;  // transition table budget in shared memory
+
 // Decoder tables (global, staged per CTA): plen[256] then pat[256][16].
 constexpr uint32_t kDecBytes = 256 + 256 * kMaxPat;
 
@@ -131,7 +152,10 @@ struct zs_dict {
     int device = -1;
     int lmax = 0;
     zs::EncLayout layout{};
+    zs::MachineLayout mlayout{};
+    bool has_machine = false;
     uint8_t *d_enc = nullptr;  // encoder image (layout.img_bytes)
+    uint8_t *d_mimg = nullptr; // parse-transducer image (mlayout.img_bytes), if it fits
     uint8_t *d_dec = nullptr;  // decoder tables (kDecBytes)
     uint8_t plen[256];
     uint8_t pat[256][zs::kMaxPat];
@@ -180,13 +204,15 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+// Waits for the phase with the thread suspended in hardware for up to ~20 us (the suspend-time hint),
+// so a waiting warp does not take issue slots from the warps that are working.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
 {
     uint32_t ok;
     asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
+        : "r"(smem_u32(bar)), "r"(phase), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -344,6 +370,63 @@ __device__ __forceinline__ void lookback(TileState *tiles, uint64_t t, uint64_t 
         b += tiles[p].agg_b;
         --p;
         timed = false;
+    }
+    *ea = a;
+    *eb = b;
+}
+
+// Decoupled look-back by a whole warp: each round, lane j inspects tile t-1-j, so one round trip to L2
+// covers 32 predecessors. Sums aggregates from the nearest predecessor back to (and including) the
+// nearest one that has published its inclusive prefix. Called by all 32 lanes; every lane returns the
+// same sums. Waits are bounded (kStTimeout on expiry).
+__device__ __forceinline__ void lookback_warp(TileState *tiles, uint64_t t, uint64_t *ea, uint64_t *eb,
+                                              uint64_t limit_ns, uint32_t *status)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint64_t a = 0, b = 0;
+    int64_t top = (int64_t)t - 1;
+    uint64_t t0 = 0;
+    bool timed = false, gave_up = false;
+    while (top >= 0 && !gave_up) {
+        const int64_t p = top - (int64_t)lane;
+        uint32_t f = p >= 0 ? ld_acquire(&tiles[p].flag) : 2u;
+        while (__any_sync(0xffffffffu, f == 0)) {
+            if (*((volatile uint32_t *)status) & kStTimeout) {
+                gave_up = true;
+                break;
+            }
+            if (!timed) {
+                t0 = gtime();
+                timed = true;
+            } else if (gtime() - t0 > limit_ns) {
+                if (lane == 0) atomicOr(status, kStTimeout);
+                gave_up = true;
+                break;
+            }
+            __nanosleep(256);
+            if (f == 0) f = ld_acquire(&tiles[p].flag);
+        }
+        if (gave_up) break;
+        timed = false;
+        const uint32_t incl = __ballot_sync(0xffffffffu, f == 2u);
+        const int stop = incl ? __ffs(incl) - 1 : 32;  // nearest lane holding an inclusive prefix
+        uint64_t va = 0, vb = 0;
+        if ((int)lane < stop && p >= 0) {
+            va = tiles[p].agg_a;
+            vb = tiles[p].agg_b;
+        } else if ((int)lane == stop && p >= 0) {
+            va = tiles[p].inc_a;
+            vb = tiles[p].inc_b;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            va += __shfl_xor_sync(0xffffffffu, va, o);
+            vb += __shfl_xor_sync(0xffffffffu, vb, o);
+        }
+        a += va;
+        b += vb;
+        if (stop < 32) break;
+        top -= 32;
     }
     *ea = a;
     *eb = b;

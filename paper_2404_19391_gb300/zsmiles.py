@@ -53,7 +53,8 @@ def load_library(rebuild: bool = False) -> ctypes.CDLL:
     global _lib
     if _lib is not None and not rebuild:
         return _lib
-    path = _build.build() if (rebuild or not os.path.exists(_build.LIB)) else _build.LIB
+    path = os.environ.get("ZS_LIBRARY") or (_build.build() if (rebuild or not os.path.exists(_build.LIB))
+                                             else _build.LIB)
     lib = ctypes.CDLL(path)
     vp, sz, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64
     pres = ctypes.POINTER(_Result)
@@ -70,6 +71,7 @@ def load_library(rebuild: bool = False) -> ctypes.CDLL:
         "zs_last_error": (ctypes.c_char_p, []),
         "zs_version": (ctypes.c_char_p, []),
         "zs_last_kernel_ms": (ctypes.c_double, []),
+        "zs_dictionary_uses_transducer": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -141,6 +143,10 @@ class Dictionary:
             self.close()
         except Exception:
             pass
+
+    @property
+    def uses_transducer(self) -> bool:
+        return bool(_L().zs_dictionary_uses_transducer(self.handle))
 
     def decompress_bound(self, in_len: int) -> int:
         return int(_L().zs_decompress_bound(self.handle, in_len))

@@ -23,10 +23,19 @@ def zs():
     return zsmiles
 
 
-@pytest.fixture(scope="module")
-def dicts(zs):
+@pytest.fixture(scope="module", params=["transducer", "generic"])
+def dicts(zs, request):
+    """The default dictionary loaded twice: with its parse transducer (the normal path) and with the
+    transducer disabled, which runs the generic per-byte automaton kernel."""
     data = open(DICT_PATH, "rb").read()
-    return zs.Dictionary(data), oracle.Dict(data)
+    if request.param == "generic":
+        os.environ["ZS_FORCE_GENERIC"] = "1"
+    try:
+        d = zs.Dictionary(data)
+    finally:
+        os.environ.pop("ZS_FORCE_GENERIC", None)
+    assert d.uses_transducer == (request.param == "transducer")
+    return d, oracle.Dict(data)
 
 
 def dev(a):
