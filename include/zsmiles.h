@@ -170,13 +170,13 @@ zs_status zs_decompress_lines(const zs_dict *d, const uint8_t *d_comp, size_t co
  * allocator (a framework's caching allocator that already holds the free HBM, a fixed arena in an
  * embedded service), or they run latency-critical loops in which cudaMalloc, cudaFree or cudaMallocHost
  * would implicitly synchronise the device. This call decodes exactly like zs_decompress (same
- * arguments, same output, same errors) but allocates nothing: its scratch is a fixed 2 MiB array of
+ * arguments, same output, same errors) but allocates nothing: its scratch is a fixed 8 MiB array of
  * device memory compiled into the library, which every GPU that loads the library holds until the
  * process exits, and its result is copied straight into *res.
  *
- * Limit: the scratch holds 43,689 tile records of 8 KiB of compressed input each, so in_len may be at
- * most 357,900,288 bytes; a larger input returns ZS_ERR_INVALID_ARG without touching the device (use
- * zs_decompress instead).
+ * Limit: the scratch holds 174,761 tile records of 1,408 bytes of compressed input each, so in_len may be
+ * at most 246,063,488 bytes (zs_decompress_noalloc_limit() returns this figure); a larger input returns
+ * ZS_ERR_INVALID_ARG without touching the device (use zs_decompress instead).
  *
  * Set-up: the first call on each device (with that device current) looks up the array's device address
  * once; make that first call before any stream capture on the device.
@@ -186,6 +186,9 @@ zs_status zs_decompress_lines(const zs_dict *d, const uint8_t *d_comp, size_t co
  */
 zs_status zs_decompress_noalloc(const zs_dict *d, const uint8_t *d_in, size_t in_len, uint8_t *d_out,
                                 size_t out_cap, zs_result *res, void *stream);
+
+/* The largest in_len that zs_decompress_noalloc accepts, in bytes. Host-only; never fails. */
+size_t zs_decompress_noalloc_limit(void);
 
 /* Device time, in milliseconds, of the main kernel of the last successful zs_compress, zs_decompress,
  * zs_build_line_index or zs_decompress_lines on this thread, measured with CUDA events recorded on the

@@ -1,218 +1,11 @@
-// zs_decompress (Sec. IV-D2), zs_build_line_index and zs_decompress_lines (random access, Sec. I).
-//
-// Escapes without a sequential scan: a byte is a verbatim (escaped) byte exactly when the run of ' '
-// bytes just before it has odd length - each ' ' that is not itself escaped escapes the byte after it,
-// and a run always starts unescaped (the byte before a run is never an unescaped ' '). So every thread
-// can decode its own slice after counting the spaces in front of it.
+// zs_decompress entry point, zs_build_line_index and zs_decompress_lines (random access, Sec. I). The
+// decompression kernel itself is in decode_warp.cu.
 #include <algorithm>
 
 #include "zs_common.cuh"
 
 namespace zs {
 namespace {
-
-// ------------------------------------------------------------------------------------------------
-// Full-stream decompression: tiles of kDT compressed bytes, kPerT per thread, single pass with decoupled
-// look-back; the tile's output is assembled in a shared buffer aligned to the output's 16-byte grid and
-// written with coalesced 16-byte stores (direct stores when a tile expands past the buffer).
-// ------------------------------------------------------------------------------------------------
-constexpr int kDNT = 256;
-constexpr int kDT = 8192;
-constexpr int kPerT = kDT / kDNT;  // 32
-constexpr int kDOutCap = 40960;
-
-struct DecArgs {
-    const uint8_t *in;
-    uint64_t n;
-    uint8_t *out;
-    uint64_t out_cap;
-    uint32_t in_aligned;
-    uint64_t ntiles;
-    const uint8_t *dec;  // plen[256], pat[256][16]
-    DevResult *res;
-    TileState *tiles;
-    uint64_t limit_ns;
-    int64_t stall_tile;
-};
-
-constexpr int kDOffStage = 0;
-constexpr int kDOffOut = kDOffStage + kDT + 16;
-constexpr int kDOffDec = kDOffOut + kDOutCap + 32;
-constexpr int kDOffScan = kDOffDec + kDecBytes;
-constexpr int kDOffVars = kDOffScan + 16 * (kDNT / 32 + 1) + 16;
-constexpr int kDOffBar = kDOffVars + 64;
-constexpr int kDSmem = kDOffBar + 16;
-
-struct DVars {
-    uint64_t tile;
-    uint64_t E_a, E_b;
-    uint32_t carry;  // spaces immediately before the tile
-    uint32_t staged;
-    uint32_t so;
-    uint32_t pad;
-};
-
-__global__ void __launch_bounds__(kDNT) decompress_kernel(DecArgs A)
-{
-    extern __shared__ __align__(128) uint8_t smem[];
-    uint8_t *st = smem + kDOffStage;
-    uint8_t *ost = smem + kDOffOut;
-    uint8_t *dec = smem + kDOffDec;
-    uint64_t *scan = reinterpret_cast<uint64_t *>(smem + kDOffScan);
-    DVars *V = reinterpret_cast<DVars *>(smem + kDOffVars);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kDOffBar);
-    const int tid = threadIdx.x;
-    uint32_t *status = &A.res->status;
-    const uint8_t *plen = dec;
-    const uint8_t *pat = dec + 256;
-
-    if (tid == 0) mbar_init(bar, 1);
-    __syncthreads();
-    uint32_t phase = 0;
-    if (tid == 0) {
-        mbar_arrive_tx(bar, kDecBytes);
-        bulk_g2s(dec, A.dec, kDecBytes, bar);
-    }
-    if (!mbar_wait_bounded(bar, phase, A.limit_ns, status)) {
-        mbar_wait_bounded(bar, phase, A.limit_ns, status);
-        return;
-    }
-    phase ^= 1u;
-
-    for (;;) {
-        if (tid == 0) V->tile = atomicAdd(&A.res->tile_counter, 1ull);
-        __syncthreads();
-        const uint64_t t = V->tile;
-        if (t >= A.ntiles) break;
-        const uint64_t base = t * (uint64_t)kDT;
-        const uint32_t nown = (uint32_t)(min(A.n, base + kDT) - base);
-        const uint32_t nbulk = A.in_aligned ? (nown & ~15u) : 0u;
-        if (tid == 0) {
-            fence_proxy_async_smem();
-            mbar_arrive_tx(bar, nbulk);
-            if (nbulk) bulk_g2s(st, A.in + base, nbulk, bar);
-            uint32_t c = 0;
-            while (base > c && A.in[base - 1 - c] == kEsc) ++c;  // space run ending just before the tile
-            V->carry = c;
-        }
-        for (uint32_t j = nbulk + tid; j < nown; j += kDNT) st[j] = A.in[base + j];
-        if (!mbar_wait_bounded(bar, phase, A.limit_ns, status)) {
-            mbar_wait_bounded(bar, phase, A.limit_ns, status);
-            return;
-        }
-        phase ^= 1u;
-        __syncthreads();
-
-        // ---- sizes of this thread's slice ----
-        const uint32_t p0 = min(nown, (uint32_t)tid * kPerT);
-        const uint32_t p1 = min(nown, p0 + kPerT);
-        uint32_t run = 0;
-        {
-            int q = (int)p0 - 1;
-            while (q >= 0 && st[q] == kEsc) {
-                ++run;
-                --q;
-            }
-            if (q < 0) run += V->carry;
-        }
-        const bool lit0 = (run & 1u) != 0;
-        bool lit = lit0;
-        uint32_t outb = 0, nls = 0;
-        for (uint32_t p = p0; p < p1; ++p) {
-            const uint8_t b = st[p];
-            if (lit) {
-                if (b == kNl) {  // a line ending in an unpaired escape
-                    note_error_offset(A.res, base + p - 1);
-                    atomicOr(status, kStMalformed);
-                }
-                outb += 1;
-                nls += (b == kNl);
-                lit = false;
-            } else if (b == kEsc) {
-                lit = true;
-            } else if (b == kNl) {
-                outb += 1;
-                nls += 1;
-            } else {
-                const uint32_t l = plen[b];
-                if (l == 0) {
-                    note_error_offset(A.res, base + p);
-                    atomicOr(status, kStMalformed);
-                }
-                outb += l;
-            }
-        }
-        if (lit && p1 > p0 && base + p1 == A.n) {
-            note_error_offset(A.res, A.n - 1);
-            atomicOr(status, kStMalformed);
-        }
-
-        uint64_t xa, xb, ta, tb;
-        block_excl2_u64<kDNT>(outb, nls, scan, &xa, &xb, &ta, &tb);
-        if (tid == 0) {
-            const bool stall = (int64_t)t == A.stall_tile;
-            if (!stall) publish(&A.tiles[t], t == 0 ? 2u : 1u, ta, tb);
-            uint64_t ea = 0, eb = 0;
-            if (t > 0) lookback(A.tiles, t, &ea, &eb, A.limit_ns, status);
-            if (t > 0 && !stall) publish(&A.tiles[t], 2u, ea + ta, eb + tb);
-            V->E_a = ea;
-            V->E_b = eb;
-            V->so = (uint32_t)(((uint64_t)(uintptr_t)A.out + ea) & 15u);
-            V->staged = (ta + 32 <= (uint64_t)kDOutCap) ? 1u : 0u;
-            if (t == A.ntiles - 1) {
-                A.res->out_len = ea + ta;
-                A.res->n_lines = eb + tb + ((A.in[A.n - 1] != kNl) ? 1u : 0u);
-            }
-        }
-        __syncthreads();
-
-        // ---- emit ----
-        const uint64_t E_a = V->E_a;
-        const bool staged = V->staged != 0;
-        const uint32_t so = V->so;
-        uint64_t pos = xa;
-        lit = lit0;
-        for (uint32_t p = p0; p < p1; ++p) {
-            const uint8_t b = st[p];
-            if (!lit && b == kEsc) {
-                lit = true;
-                continue;
-            }
-            if (lit || b == kNl) {
-                lit = false;
-                if (staged) ost[so + pos] = b;
-                else if (E_a + pos < A.out_cap) A.out[E_a + pos] = b;
-                pos += 1;
-                continue;
-            }
-            const uint32_t l = plen[b];
-            const uint8_t *src = pat + 16u * b;
-            if (staged) {
-                uint8_t *d = ost + so + pos;
-                for (uint32_t k = 0; k < l; ++k) d[k] = src[k];
-            } else {
-                for (uint32_t k = 0; k < l; ++k)
-                    if (E_a + pos + k < A.out_cap) A.out[E_a + pos + k] = src[k];
-            }
-            pos += l;
-        }
-        __syncthreads();
-        if (staged) {
-            uint8_t *gdst = A.out + E_a - so;
-            const uint32_t nchunks = (uint32_t)((so + ta + 15) >> 4);
-            for (uint32_t c = tid; c < nchunks; c += kDNT) {
-                const uint32_t lo = c * 16u, hi = lo + 16u;
-                if (lo >= so && hi <= so + ta && E_a - so + hi <= A.out_cap) {
-                    *reinterpret_cast<uint4 *>(gdst + lo) = *reinterpret_cast<const uint4 *>(ost + lo);
-                } else {
-                    for (uint32_t k = lo; k < hi; ++k)
-                        if (k >= so && k < so + ta && E_a - so + k < A.out_cap) gdst[k] = ost[k];
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
 
 // ------------------------------------------------------------------------------------------------
 // Line index: newline ranks via warp-segmented 16-byte loads, block scan, decoupled look-back.
@@ -452,34 +245,12 @@ int blocks_per_sm(K kernel, int nt, int smem)
 
 }  // namespace
 
-uint64_t decompress_tiles(uint64_t n) { return (n + kDT - 1) / kDT; }
 uint64_t index_tiles(uint64_t n) { return (n + kIT - 1) / kIT; }
 uint64_t lines_tiles(uint64_t k) { return (k + kRNT - 1) / kRNT; }
 
+uint64_t decompress_tiles(uint64_t n);
 cudaError_t launch_decompress(const zs_dict *d, const uint8_t *in, uint64_t n, uint8_t *out, uint64_t out_cap,
-                              DevResult *res, TileState *tiles, cudaStream_t s)
-{
-    DecArgs a{};
-    a.in = in;
-    a.n = n;
-    a.out = out;
-    a.out_cap = out_cap;
-    a.in_aligned = (((uintptr_t)in) & 15u) == 0;
-    a.ntiles = decompress_tiles(n);
-    a.dec = d->d_dec;
-    a.res = res;
-    a.tiles = tiles;
-    a.limit_ns = wait_limit_ns();
-    a.stall_tile = injected_stall_tile();
-    static int per = -1;
-    if (per < 0) {
-        cudaFuncSetAttribute(decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDSmem);
-        per = blocks_per_sm(decompress_kernel, kDNT, kDSmem);
-    }
-    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.ntiles, (uint64_t)per * sm_count()));
-    decompress_kernel<<<(unsigned)grid, kDNT, kDSmem, s>>>(a);
-    return cudaGetLastError();
-}
+                              DevResult *res, TileState *tiles, cudaStream_t s);
 
 cudaError_t launch_line_index(const uint8_t *in, uint64_t n, uint64_t *index, uint64_t index_cap, DevResult *res,
                               TileState *tiles, cudaStream_t s)

@@ -8,7 +8,7 @@
 // fixed array compiled into the library, and copies the result into the caller's zs_result itself.
 // It calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating routine.
 //
-// The array is kNoAllocScratchBytes (2 MiB) of device memory that every GPU loading the library holds
+// The array is kNoAllocScratchBytes (8 MiB) of device memory that every GPU loading the library holds
 // until the process exits. Every call shares it; calls whose work overlaps on the GPU (from several
 // host threads or streams at once) race on it and must be serialised by the caller.
 #include <mutex>
@@ -20,10 +20,11 @@ namespace zs {
 cudaError_t launch_decompress(const zs_dict *d, const uint8_t *in, uint64_t n, uint8_t *out, uint64_t out_cap,
                               DevResult *res, TileState *tiles, cudaStream_t s);
 uint64_t decompress_tiles(uint64_t n);
+uint64_t decompress_tile_bytes();
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 2u << 20;
+constexpr size_t kNoAllocScratchBytes = 8u << 20;
 
 // The scratch itself. In host code this name is only a host-side stand-in for the device array, never
 // a device address: the kernel gets the address returned by cudaGetSymbolAddress below.
@@ -67,7 +68,7 @@ extern "C" zs_status zs_decompress_noalloc(const zs_dict *d, const uint8_t *d_in
     const uint64_t ntiles = zs::decompress_tiles(in_len);
     if (ntiles > max_tiles) {
         zs::set_error("zs_decompress_noalloc: input of " + std::to_string(in_len) + " bytes needs " +
-                      std::to_string(ntiles) + " tile records; the fixed 2 MiB scratch holds " +
+                      std::to_string(ntiles) + " tile records; the fixed 8 MiB scratch holds " +
                       std::to_string(max_tiles) + " (use zs_decompress for larger inputs)");
         return ZS_ERR_INVALID_ARG;
     }
@@ -109,4 +110,10 @@ extern "C" zs_status zs_decompress_noalloc(const zs_dict *d, const uint8_t *d_in
         return ZS_ERR_CAPACITY;
     }
     return ZS_OK;
+}
+
+extern "C" size_t zs_decompress_noalloc_limit(void)
+{
+    const uint64_t max_tiles = (zs::kNoAllocScratchBytes - sizeof(zs::DevResult)) / sizeof(zs::TileState);
+    return (size_t)(max_tiles * zs::decompress_tile_bytes());
 }

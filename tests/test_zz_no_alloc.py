@@ -15,7 +15,7 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-MAX_INPUT = 43689 * 8192
+MAX_INPUT = 174761 * 1408  # tile records in the 8 MiB scratch x compressed bytes per tile
 
 
 class _Result(ctypes.Structure):
@@ -32,6 +32,8 @@ def env():
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
                   ctypes.POINTER(_Result), ctypes.c_void_p]
+    lib.zs_decompress_noalloc_limit.restype = ctypes.c_size_t
+    assert lib.zs_decompress_noalloc_limit() == MAX_INPUT
     return zs, lib, zs.Dictionary()
 
 
