@@ -190,6 +190,72 @@ zs_status zs_decompress_noalloc(const zs_dict *d, const uint8_t *d_in, size_t in
 /* The largest in_len that zs_decompress_noalloc accepts, in bytes. Host-only; never fails. */
 size_t zs_decompress_noalloc_limit(void);
 
+/* ---- Batched form: many shards, one persistent launch, CUDA graph replay ---------------------------
+ *
+ * Library files are often split into many shards of very uneven sizes (the paper's method works line
+ * by line, Sec. IV, so shards are independent). These calls run the compression (or decompression) of
+ * a whole set of shards as ONE launch of the persistent kernel: the warps claim fixed-size tiles from a
+ * launch-wide numbering that runs through all shards, and each shard's output offsets come from its own
+ * look-back chain, so every shard gets exactly the bytes (and line index) that zs_compress /
+ * zs_decompress give it alone. The batching itself is not in the paper.
+ */
+
+/* One shard. Device pointers; the caller owns every buffer. For compression, in is the SMILES text,
+ * out receives the compressed stream (capacity zs_compress_bound(in_len) always suffices) and
+ * line_index (nullable, index_cap entries) the line index. For decompression, in is a compressed stream,
+ * out receives the decoded text (zs_decompress_bound), and line_index must be NULL with index_cap 0. */
+typedef struct zs_shard {
+    const uint8_t *in;
+    size_t in_len;
+    uint8_t *out;
+    size_t out_cap;
+    uint64_t *line_index;
+    size_t index_cap;
+} zs_shard;
+
+typedef enum { ZS_OP_COMPRESS = 0, ZS_OP_DECOMPRESS = 1 } zs_op;
+
+enum { ZS_MAX_SHARDS = 1 << 20 };
+
+/* Kernel variants: each operation is compiled for a few tile geometries (warps per SM x input bytes per
+ * warp tile; for compression this sets how many lines a warp holds at once). All give identical
+ * output; their speed depends on the line-length mix. */
+int zs_kernel_variants(zs_op op);                     /* number of compiled variants (0 for a bad op) */
+const char *zs_kernel_variant_name(zs_op op, int v);  /* static string, or NULL */
+
+/* One-shot batched calls: one launch of the default variant over all shards, then a wait. res: host
+ * array of n_shards results (out_len, n_lines and err_offset of each shard). Errors: as for
+ * zs_compress / zs_decompress; the first failing shard is named in zs_last_error(), and every shard's
+ * res entry is filled. A dictionary whose transducer does not fit in shared memory (see
+ * zs_dictionary_uses_transducer) cannot be used here: ZS_ERR_BAD_DICT. */
+zs_status zs_compress_batch(const zs_dict *d, const zs_shard *shards, size_t n_shards, unsigned flags,
+                            zs_result *res, void *stream);
+zs_status zs_decompress_batch(const zs_dict *d, const zs_shard *shards, size_t n_shards, zs_result *res,
+                              void *stream);
+
+/* Plans: a fixed set of shards run many times (new data in the same buffers). */
+typedef struct zs_plan zs_plan; /* opaque, library-owned */
+
+typedef struct zs_plan_options {
+    int variant;   /* -1: autotune (time every variant on this batch, keep the fastest); else a variant */
+    int use_graph; /* nonzero: capture clear + launch + result copy in a CUDA graph, replay it per run */
+    int tune_reps; /* timed runs per variant when autotuning (<= 0: 3) */
+} zs_plan_options;
+
+/* Makes a plan for `op` over the shards (host array, copied). opt may be NULL: autotune, with a graph.
+ * Autotuning RUNS the operation on the shards (writing their outputs) a few times per variant, on a
+ * private stream, and waits for it. Allocates the plan's device scratch (results, shard table, tile
+ * records, long-line work space) and pinned host memory. */
+zs_status zs_plan_create(const zs_dict *d, zs_op op, unsigned flags, const zs_shard *shards, size_t n_shards,
+                         const zs_plan_options *opt, zs_plan **out);
+/* Runs the plan on `stream` and waits for it; res (host, n_shards entries, nullable) as above. Calls on
+ * one plan must not overlap (the plan's scratch is reused). */
+zs_status zs_plan_run(zs_plan *p, zs_result *res, void *stream);
+int zs_plan_variant(const zs_plan *p);             /* the variant the plan runs */
+double zs_plan_tuned_ms(const zs_plan *p, int v);  /* median kernel ms of variant v when tuned, else -1 */
+double zs_plan_last_ms(const zs_plan *p);          /* kernel ms of the last run */
+void zs_plan_destroy(zs_plan *p);
+
 /* Device time, in milliseconds, of the main kernel of the last successful zs_compress, zs_decompress,
  * zs_build_line_index or zs_decompress_lines on this thread, measured with CUDA events recorded on the
  * call's stream just before and just after the kernel launch (no paper counterpart: instrumentation). */

@@ -751,22 +751,9 @@ cudaError_t launch_compress(const zs_dict *d, const uint8_t *in, uint64_t n, uns
 
 uint64_t compress_tiles(uint64_t n) { return (n + kTB - 1) / kTB; }
 
-uint64_t compress_warp_tiles(uint64_t n);
-size_t compress_warp_smem(const zs_dict *d);
-cudaError_t launch_compress_warp(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,
-                                 uint64_t out_cap, uint64_t *index, uint64_t index_cap, DevResult *res,
-                                 TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s);
-
 // The transducer kernel runs when the dictionary has a transducer and its tables fit in shared memory;
 // otherwise the generic kernel (automaton + window scan per byte) runs.
-bool use_transducer(const zs_dict *d)
-{
-    if (!d->has_machine) return false;
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return compress_warp_smem(d) <= (size_t)optin;
-}
+bool use_transducer(const zs_dict *d) { return compress_warp_fits(kDefaultVariant, d); }
 
 }  // namespace zs
 
@@ -776,16 +763,24 @@ namespace zs {
 
 uint64_t compress_scratch_tiles(const zs_dict *d, uint64_t n)
 {
-    return use_transducer(d) ? compress_warp_tiles(n) : compress_tiles(n);
+    return use_transducer(d) ? tiles_for(n, compress_warp_variant(kDefaultVariant)->tile_bytes) : compress_tiles(n);
 }
 
 cudaError_t launch_compress_any(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,
                                 uint64_t out_cap, uint64_t *index, uint64_t index_cap, DevResult *res,
                                 TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s)
 {
-    if (use_transducer(d))
-        return launch_compress_warp(d, in, n, flags, out, out_cap, index, index_cap, res, tiles, slow, slow_cap, s);
-    return launch_compress(d, in, n, flags, out, out_cap, index, index_cap, res, tiles, slow, slow_cap, s);
+    if (!use_transducer(d))
+        return launch_compress(d, in, n, flags, out, out_cap, index, index_cap, res, tiles, slow, slow_cap, s);
+    TiledLaunch L{};
+    L.one = single_shard(in, n, out, out_cap, index, index_cap, tiles, res,
+                         tiles_for(n, compress_warp_variant(kDefaultVariant)->tile_bytes));
+    L.n_shards = 1;
+    L.total_tiles = L.one.ntiles;
+    L.g = res;
+    L.slow = slow;
+    L.slow_cap = slow_cap;
+    return launch_compress_warp(kDefaultVariant, d, L, flags, s);
 }
 
 }  // namespace zs

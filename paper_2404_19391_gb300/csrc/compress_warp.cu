@@ -32,775 +32,845 @@ namespace zs {
 namespace {
 using namespace cx;
 
-#ifndef ZS_CW_WARPS
-#define ZS_CW_WARPS 8
-#endif
-constexpr int kMW = ZS_CW_WARPS;      // warps per CTA
-constexpr int kMNT = 32 * kMW;
-constexpr int kTW = 4096;             // owned bytes per warp tile
-constexpr int kHW = 1024;             // halo
-constexpr int kStW = 16 + kTW + kHW;  // staged bytes: the byte before the tile (index 15), tile, halo
-constexpr int kMaxLW = 192;           // lines per batch
-constexpr int kOutW = 2560;           // staged output bytes per tile
+// Tile geometry of one compiled variant of the kernel.
+template <int W, int TW, int HW, int MAXL, int OUTW>
+struct CwGeom {
+    static constexpr int kWarps = W;        // warps per CTA
+    static constexpr int kTile = TW;        // owned bytes per warp tile
+    static constexpr int kHalo = HW;        // bytes staged past the tile for the tile's last line
+    static constexpr int kMaxLines = MAXL;  // lines per batch
+    static constexpr int kOut = OUTW;       // staged output bytes per tile
+};
+
 constexpr int kTokMax = 32;           // ring labels per line on the fast path
 constexpr int kFastMax = 2047;        // longest line on the fast path (token positions use 11 bits)
 constexpr uint32_t kLongLine = 1u << 30;
 constexpr uint8_t kLfNl = 1, kLfSlow = 2;
 constexpr unsigned kFull = 0xffffffffu;
 
-struct alignas(16) Slot {
-    uint8_t st[kStW + 48];
-    uint16_t start[kMaxLW + 8];
-    uint16_t plen[kMaxLW];
-    uint32_t olen[kMaxLW];
-    uint32_t loff[kMaxLW];
-    uint32_t soff[kMaxLW];
-    uint8_t flag[kMaxLW];
-    uint8_t perm[kMaxLW];
-    uint64_t bar;
-    uint64_t btotal;
-    uint32_t Lt, first_start, last_end, last_nl, last_long, any_slow, nown, pad;
-};
-
-struct alignas(16) WarpMem {
-    Slot slot[2];
-    uint8_t ost[kOutW + 32];
-    uint16_t tok[kTokMax * 32];  // ring labels of the lane's line: entry k of lane l at [k * 32 + l]
-    uint16_t open2[16 * 32];     // open %nn labels (>= 10): slot j of lane l at [j * 32 + l] = label << 8 | token + 1
-    uint32_t hist[64];
-    uint16_t imask[(kStW + 31) / 16 + 2];  // per 16-byte chunk of the staged tile: bytes of class < kClsNl
-};
-
-struct MArgs {
-    const uint8_t *in;
-    uint64_t n;
-    uint8_t *out;
-    uint64_t out_cap;
-    uint64_t *index;
-    uint64_t index_cap;
+// Launch-wide arguments; the per-shard ones are in the ShardView of each claimed tile.
+struct CwArgs {
+    ShardView one;            // the shard when n_shards == 1
+    const ShardView *shards;  // device shard table when n_shards > 1 (tile0 ascending, shards[0].tile0 == 0)
+    uint32_t n_shards;
     uint32_t flags;
-    uint32_t in_aligned;
-    uint64_t ntiles;
+    uint64_t total_tiles;
     const uint8_t *mimg;
     uint32_t img_bytes;
     uint32_t n_classes;
     uint32_t start_state;
-    DevResult *res;
-    TileState *tiles;
+    uint32_t _pad;
+    DevResult *g;             // tile counter, status bits, long-line scratch use
     uint8_t *slow;
     uint64_t slow_cap;
     uint64_t limit_ns;
     int64_t stall_tile;
 };
 
-struct Ctx {
-    const MArgs *A;
-    WarpMem *M;
-    const uint8_t *clsrep;
-    const uint8_t *plen_tab;
-    const uint32_t *T;
-    uint32_t nc, q0, lane;
-    uint32_t *status;
-};
+template <class Geo>
+struct CW {
+    static constexpr int kMW = Geo::kWarps;
+    static constexpr int kMNT = 32 * kMW;
+    static constexpr int kTW = Geo::kTile;
+    static constexpr int kHW = Geo::kHalo;
+    static constexpr int kStW = 16 + kTW + kHW;  // staged bytes: the byte before the tile (index 15), tile, halo
+    static constexpr int kMaxLW = Geo::kMaxLines;
+    static constexpr int kOutW = Geo::kOut;
+    static_assert(kTW % 512 == 0 && kHW % 16 == 0 && kOutW % 16 == 0 && kMaxLW % 8 == 0 && kMaxLW <= 256,
+                  "tile geometry");
 
-__device__ __forceinline__ uint32_t cls_of(const uint8_t *clsrep, uint32_t c, uint32_t lane)
-{
-    return clsrep[((((c >> 2) << 5) + lane) << 2) | (c & 3u)];
-}
-
-// One transducer step (last byte first): returns the chosen symbol, updates state and cost.
-__device__ __forceinline__ uint32_t step(const uint32_t *T, uint32_t nc, uint32_t k, uint32_t &q, int32_t &cost)
-{
-    const uint32_t t = T[q * nc + k];
-    q = t & 0xFFFFu;
-    cost += (int32_t)((t >> 16) & 31u) - 16;
-    return t >> 24;
-}
-
-// Transducer walk over the class codes st[a, a+n) in place (last byte first); each code is replaced by
-// the symbol chosen at that byte. Whole 4-byte words where the word belongs to the line.
-__device__ __forceinline__ uint32_t parse_classes(uint8_t *st, uint32_t a, uint32_t n, const Ctx &C, bool *esc)
-{
-    uint32_t q = C.q0, e = 0;
-    int32_t cost = 0;
-    int32_t p = (int32_t)(a + n) - 1;
-    const int32_t lo = (int32_t)a;
-    while (p >= lo && ((p + 1) & 3) != 0) {
-        const uint32_t sy = step(C.T, C.nc, st[p], q, cost);
-        e |= (sy == kEsc);
-        st[p] = (uint8_t)sy;
-        --p;
-    }
-    while (p - 3 >= lo) {
-        const int32_t wp = p - 3;
-        const uint32_t w = *reinterpret_cast<const uint32_t *>(st + wp);
-        const uint32_t s3 = step(C.T, C.nc, w >> 24, q, cost);
-        const uint32_t s2 = step(C.T, C.nc, (w >> 16) & 255u, q, cost);
-        const uint32_t s1 = step(C.T, C.nc, (w >> 8) & 255u, q, cost);
-        const uint32_t s0 = step(C.T, C.nc, w & 255u, q, cost);
-        e |= (s3 == kEsc) | (s2 == kEsc) | (s1 == kEsc) | (s0 == kEsc);
-        *reinterpret_cast<uint32_t *>(st + wp) = s0 | (s1 << 8) | (s2 << 16) | (s3 << 24);
-        p -= 4;
-    }
-    while (p >= lo) {
-        const uint32_t sy = step(C.T, C.nc, st[p], q, cost);
-        e |= (sy == kEsc);
-        st[p] = (uint8_t)sy;
-        --p;
-    }
-    *esc = e != 0;
-    return (uint32_t)cost;
-}
-
-// The same walk over separate global arrays (slow path).
-__device__ uint32_t parse_global(const uint8_t *text, uint8_t *choice, uint32_t n, const Ctx &C)
-{
-    uint32_t q = C.q0;
-    int32_t cost = 0;
-    for (uint32_t i = n; i-- > 0;) choice[i] = (uint8_t)step(C.T, C.nc, cls_of(C.clsrep, text[i], C.lane), q, cost);
-    return (uint32_t)cost;
-}
-
-// Pre-processing of the class codes st[a, a+n) in place (Sec. IV-A), in one pass over the bytes flagged
-// in imask (digits, '%', brackets, space, tab). Rings are labelled in the order they close, each with
-// the smallest label that no ring closed since it opened still holds: lc[x] = position + 1 of the latest
-// close that took label x. A ring open under a label below 10 is found through dmap (5 bits of token
-// index per label, in registers); %nn labels of 10 and more through the small open2 table. New labels
-// are kept in the token entries and written only once the line is known to be valid.
-// Returns the new length, or -1 for the slow path (a label >= 10 needed, more than 32 ring labels or
-// more than 16 open %nn rings). *modified: some ring label was rewritten. An invalid line (unclosed ring
-// or bracket, bad %) is left as it is. tok, open2: this lane's columns (stride 32). Token entry: position
-// in the line (bits 0-10), %nn flag (bit 11), new label (bits 12-15).
-__device__ __forceinline__ int preprocess_classes(uint8_t *st, const uint16_t *imask, uint32_t a, uint32_t n,
-                                                  uint16_t *tok, uint16_t *open2, bool *modified)
-{
-    *modified = false;
-    if (n > (uint32_t)kFastMax) return -1;
-    if (n == 0) return 0;
-    const uint32_t end = a + n;
-    uint32_t lc[10];
-#pragma unroll
-    for (int x = 0; x < 10; ++x) lc[x] = 0;
-    uint64_t dmap = 0;
-    uint32_t dopen = 0, nopen2 = 0, ntok = 0, skipto = 0;
-    bool in_br = false, bad = false, any_pct = false, done = false, need_slow = false;
-    // one flat loop over the flagged bytes of the line (lanes of a warp then pay for the longest list of
-    // flagged bytes, not for the busiest chunk of each step)
-    const uint32_t clast = (end - 1) >> 4;
-    uint32_t c = a >> 4;
-    auto chunk_mask = [&](uint32_t cc) -> uint32_t {
-        const uint32_t cb = cc << 4;
-        uint32_t mm = imask[cc];
-        if (cb < a) mm &= 0xFFFFu << (a - cb);
-        if (cb + 16 > end) mm &= (1u << (end - cb)) - 1u;
-        return mm;
+    struct alignas(16) Slot {
+        uint8_t st[kStW + 48];
+        uint16_t start[kMaxLW + 8];
+        uint16_t plen[kMaxLW];
+        uint32_t olen[kMaxLW];
+        uint32_t loff[kMaxLW];
+        uint32_t soff[kMaxLW];
+        uint8_t flag[kMaxLW];
+        uint8_t perm[kMaxLW];
+        uint64_t bar;
+        uint64_t btotal;
+        uint32_t Lt, first_start, last_end, last_nl, last_long, any_slow, nown, pad;
+        ShardView sv;  // the shard of the staged tile
     };
-    uint32_t m = chunk_mask(c);
+
+    struct alignas(16) WarpMem {
+        Slot slot[2];
+        uint8_t ost[kOutW + 32];
+        uint16_t tok[kTokMax * 32];  // ring labels of the lane's line: entry k of lane l at [k * 32 + l]
+        uint16_t open2[16 * 32];     // open %nn labels (>= 10): slot j of lane l at [j * 32 + l] = label << 8 | token + 1
+        uint32_t hist[64];
+        uint16_t imask[(kStW + 31) / 16 + 2];  // per 16-byte chunk of the staged tile: bytes of class < kClsNl
+    };
+
+    struct Ctx {
+        const CwArgs *P;      // launch-wide arguments
+        const ShardView *A;   // shard of the tile being worked on
+        WarpMem *M;
+        const uint8_t *clsrep;
+        const uint8_t *plen_tab;
+        const uint32_t *T;
+        uint32_t nc, q0, lane;
+        uint32_t *status;
+    };
+
+    static __device__ __forceinline__ uint32_t cls_of(const uint8_t *clsrep, uint32_t c, uint32_t lane)
     {
-        for (;;) {
-            while (m == 0 && c < clast) m = chunk_mask(++c);
-            if (m == 0 || done) break;
-            const uint32_t p = (c << 4) + (uint32_t)(__ffs(m) - 1);
-            m &= m - 1;
-            const uint32_t k = st[p];
-            const bool live = p >= skipto;  // not one of the two digits of a %nn label
-            const bool ws = live & ((k == kClsSpace) | (k == kClsTab));
-            done = ws;  // the SMILES field ends at the first space or tab
-            const bool lb = live & !ws & !in_br & (k == kClsLbr);
-            const bool rb = live & in_br & (k == kClsRbr);
-            const bool ring = live & !in_br & (k <= kClsPct);  // a digit or a '%'
-            in_br = (in_br | lb) & !rb;
-            if (!ring) continue;
-            uint32_t label = k, pct = 0;
-            if (k == kClsPct) {  // %nn: two digits must follow inside the line
-                if (p + 2 >= end || st[p + 1] >= 10 || st[p + 2] >= 10) {
-                    bad = true;
-                    done = true;
-                    break;
-                }
-                label = st[p + 1] * 10u + st[p + 2];
-                pct = 1;
-                any_pct = true;
-                skipto = p + 3;
-            }
-            if (ntok == (uint32_t)kTokMax) {
-                need_slow = true;
-                done = true;
-                break;
-            }
-            const uint32_t me = ntok++;
-            tok[me * 32] = (uint16_t)((p - a) | (pct << 11));
-            int ko = -1;
-            if (label < 10) {
-                if ((dopen >> label) & 1u) {
-                    ko = (int)((dmap >> (5 * label)) & 31u);
-                    dopen &= ~(1u << label);
-                } else {
-                    dmap = (dmap & ~(31ull << (5 * label))) | ((uint64_t)me << (5 * label));
-                    dopen |= 1u << label;
-                }
-            } else {
-                int hit = -1, empty = -1;
-                for (int j = 0; j < 16; ++j) {
-                    const uint32_t v = open2[j * 32];
-                    if (v == 0) {
-                        if (empty < 0) empty = j;
-                    } else if ((v >> 8) == label) {
-                        hit = j;
+        return clsrep[((((c >> 2) << 5) + lane) << 2) | (c & 3u)];
+    }
+
+    // One transducer step (last byte first): returns the chosen symbol, updates state and cost.
+    static __device__ __forceinline__ uint32_t step(const uint32_t *T, uint32_t nc, uint32_t k, uint32_t &q, int32_t &cost)
+    {
+        const uint32_t t = T[q * nc + k];
+        q = t & 0xFFFFu;
+        cost += (int32_t)((t >> 16) & 31u) - 16;
+        return t >> 24;
+    }
+
+    // Transducer walk over the class codes st[a, a+n) in place (last byte first); each code is replaced by
+    // the symbol chosen at that byte. Whole 4-byte words where the word belongs to the line.
+    static __device__ __forceinline__ uint32_t parse_classes(uint8_t *st, uint32_t a, uint32_t n, const Ctx &C, bool *esc)
+    {
+        uint32_t q = C.q0, e = 0;
+        int32_t cost = 0;
+        int32_t p = (int32_t)(a + n) - 1;
+        const int32_t lo = (int32_t)a;
+        while (p >= lo && ((p + 1) & 3) != 0) {
+            const uint32_t sy = step(C.T, C.nc, st[p], q, cost);
+            e |= (sy == kEsc);
+            st[p] = (uint8_t)sy;
+            --p;
+        }
+        while (p - 3 >= lo) {
+            const int32_t wp = p - 3;
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(st + wp);
+            const uint32_t s3 = step(C.T, C.nc, w >> 24, q, cost);
+            const uint32_t s2 = step(C.T, C.nc, (w >> 16) & 255u, q, cost);
+            const uint32_t s1 = step(C.T, C.nc, (w >> 8) & 255u, q, cost);
+            const uint32_t s0 = step(C.T, C.nc, w & 255u, q, cost);
+            e |= (s3 == kEsc) | (s2 == kEsc) | (s1 == kEsc) | (s0 == kEsc);
+            *reinterpret_cast<uint32_t *>(st + wp) = s0 | (s1 << 8) | (s2 << 16) | (s3 << 24);
+            p -= 4;
+        }
+        while (p >= lo) {
+            const uint32_t sy = step(C.T, C.nc, st[p], q, cost);
+            e |= (sy == kEsc);
+            st[p] = (uint8_t)sy;
+            --p;
+        }
+        *esc = e != 0;
+        return (uint32_t)cost;
+    }
+
+    // The same walk over separate global arrays (slow path).
+    static __device__ uint32_t parse_global(const uint8_t *text, uint8_t *choice, uint32_t n, const Ctx &C)
+    {
+        uint32_t q = C.q0;
+        int32_t cost = 0;
+        for (uint32_t i = n; i-- > 0;) choice[i] = (uint8_t)step(C.T, C.nc, cls_of(C.clsrep, text[i], C.lane), q, cost);
+        return (uint32_t)cost;
+    }
+
+    // Pre-processing of the class codes st[a, a+n) in place (Sec. IV-A), in one pass over the bytes flagged
+    // in imask (digits, '%', brackets, space, tab). Rings are labelled in the order they close, each with
+    // the smallest label that no ring closed since it opened still holds: lc[x] = position + 1 of the latest
+    // close that took label x. A ring open under a label below 10 is found through dmap (5 bits of token
+    // index per label, in registers); %nn labels of 10 and more through the small open2 table. New labels
+    // are kept in the token entries and written only once the line is known to be valid.
+    // Returns the new length, or -1 for the slow path (a label >= 10 needed, more than 32 ring labels or
+    // more than 16 open %nn rings). *modified: some ring label was rewritten. An invalid line (unclosed ring
+    // or bracket, bad %) is left as it is. tok, open2: this lane's columns (stride 32). Token entry: position
+    // in the line (bits 0-10), %nn flag (bit 11), new label (bits 12-15).
+    static __device__ __forceinline__ int preprocess_classes(uint8_t *st, const uint16_t *imask, uint32_t a, uint32_t n,
+                                                      uint16_t *tok, uint16_t *open2, bool *modified)
+    {
+        *modified = false;
+        if (n > (uint32_t)kFastMax) return -1;
+        if (n == 0) return 0;
+        const uint32_t end = a + n;
+        uint32_t lc[10];
+    #pragma unroll
+        for (int x = 0; x < 10; ++x) lc[x] = 0;
+        uint64_t dmap = 0;
+        uint32_t dopen = 0, nopen2 = 0, ntok = 0, skipto = 0;
+        bool in_br = false, bad = false, any_pct = false, done = false, need_slow = false;
+        // one flat loop over the flagged bytes of the line (lanes of a warp then pay for the longest list of
+        // flagged bytes, not for the busiest chunk of each step)
+        const uint32_t clast = (end - 1) >> 4;
+        uint32_t c = a >> 4;
+        auto chunk_mask = [&](uint32_t cc) -> uint32_t {
+            const uint32_t cb = cc << 4;
+            uint32_t mm = imask[cc];
+            if (cb < a) mm &= 0xFFFFu << (a - cb);
+            if (cb + 16 > end) mm &= (1u << (end - cb)) - 1u;
+            return mm;
+        };
+        uint32_t m = chunk_mask(c);
+        {
+            for (;;) {
+                while (m == 0 && c < clast) m = chunk_mask(++c);
+                if (m == 0 || done) break;
+                const uint32_t p = (c << 4) + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1;
+                const uint32_t k = st[p];
+                const bool live = p >= skipto;  // not one of the two digits of a %nn label
+                const bool ws = live & ((k == kClsSpace) | (k == kClsTab));
+                done = ws;  // the SMILES field ends at the first space or tab
+                const bool lb = live & !ws & !in_br & (k == kClsLbr);
+                const bool rb = live & in_br & (k == kClsRbr);
+                const bool ring = live & !in_br & (k <= kClsPct);  // a digit or a '%'
+                in_br = (in_br | lb) & !rb;
+                if (!ring) continue;
+                uint32_t label = k, pct = 0;
+                if (k == kClsPct) {  // %nn: two digits must follow inside the line
+                    if (p + 2 >= end || st[p + 1] >= 10 || st[p + 2] >= 10) {
+                        bad = true;
+                        done = true;
+                        break;
                     }
+                    label = st[p + 1] * 10u + st[p + 2];
+                    pct = 1;
+                    any_pct = true;
+                    skipto = p + 3;
                 }
-                if (hit >= 0) {
-                    ko = (int)(open2[hit * 32] & 0xFFu) - 1;
-                    open2[hit * 32] = 0;
-                    --nopen2;
-                } else if (empty >= 0) {
-                    open2[empty * 32] = (uint16_t)((label << 8) | (me + 1));
-                    ++nopen2;
-                } else {
+                if (ntok == (uint32_t)kTokMax) {
                     need_slow = true;
                     done = true;
                     break;
                 }
+                const uint32_t me = ntok++;
+                tok[me * 32] = (uint16_t)((p - a) | (pct << 11));
+                int ko = -1;
+                if (label < 10) {
+                    if ((dopen >> label) & 1u) {
+                        ko = (int)((dmap >> (5 * label)) & 31u);
+                        dopen &= ~(1u << label);
+                    } else {
+                        dmap = (dmap & ~(31ull << (5 * label))) | ((uint64_t)me << (5 * label));
+                        dopen |= 1u << label;
+                    }
+                } else {
+                    int hit = -1, empty = -1;
+                    for (int j = 0; j < 16; ++j) {
+                        const uint32_t v = open2[j * 32];
+                        if (v == 0) {
+                            if (empty < 0) empty = j;
+                        } else if ((v >> 8) == label) {
+                            hit = j;
+                        }
+                    }
+                    if (hit >= 0) {
+                        ko = (int)(open2[hit * 32] & 0xFFu) - 1;
+                        open2[hit * 32] = 0;
+                        --nopen2;
+                    } else if (empty >= 0) {
+                        open2[empty * 32] = (uint16_t)((label << 8) | (me + 1));
+                        ++nopen2;
+                    } else {
+                        need_slow = true;
+                        done = true;
+                        break;
+                    }
+                }
+                if (ko < 0) continue;
+                const uint32_t eo = tok[ko * 32];
+                const uint32_t po = eo & 0x7FFu;
+                int nl = -1;
+    #pragma unroll
+                for (int x = 9; x >= 0; --x)
+                    if (lc[x] <= po + 1) nl = x;
+                if (nl < 0) {  // needs a two-digit label
+                    need_slow = true;
+                    done = true;
+                    break;
+                }
+    #pragma unroll
+                for (int x = 0; x < 10; ++x)
+                    if (x == nl) lc[x] = (p - a) + 1;
+                tok[ko * 32] = (uint16_t)(eo | ((uint32_t)nl << 12));
+                tok[me * 32] = (uint16_t)(tok[me * 32] | ((uint32_t)nl << 12));
             }
-            if (ko < 0) continue;
-            const uint32_t eo = tok[ko * 32];
-            const uint32_t po = eo & 0x7FFu;
-            int nl = -1;
-#pragma unroll
-            for (int x = 9; x >= 0; --x)
-                if (lc[x] <= po + 1) nl = x;
-            if (nl < 0) {  // needs a two-digit label
-                need_slow = true;
-                done = true;
-                break;
-            }
-#pragma unroll
-            for (int x = 0; x < 10; ++x)
-                if (x == nl) lc[x] = (p - a) + 1;
-            tok[ko * 32] = (uint16_t)(eo | ((uint32_t)nl << 12));
-            tok[me * 32] = (uint16_t)(tok[me * 32] | ((uint32_t)nl << 12));
         }
-    }
-    if (any_pct && nopen2 > 0)
-        for (int j = 0; j < 16; ++j) open2[j * 32] = 0;
-    if (need_slow) return -1;
-    if (bad || in_br || dopen != 0 || nopen2 != 0 || ntok == 0) return (int)n;  // left as it is
-    *modified = true;
-    if (!any_pct) {
+        if (any_pct && nopen2 > 0)
+            for (int j = 0; j < 16; ++j) open2[j * 32] = 0;
+        if (need_slow) return -1;
+        if (bad || in_br || dopen != 0 || nopen2 != 0 || ntok == 0) return (int)n;  // left as it is
+        *modified = true;
+        if (!any_pct) {
+            for (uint32_t k = 0; k < ntok; ++k) {
+                const uint32_t e = tok[k * 32];
+                st[a + (e & 0x7FFu)] = (uint8_t)(e >> 12);  // the class of digit d is d
+            }
+            return (int)n;
+        }
+        uint32_t w = 0, r = 0;
         for (uint32_t k = 0; k < ntok; ++k) {
             const uint32_t e = tok[k * 32];
-            st[a + (e & 0x7FFu)] = (uint8_t)(e >> 12);  // the class of digit d is d
+            const uint32_t p = e & 0x7FFu;
+            for (; r < p; ++r, ++w) st[a + w] = st[a + r];
+            st[a + w] = (uint8_t)(e >> 12);
+            ++w;
+            r = p + ((e & 0x800u) ? 3u : 1u);
         }
-        return (int)n;
+        for (; r < n; ++r, ++w) st[a + w] = st[a + r];
+        return (int)w;
     }
-    uint32_t w = 0, r = 0;
-    for (uint32_t k = 0; k < ntok; ++k) {
-        const uint32_t e = tok[k * 32];
-        const uint32_t p = e & 0x7FFu;
-        for (; r < p; ++r, ++w) st[a + w] = st[a + r];
-        st[a + w] = (uint8_t)(e >> 12);
-        ++w;
-        r = p + ((e & 0x800u) ? 3u : 1u);
-    }
-    for (; r < n; ++r, ++w) st[a + w] = st[a + r];
-    return (int)w;
-}
 
-// Replace the staged bytes by their classes (coalesced 16-byte chunks, lane-replicated table) and flag,
-// per chunk, the bytes pre-processing has to look at.
-__device__ __forceinline__ void to_classes(const Ctx &C, Slot &S, uint32_t stage_end)
-{
-    const uint32_t nchunks = (stage_end + 15) >> 4;
-    for (uint32_t c = C.lane; c < nchunks; c += 32) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(S.st + c * 16);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        uint32_t o[4], mask = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t b0 = cls_of(C.clsrep, w[i] & 255u, C.lane), b1 = cls_of(C.clsrep, (w[i] >> 8) & 255u, C.lane);
-            const uint32_t b2 = cls_of(C.clsrep, (w[i] >> 16) & 255u, C.lane), b3 = cls_of(C.clsrep, w[i] >> 24, C.lane);
-            o[i] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-            mask |= ((uint32_t)(b0 < kClsNl) | ((uint32_t)(b1 < kClsNl) << 1) | ((uint32_t)(b2 < kClsNl) << 2) |
-                     ((uint32_t)(b3 < kClsNl) << 3)) << (4 * i);
+    // Replace the staged bytes by their classes (coalesced 16-byte chunks, lane-replicated table) and flag,
+    // per chunk, the bytes pre-processing has to look at.
+    static __device__ __forceinline__ void to_classes(const Ctx &C, Slot &S, uint32_t stage_end)
+    {
+        const uint32_t nchunks = (stage_end + 15) >> 4;
+        for (uint32_t c = C.lane; c < nchunks; c += 32) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(S.st + c * 16);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            uint32_t o[4], mask = 0;
+    #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t b0 = cls_of(C.clsrep, w[i] & 255u, C.lane), b1 = cls_of(C.clsrep, (w[i] >> 8) & 255u, C.lane);
+                const uint32_t b2 = cls_of(C.clsrep, (w[i] >> 16) & 255u, C.lane), b3 = cls_of(C.clsrep, w[i] >> 24, C.lane);
+                o[i] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+                mask |= ((uint32_t)(b0 < kClsNl) | ((uint32_t)(b1 < kClsNl) << 1) | ((uint32_t)(b2 < kClsNl) << 2) |
+                         ((uint32_t)(b3 < kClsNl) << 3)) << (4 * i);
+            }
+            *reinterpret_cast<uint4 *>(S.st + c * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+            C.M->imask[c] = (uint16_t)mask;
         }
-        *reinterpret_cast<uint4 *>(S.st + c * 16) = make_uint4(o[0], o[1], o[2], o[3]);
-        C.M->imask[c] = (uint16_t)mask;
+        __syncwarp();
     }
-    __syncwarp();
-}
 
-__device__ __forceinline__ uint32_t nl_bits_masked(const uint8_t *st, uint32_t p0, uint32_t lim)
-{
-    if (p0 >= lim) return 0;
-    uint32_t bits = eq_bits16(*reinterpret_cast<const uint4 *>(st + p0), kClsNl * 0x01010101u);
-    if (p0 + 16 > lim) bits &= (1u << (lim - p0)) - 1u;
-    return bits;
-}
-
-__device__ __forceinline__ uint64_t tile_base(uint64_t t) { return t * (uint64_t)kTW; }
-
-// Issue the bulk copy of tile t into slot S (lane 0), plus the unaligned tail bytes (all lanes).
-__device__ __forceinline__ void stage_issue(const Ctx &C, Slot &S, uint64_t t)
-{
-    const MArgs &A = *C.A;
-    const uint64_t base = tile_base(t);
-    const uint64_t stage_hi = min(A.n, base + (uint64_t)kTW + kHW);
-    const uint64_t lo = base >= 16 ? base - 16 : 0;
-    const uint32_t j0 = (uint32_t)(lo + 16 - base);
-    const uint32_t nbytes = (uint32_t)(stage_hi - lo);
-    const uint32_t nbulk = A.in_aligned ? (nbytes & ~15u) : 0u;
-    __syncwarp();
-    if (C.lane == 0) {
-        fence_proxy_async_smem();
-        mbar_arrive_tx(&S.bar, nbulk);
-        if (nbulk) bulk_g2s(S.st + j0, A.in + lo, nbulk, &S.bar);
+    static __device__ __forceinline__ uint32_t nl_bits_masked(const uint8_t *st, uint32_t p0, uint32_t lim)
+    {
+        if (p0 >= lim) return 0;
+        uint32_t bits = eq_bits16(*reinterpret_cast<const uint4 *>(st + p0), kClsNl * 0x01010101u);
+        if (p0 + 16 > lim) bits &= (1u << (lim - p0)) - 1u;
+        return bits;
     }
-    for (uint32_t j = nbulk + C.lane; j < nbytes; j += 32) S.st[j0 + j] = A.in[lo + j];
-    if (t == 0 && C.lane == 0) S.st[15] = kNl;  // position 0 starts a line
-}
 
-// Segmentation of the staged tile: line count, first start, end of the last line.
-__device__ __forceinline__ void segment(const Ctx &C, Slot &S, uint64_t t)
-{
-    const MArgs &A = *C.A;
-    const uint64_t base = tile_base(t);
-    const uint32_t nown = (uint32_t)(min(A.n, base + kTW) - base);
-    const uint64_t stage_hi = min(A.n, base + (uint64_t)kTW + kHW);
-    const uint32_t stage_end = (uint32_t)(stage_hi - base) + 16u;
-    to_classes(C, S, stage_end);
-    const uint8_t *st = S.st;
-    const uint32_t lim = 15u + nown;
-    const uint32_t first_start = (st[15] == kClsNl && nown > 0) ? 1u : 0u;
-    uint32_t Lt = first_start;
-#pragma unroll
-    for (int it = 0; it < kTW / 512; ++it)
-        Lt += __reduce_add_sync(kFull, __popc(nl_bits_masked(st, 16u + it * 512u + C.lane * 16u, lim)));
-    uint32_t last_end = 0, last_nl = 0, last_long = 0;
-    if (Lt > 0) {
-        uint32_t end = 0xFFFFFFFFu;
-        if (st[15 + nown] == kClsNl) {
-            end = 15 + nown;
-        } else {
-            for (uint32_t off = 16 + nown; off < stage_end && end == 0xFFFFFFFFu; off += 512) {
-                const uint32_t p0 = off + C.lane * 16u;
-                uint32_t bits = 0;
-                if (p0 < stage_end) {
-                    if (p0 + 16 <= stage_end && (p0 & 15u) == 0) {
-                        bits = eq_bits16(*reinterpret_cast<const uint4 *>(st + p0), kClsNl * 0x01010101u);
-                    } else {
-                        for (uint32_t q = 0; q < 16 && p0 + q < stage_end; ++q)
-                            if (st[p0 + q] == kClsNl) bits |= 1u << q;
+    static __device__ __forceinline__ uint64_t tile_base(uint64_t t) { return t * (uint64_t)kTW; }
+
+    // Issue the bulk copy of tile t into slot S (lane 0), plus the unaligned tail bytes (all lanes).
+    static __device__ __forceinline__ void stage_issue(const Ctx &C, Slot &S, uint64_t t)
+    {
+        const ShardView &A = *C.A;
+        const uint64_t base = tile_base(t);
+        const uint64_t stage_hi = min(A.n, base + (uint64_t)kTW + kHW);
+        const uint64_t lo = base >= 16 ? base - 16 : 0;
+        const uint32_t j0 = (uint32_t)(lo + 16 - base);
+        const uint32_t nbytes = (uint32_t)(stage_hi - lo);
+        const uint32_t nbulk = A.in_aligned ? (nbytes & ~15u) : 0u;
+        __syncwarp();
+        if (C.lane == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_tx(&S.bar, nbulk);
+            if (nbulk) bulk_g2s(S.st + j0, A.in + lo, nbulk, &S.bar);
+        }
+        for (uint32_t j = nbulk + C.lane; j < nbytes; j += 32) S.st[j0 + j] = A.in[lo + j];
+        if (t == 0 && C.lane == 0) S.st[15] = kNl;  // position 0 starts a line
+    }
+
+    // Segmentation of the staged tile: line count, first start, end of the last line.
+    static __device__ __forceinline__ void segment(const Ctx &C, Slot &S, uint64_t t)
+    {
+        const ShardView &A = *C.A;
+        const uint64_t base = tile_base(t);
+        const uint32_t nown = (uint32_t)(min(A.n, base + kTW) - base);
+        const uint64_t stage_hi = min(A.n, base + (uint64_t)kTW + kHW);
+        const uint32_t stage_end = (uint32_t)(stage_hi - base) + 16u;
+        to_classes(C, S, stage_end);
+        const uint8_t *st = S.st;
+        const uint32_t lim = 15u + nown;
+        const uint32_t first_start = (st[15] == kClsNl && nown > 0) ? 1u : 0u;
+        uint32_t Lt = first_start;
+    #pragma unroll
+        for (int it = 0; it < kTW / 512; ++it)
+            Lt += __reduce_add_sync(kFull, __popc(nl_bits_masked(st, 16u + it * 512u + C.lane * 16u, lim)));
+        uint32_t last_end = 0, last_nl = 0, last_long = 0;
+        if (Lt > 0) {
+            uint32_t end = 0xFFFFFFFFu;
+            if (st[15 + nown] == kClsNl) {
+                end = 15 + nown;
+            } else {
+                for (uint32_t off = 16 + nown; off < stage_end && end == 0xFFFFFFFFu; off += 512) {
+                    const uint32_t p0 = off + C.lane * 16u;
+                    uint32_t bits = 0;
+                    if (p0 < stage_end) {
+                        if (p0 + 16 <= stage_end && (p0 & 15u) == 0) {
+                            bits = eq_bits16(*reinterpret_cast<const uint4 *>(st + p0), kClsNl * 0x01010101u);
+                        } else {
+                            for (uint32_t q = 0; q < 16 && p0 + q < stage_end; ++q)
+                                if (st[p0 + q] == kClsNl) bits |= 1u << q;
+                        }
                     }
+                    const uint32_t cand = bits ? p0 + (uint32_t)(__ffs(bits) - 1) : 0xFFFFFFFFu;
+                    end = __reduce_min_sync(kFull, cand);
                 }
-                const uint32_t cand = bits ? p0 + (uint32_t)(__ffs(bits) - 1) : 0xFFFFFFFFu;
-                end = __reduce_min_sync(kFull, cand);
+            }
+            if (end != 0xFFFFFFFFu) {
+                last_end = end;
+                last_nl = 1;
+            } else if (stage_hi == A.n) {
+                last_end = stage_end;
+            } else {
+                last_long = 1;
             }
         }
-        if (end != 0xFFFFFFFFu) {
-            last_end = end;
-            last_nl = 1;
-        } else if (stage_hi == A.n) {
-            last_end = stage_end;
-        } else {
-            last_long = 1;
+        if (C.lane == 0) {
+            S.Lt = Lt;
+            S.first_start = first_start;
+            S.last_end = last_end;
+            S.last_nl = last_nl;
+            S.last_long = last_long;
+            S.nown = nown;
         }
+        __syncwarp();
     }
-    if (C.lane == 0) {
-        S.Lt = Lt;
-        S.first_start = first_start;
-        S.last_end = last_end;
-        S.last_nl = last_nl;
-        S.last_long = last_long;
-        S.nown = nown;
-    }
-    __syncwarp();
-}
 
-// Lines [r0, r1) of the staged tile: starts, extents, length sort, encode, output offsets.
-// Returns the batch's output bytes; *any_slow reports slow-path lines.
-__device__ uint64_t prepare_batch(const Ctx &C, Slot &S, uint64_t t, uint32_t r0, uint32_t r1, bool *any_slow)
-{
-    const MArgs &A = *C.A;
-    WarpMem &M = *C.M;
-    const uint32_t lane = C.lane;
-    uint8_t *st = S.st;
-    const uint32_t nb = r1 - r0, Lt = S.Lt, first_start = S.first_start;
-    const uint32_t lim = 15u + S.nown;
-    const uint64_t base = tile_base(t);
-
-    if (lane == 0 && first_start && r0 == 0) S.start[0] = 16;
+    // Lines [r0, r1) of the staged tile: starts, extents, length sort, encode, output offsets.
+    // Returns the batch's output bytes; *any_slow reports slow-path lines.
+    static __device__ uint64_t prepare_batch(const Ctx &C, Slot &S, uint64_t t, uint32_t r0, uint32_t r1, bool *any_slow)
     {
-        uint32_t rank = first_start;
-#pragma unroll 1
-        for (int it = 0; it < kTW / 512; ++it) {
-            const uint32_t p0 = 16u + it * 512u + lane * 16u;
-            uint32_t bits = nl_bits_masked(st, p0, lim);
-            const uint32_t c = __popc(bits);
-            const uint32_t inc = warp_incl_u32(c);
-            uint32_t rk = rank + inc - c;
-            while (bits) {
-                const int q = __ffs(bits) - 1;
-                bits &= bits - 1;
-                if (rk >= r0 && rk <= r1) S.start[rk - r0] = (uint16_t)(p0 + (uint32_t)q + 1u);
-                ++rk;
-            }
-            rank += __shfl_sync(kFull, inc, 31);
-        }
-    }
-    M.hist[lane] = 0;
-    M.hist[lane + 32] = 0;
-    __syncwarp();
-    for (uint32_t r = lane; r < nb; r += 32) {
-        const uint32_t s = S.start[r];
-        uint32_t end;
-        uint8_t fl;
-        if (r0 + r + 1 < Lt) {
-            end = (uint32_t)S.start[r + 1] - 1u;
-            fl = kLfNl;
-        } else if (S.last_long) {
-            end = s;  // found by the slow path
-            fl = kLfSlow;
-        } else {
-            end = S.last_end;
-            fl = S.last_nl ? kLfNl : 0;
-        }
-        const uint32_t len = end - s;
-        S.plen[r] = (uint16_t)min(len, 65535u);
-        S.flag[r] = fl;
-        const uint32_t bucket = 63u - min(len >> 3, 63u);
-        S.olen[r] = bucket;
-        S.loff[r] = atomicAdd(&M.hist[bucket], 1u);
-    }
-    __syncwarp();
-    {
-        const uint32_t h0 = M.hist[2 * lane], h1 = M.hist[2 * lane + 1];
-        const uint32_t ex = warp_incl_u32(h0 + h1) - (h0 + h1);
-        M.hist[2 * lane] = ex;
-        M.hist[2 * lane + 1] = ex + h0;
-    }
-    __syncwarp();
-    for (uint32_t r = lane; r < nb; r += 32) S.perm[M.hist[S.olen[r]] + S.loff[r]] = (uint8_t)r;
-    __syncwarp();
+        const ShardView &A = *C.A;
+        WarpMem &M = *C.M;
+        const uint32_t lane = C.lane;
+        uint8_t *st = S.st;
+        const uint32_t nb = r1 - r0, Lt = S.Lt, first_start = S.first_start;
+        const uint32_t lim = 15u + S.nown;
+        const uint64_t base = tile_base(t);
 
-    bool lane_slow = false;
-    for (uint32_t qd = lane; qd < nb; qd += 32) {
-        const uint32_t r = S.perm[qd];
-        const uint32_t a = S.start[r];
-        uint8_t fl = S.flag[r];
-        uint32_t n = S.plen[r];
-        uint32_t cost = 0;
-        bool slow = (fl & kLfSlow) != 0;
-        if (!slow) {
-            bool modified = false;
-            int m = (int)n;
-            if (A.flags & ZS_PREPROCESS) m = preprocess_classes(st, M.imask, a, n, M.tok + lane, M.open2 + lane, &modified);
-            if (m < 0) {
-                slow = true;
-            } else {
-                bool esc = false;
-                cost = parse_classes(st, a, (uint32_t)m, C, &esc);
-                if (esc && modified) slow = true;  // escapes are emitted from the input bytes
-                n = (uint32_t)m;
+        if (lane == 0 && first_start && r0 == 0) S.start[0] = 16;
+        {
+            uint32_t rank = first_start;
+    #pragma unroll 1
+            for (int it = 0; it < kTW / 512; ++it) {
+                const uint32_t p0 = 16u + it * 512u + lane * 16u;
+                uint32_t bits = nl_bits_masked(st, p0, lim);
+                const uint32_t c = __popc(bits);
+                const uint32_t inc = warp_incl_u32(c);
+                uint32_t rk = rank + inc - c;
+                while (bits) {
+                    const int q = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (rk >= r0 && rk <= r1) S.start[rk - r0] = (uint16_t)(p0 + (uint32_t)q + 1u);
+                    ++rk;
+                }
+                rank += __shfl_sync(kFull, inc, 31);
             }
         }
-        if (slow) {
-            const uint64_t gs = base - 16 + a;
-            uint64_t glen;
-            if (fl & kLfSlow) {
-                uint64_t ge = gs;
-                while (ge < A.n && A.in[ge] != kNl) ++ge;
-                if (ge < A.n) fl |= kLfNl;
-                glen = ge - gs;
+        M.hist[lane] = 0;
+        M.hist[lane + 32] = 0;
+        __syncwarp();
+        for (uint32_t r = lane; r < nb; r += 32) {
+            const uint32_t s = S.start[r];
+            uint32_t end;
+            uint8_t fl;
+            if (r0 + r + 1 < Lt) {
+                end = (uint32_t)S.start[r + 1] - 1u;
+                fl = kLfNl;
+            } else if (S.last_long) {
+                end = s;  // found by the slow path
+                fl = kLfSlow;
             } else {
-                glen = S.plen[r];
+                end = S.last_end;
+                fl = S.last_nl ? kLfNl : 0;
             }
-            cost = 0;
-            n = 0;
-            S.soff[r] = 0xFFFFFFFFu;
-            if (glen >= kLongLine) {
-                atomicOr(C.status, kStTooBig);
-            } else {
-                const SlowLayout sl = slow_layout((uint32_t)glen);
-                const unsigned long long off = atomicAdd(&A.res->slow_used, (unsigned long long)sl.need);
-                if (off + sl.need > A.slow_cap) {
-                    atomicOr(C.status, kStSlowOverflow);
+            const uint32_t len = end - s;
+            S.plen[r] = (uint16_t)min(len, 65535u);
+            S.flag[r] = fl;
+            const uint32_t bucket = 63u - min(len >> 3, 63u);
+            S.olen[r] = bucket;
+            S.loff[r] = atomicAdd(&M.hist[bucket], 1u);
+        }
+        __syncwarp();
+        {
+            const uint32_t h0 = M.hist[2 * lane], h1 = M.hist[2 * lane + 1];
+            const uint32_t ex = warp_incl_u32(h0 + h1) - (h0 + h1);
+            M.hist[2 * lane] = ex;
+            M.hist[2 * lane + 1] = ex + h0;
+        }
+        __syncwarp();
+        for (uint32_t r = lane; r < nb; r += 32) S.perm[M.hist[S.olen[r]] + S.loff[r]] = (uint8_t)r;
+        __syncwarp();
+
+        bool lane_slow = false;
+        for (uint32_t qd = lane; qd < nb; qd += 32) {
+            const uint32_t r = S.perm[qd];
+            const uint32_t a = S.start[r];
+            uint8_t fl = S.flag[r];
+            uint32_t n = S.plen[r];
+            uint32_t cost = 0;
+            bool slow = (fl & kLfSlow) != 0;
+            if (!slow) {
+                bool modified = false;
+                int m = (int)n;
+                if (C.P->flags & ZS_PREPROCESS) m = preprocess_classes(st, M.imask, a, n, M.tok + lane, M.open2 + lane, &modified);
+                if (m < 0) {
+                    slow = true;
                 } else {
-                    uint8_t *ws = A.slow + off;
-                    uint32_t m;
-                    if (A.flags & ZS_PREPROCESS) {
-                        m = preprocess_slow(A.in + gs, (uint32_t)glen, ws + sl.text, ws + sl.tok,
-                                            reinterpret_cast<int32_t *>(ws + sl.tables),
-                                            reinterpret_cast<int32_t *>(ws + sl.tables) + 100);
-                    } else {
-                        for (uint32_t i = 0; i < glen; ++i) ws[sl.text + i] = A.in[gs + i];
-                        m = (uint32_t)glen;
-                    }
-                    cost = parse_global(ws + sl.text, ws + sl.chs, m, C);
-                    reinterpret_cast<uint32_t *>(ws)[0] = (uint32_t)glen;
-                    reinterpret_cast<uint32_t *>(ws)[1] = m;
-                    S.soff[r] = (uint32_t)(off >> 4);
+                    bool esc = false;
+                    cost = parse_classes(st, a, (uint32_t)m, C, &esc);
+                    if (esc && modified) slow = true;  // escapes are emitted from the input bytes
+                    n = (uint32_t)m;
                 }
             }
-            fl |= kLfSlow;
-            lane_slow = true;
+            if (slow) {
+                const uint64_t gs = base - 16 + a;
+                uint64_t glen;
+                if (fl & kLfSlow) {
+                    uint64_t ge = gs;
+                    while (ge < A.n && A.in[ge] != kNl) ++ge;
+                    if (ge < A.n) fl |= kLfNl;
+                    glen = ge - gs;
+                } else {
+                    glen = S.plen[r];
+                }
+                cost = 0;
+                n = 0;
+                S.soff[r] = 0xFFFFFFFFu;
+                if (glen >= kLongLine) {
+                    atomicOr(C.status, kStTooBig);
+                } else {
+                    const SlowLayout sl = slow_layout((uint32_t)glen);
+                    const unsigned long long off = atomicAdd(&C.P->g->slow_used, (unsigned long long)sl.need);
+                    if (off + sl.need > C.P->slow_cap) {
+                        atomicOr(C.status, kStSlowOverflow);
+                    } else {
+                        uint8_t *ws = C.P->slow + off;
+                        uint32_t m;
+                        if (C.P->flags & ZS_PREPROCESS) {
+                            m = preprocess_slow(A.in + gs, (uint32_t)glen, ws + sl.text, ws + sl.tok,
+                                                reinterpret_cast<int32_t *>(ws + sl.tables),
+                                                reinterpret_cast<int32_t *>(ws + sl.tables) + 100);
+                        } else {
+                            for (uint32_t i = 0; i < glen; ++i) ws[sl.text + i] = A.in[gs + i];
+                            m = (uint32_t)glen;
+                        }
+                        cost = parse_global(ws + sl.text, ws + sl.chs, m, C);
+                        reinterpret_cast<uint32_t *>(ws)[0] = (uint32_t)glen;
+                        reinterpret_cast<uint32_t *>(ws)[1] = m;
+                        S.soff[r] = (uint32_t)(off >> 4);
+                    }
+                }
+                fl |= kLfSlow;
+                lane_slow = true;
+            }
+            S.flag[r] = fl;
+            S.plen[r] = (uint16_t)min(n, 65535u);
+            S.olen[r] = cost + ((fl & kLfNl) ? 1u : 0u);
         }
-        S.flag[r] = fl;
-        S.plen[r] = (uint16_t)min(n, 65535u);
-        S.olen[r] = cost + ((fl & kLfNl) ? 1u : 0u);
-    }
-    *any_slow = __any_sync(kFull, lane_slow);
-    __syncwarp();
+        *any_slow = __any_sync(kFull, lane_slow);
+        __syncwarp();
 
-    const uint32_t per = (nb + 31) / 32;
-    uint64_t local = 0;
-    for (uint32_t k = 0; k < per; ++k) {
-        const uint32_t r = lane * per + k;
-        if (r < nb) local += S.olen[r];
-    }
-    uint64_t inc = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(kFull, inc, o);
-        if (lane >= (uint32_t)o) inc += u;
-    }
-    const uint64_t btotal = __shfl_sync(kFull, inc, 31);
-    {
-        uint64_t acc = inc - local;
+        const uint32_t per = (nb + 31) / 32;
+        uint64_t local = 0;
         for (uint32_t k = 0; k < per; ++k) {
             const uint32_t r = lane * per + k;
-            if (r < nb) {
-                S.loff[r] = (uint32_t)acc;
-                acc += S.olen[r];
+            if (r < nb) local += S.olen[r];
+        }
+        uint64_t inc = local;
+    #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t u = __shfl_up_sync(kFull, inc, o);
+            if (lane >= (uint32_t)o) inc += u;
+        }
+        const uint64_t btotal = __shfl_sync(kFull, inc, 31);
+        {
+            uint64_t acc = inc - local;
+            for (uint32_t k = 0; k < per; ++k) {
+                const uint32_t r = lane * per + k;
+                if (r < nb) {
+                    S.loff[r] = (uint32_t)acc;
+                    acc += S.olen[r];
+                }
             }
         }
+        if (lane == 0 && btotal >= 0xFFFFFFFFull) atomicOr(C.status, kStTooBig);
+        __syncwarp();
+        return btotal;
     }
-    if (lane == 0 && btotal >= 0xFFFFFFFFull) atomicOr(C.status, kStTooBig);
-    __syncwarp();
-    return btotal;
-}
 
-// Emit lines [0, nb) of slot S at output offset out_at (lines numbered from line0).
-__device__ void emit_batch(const Ctx &C, Slot &S, uint64_t t, uint32_t nb, uint64_t out_at, uint64_t line0,
-                           uint64_t btotal, bool staged)
-{
-    const MArgs &A = *C.A;
-    WarpMem &M = *C.M;
-    const uint32_t lane = C.lane;
-    const uint8_t *gbase = A.in + tile_base(t) - 16;
-    const uint32_t so = (uint32_t)(((uint64_t)(uintptr_t)A.out + out_at) & 15u);
-    for (uint32_t qd = lane; qd < nb; qd += 32) {
-        const uint32_t r = S.perm[qd];
-        const uint32_t a = S.start[r];
-        const uint8_t fl = S.flag[r];
-        const uint32_t loff = S.loff[r];
-        if (A.index && line0 + r < A.index_cap) A.index[line0 + r] = out_at + loff;
-        if (fl & kLfSlow) {
-            if (S.soff[r] == 0xFFFFFFFFu) continue;
-            uint8_t *ws = A.slow + ((uint64_t)S.soff[r] << 4);
-            const uint32_t glen = reinterpret_cast<const uint32_t *>(ws)[0];
-            const uint32_t m = reinterpret_cast<const uint32_t *>(ws)[1];
-            const SlowLayout sl = slow_layout(glen);
-            GlobalSink sink{A.out, out_at + loff, A.out_cap};
-            emit_line(ws + sl.chs, ws + sl.text, m, C.plen_tab, sink);
-            if (fl & kLfNl) sink.put(kNl);
-        } else if (staged) {
-            SmemSink sink{M.ost + so + loff};
-            emit_line(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
-            if (fl & kLfNl) sink.put(kNl);
-        } else {
-            GlobalSink sink{A.out, out_at + loff, A.out_cap};
-            emit_line(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
-            if (fl & kLfNl) sink.put(kNl);
-        }
-    }
-    __syncwarp();
-    if (staged) {
-        uint8_t *gdst = A.out + out_at - so;  // 16-byte aligned
-        const uint32_t nchunks = (uint32_t)((so + btotal + 15) >> 4);
-        for (uint32_t c = lane; c < nchunks; c += 32) {
-            const uint32_t lo_b = c * 16u, hi_b = lo_b + 16u;
-            if (lo_b >= so && hi_b <= so + btotal && out_at - so + hi_b <= A.out_cap) {
-                *reinterpret_cast<uint4 *>(gdst + lo_b) = *reinterpret_cast<const uint4 *>(M.ost + lo_b);
+    // Emit lines [0, nb) of slot S at output offset out_at (lines numbered from line0).
+    static __device__ void emit_batch(const Ctx &C, Slot &S, uint64_t t, uint32_t nb, uint64_t out_at, uint64_t line0,
+                               uint64_t btotal, bool staged)
+    {
+        const ShardView &A = *C.A;
+        WarpMem &M = *C.M;
+        const uint32_t lane = C.lane;
+        const uint8_t *gbase = A.in + tile_base(t) - 16;
+        const uint32_t so = (uint32_t)(((uint64_t)(uintptr_t)A.out + out_at) & 15u);
+        for (uint32_t qd = lane; qd < nb; qd += 32) {
+            const uint32_t r = S.perm[qd];
+            const uint32_t a = S.start[r];
+            const uint8_t fl = S.flag[r];
+            const uint32_t loff = S.loff[r];
+            if (A.index && line0 + r < A.index_cap) A.index[line0 + r] = out_at + loff;
+            if (fl & kLfSlow) {
+                if (S.soff[r] == 0xFFFFFFFFu) continue;
+                uint8_t *ws = C.P->slow + ((uint64_t)S.soff[r] << 4);
+                const uint32_t glen = reinterpret_cast<const uint32_t *>(ws)[0];
+                const uint32_t m = reinterpret_cast<const uint32_t *>(ws)[1];
+                const SlowLayout sl = slow_layout(glen);
+                GlobalSink sink{A.out, out_at + loff, A.out_cap};
+                emit_line(ws + sl.chs, ws + sl.text, m, C.plen_tab, sink);
+                if (fl & kLfNl) sink.put(kNl);
+            } else if (staged) {
+                SmemSink sink{M.ost + so + loff};
+                emit_line(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
+                if (fl & kLfNl) sink.put(kNl);
             } else {
-                for (uint32_t k = lo_b; k < hi_b; ++k)
-                    if (k >= so && k < so + btotal && out_at - so + k < A.out_cap) gdst[k] = M.ost[k];
+                GlobalSink sink{A.out, out_at + loff, A.out_cap};
+                emit_line(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
+                if (fl & kLfNl) sink.put(kNl);
             }
         }
+        __syncwarp();
+        if (staged) {
+            uint8_t *gdst = A.out + out_at - so;  // 16-byte aligned
+            const uint32_t nchunks = (uint32_t)((so + btotal + 15) >> 4);
+            for (uint32_t c = lane; c < nchunks; c += 32) {
+                const uint32_t lo_b = c * 16u, hi_b = lo_b + 16u;
+                if (lo_b >= so && hi_b <= so + btotal && out_at - so + hi_b <= A.out_cap) {
+                    *reinterpret_cast<uint4 *>(gdst + lo_b) = *reinterpret_cast<const uint4 *>(M.ost + lo_b);
+                } else {
+                    for (uint32_t k = lo_b; k < hi_b; ++k)
+                        if (k >= so && k < so + btotal && out_at - so + k < A.out_cap) gdst[k] = M.ost[k];
+                }
+            }
+        }
+        __syncwarp();
     }
-    __syncwarp();
-}
 
-__device__ __forceinline__ void finish_result(const Ctx &C, uint64_t t, uint64_t tot_a, uint64_t tot_b)
-{
-    const MArgs &A = *C.A;
-    if (C.lane == 0 && t == A.ntiles - 1) {
-        A.res->out_len = tot_a;
-        A.res->n_lines = tot_b;
-        if (A.index && tot_b < A.index_cap) A.index[tot_b] = tot_a;
+    static __device__ __forceinline__ void finish_result(const Ctx &C, uint64_t t, uint64_t tot_a, uint64_t tot_b)
+    {
+        const ShardView &A = *C.A;
+        if (C.lane == 0 && t == A.ntiles - 1) {
+            A.res->out_len = tot_a;
+            A.res->n_lines = tot_b;
+            if (A.index && tot_b < A.index_cap) A.index[tot_b] = tot_a;
+        }
     }
-}
 
-// Encode a tile of at most kMaxLW lines and publish its aggregate.
-__device__ void encode_single(const Ctx &C, Slot &S, uint64_t t)
-{
-    bool any_slow = false;
-    const uint64_t btotal = prepare_batch(C, S, t, 0, S.Lt, &any_slow);
-    if (C.lane == 0) {
-        S.btotal = btotal;
-        S.any_slow = any_slow ? 1u : 0u;
-        if ((int64_t)t != C.A->stall_tile) publish(&C.A->tiles[t], t == 0 ? 2u : 1u, btotal, S.Lt);
-    }
-    __syncwarp();
-}
-
-// Resolve the offset of an encoded tile and emit it.
-__device__ void finish_single(const Ctx &C, Slot &S, uint64_t t)
-{
-    const MArgs &A = *C.A;
-    uint64_t ea = 0, eb = 0;
-    if (t > 0) lookback_warp(A.tiles, t, &ea, &eb, A.limit_ns, C.status);
-    const uint64_t btotal = S.btotal;
-    const uint32_t Lt = S.Lt;
-    if (C.lane == 0 && t > 0 && (int64_t)t != A.stall_tile) publish(&A.tiles[t], 2u, ea + btotal, eb + Lt);
-    const bool staged = !S.any_slow && btotal + 48 <= (uint64_t)kOutW;
-    emit_batch(C, S, t, Lt, ea, eb, btotal, staged);
-    finish_result(C, t, ea + btotal, eb + Lt);
-}
-
-// A tile with more lines than one batch holds: look back first, then encode and emit batch by batch.
-__device__ void process_batched(const Ctx &C, Slot &S, uint64_t t)
-{
-    const MArgs &A = *C.A;
-    const uint32_t Lt = S.Lt;
-    uint64_t ea = 0, eb = 0;
-    if (t > 0) lookback_warp(A.tiles, t, &ea, &eb, A.limit_ns, C.status);
-    uint64_t run = 0;
-    for (uint32_t r0 = 0; r0 < Lt; r0 += kMaxLW) {
-        const uint32_t r1 = min(Lt, r0 + kMaxLW);
+    // Encode a tile of at most kMaxLW lines and publish its aggregate.
+    static __device__ void encode_single(const Ctx &C, Slot &S, uint64_t t)
+    {
         bool any_slow = false;
-        const uint64_t btotal = prepare_batch(C, S, t, r0, r1, &any_slow);
-        emit_batch(C, S, t, r1 - r0, ea + run, eb + r0, btotal, false);
-        run += btotal;
-    }
-    if (C.lane == 0 && (int64_t)t != A.stall_tile) publish(&A.tiles[t], 2u, ea + run, eb + Lt);
-    finish_result(C, t, ea + run, eb + Lt);
-    __syncwarp();
-}
-
-__global__ void __launch_bounds__(kMNT, 1) compress_warp_kernel(MArgs A)
-{
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint64_t img_bar;
-    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpMem &M = reinterpret_cast<WarpMem *>(smem)[wid];
-    uint8_t *img = smem + kMW * sizeof(WarpMem);
-    Ctx C;
-    C.A = &A;
-    C.M = &M;
-    C.clsrep = img + kMOffClsRep;
-    C.plen_tab = img + kMOffPlen;
-    C.T = reinterpret_cast<const uint32_t *>(img + kMOffTable);
-    C.nc = A.n_classes;
-    C.q0 = A.start_state;
-    C.lane = lane;
-    C.status = &A.res->status;
-
-    if (threadIdx.x == 0) mbar_init(&img_bar, 1);
-    if (lane == 0) {
-        mbar_init(&M.slot[0].bar, 1);
-        mbar_init(&M.slot[1].bar, 1);
-    }
-    for (uint32_t j = lane; j < 16 * 32; j += 32) M.open2[j] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive_tx(&img_bar, A.img_bytes);
-        bulk_g2s(img, A.mimg, A.img_bytes, &img_bar);
-    }
-    if (!mbar_wait_bounded(&img_bar, 0, A.limit_ns, C.status)) {
-        mbar_wait_bounded(&img_bar, 0, A.limit_ns, C.status);
-        return;
+        const uint64_t btotal = prepare_batch(C, S, t, 0, S.Lt, &any_slow);
+        if (C.lane == 0) {
+            S.btotal = btotal;
+            S.any_slow = any_slow ? 1u : 0u;
+            if ((int64_t)t != C.P->stall_tile) publish(&C.A->tiles[t], t == 0 ? 2u : 1u, btotal, S.Lt);
+        }
+        __syncwarp();
     }
 
-    uint32_t ph = 0;  // phase bit of each slot's barrier (bit s)
-    uint32_t s = 0;
-    bool pending = false;
-    uint64_t t_pend = 0;
-    for (;;) {
-        unsigned long long tt = 0;
-        if (lane == 0) tt = atomicAdd(&A.res->tile_counter, 1ull);
-        const uint64_t t = __shfl_sync(kFull, tt, 0);
-        if (t >= A.ntiles) break;
-        Slot &S = M.slot[s];
-        stage_issue(C, S, t);
-        if (!mbar_wait_bounded(&S.bar, (ph >> s) & 1u, A.limit_ns, C.status)) {
-            mbar_wait_bounded(&S.bar, (ph >> s) & 1u, A.limit_ns, C.status);
+    // Resolve the offset of an encoded tile and emit it.
+    static __device__ void finish_single(const Ctx &C, Slot &S, uint64_t t)
+    {
+        const ShardView &A = *C.A;
+        uint64_t ea = 0, eb = 0;
+        if (t > 0) lookback_warp(A.tiles, t, &ea, &eb, C.P->limit_ns, C.status);
+        const uint64_t btotal = S.btotal;
+        const uint32_t Lt = S.Lt;
+        if (C.lane == 0 && t > 0 && (int64_t)t != C.P->stall_tile) publish(&A.tiles[t], 2u, ea + btotal, eb + Lt);
+        const bool staged = !S.any_slow && btotal + 48 <= (uint64_t)kOutW;
+        emit_batch(C, S, t, Lt, ea, eb, btotal, staged);
+        finish_result(C, t, ea + btotal, eb + Lt);
+    }
+
+    // A tile with more lines than one batch holds: look back first, then encode and emit batch by batch.
+    static __device__ void process_batched(const Ctx &C, Slot &S, uint64_t t)
+    {
+        const ShardView &A = *C.A;
+        const uint32_t Lt = S.Lt;
+        uint64_t ea = 0, eb = 0;
+        if (t > 0) lookback_warp(A.tiles, t, &ea, &eb, C.P->limit_ns, C.status);
+        uint64_t run = 0;
+        for (uint32_t r0 = 0; r0 < Lt; r0 += kMaxLW) {
+            const uint32_t r1 = min(Lt, r0 + kMaxLW);
+            bool any_slow = false;
+            const uint64_t btotal = prepare_batch(C, S, t, r0, r1, &any_slow);
+            emit_batch(C, S, t, r1 - r0, ea + run, eb + r0, btotal, false);
+            run += btotal;
+        }
+        if (C.lane == 0 && (int64_t)t != C.P->stall_tile) publish(&A.tiles[t], 2u, ea + run, eb + Lt);
+        finish_result(C, t, ea + run, eb + Lt);
+        __syncwarp();
+    }
+
+    static __device__ void run(const CwArgs *P)
+    {
+        extern __shared__ __align__(128) uint8_t smem[];
+        __shared__ uint64_t img_bar;
+        const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        WarpMem &M = reinterpret_cast<WarpMem *>(smem)[wid];
+        uint8_t *img = smem + kMW * sizeof(WarpMem);
+        Ctx C;
+        C.P = P;
+        C.A = nullptr;
+        C.M = &M;
+        C.clsrep = img + kMOffClsRep;
+        C.plen_tab = img + kMOffPlen;
+        C.T = reinterpret_cast<const uint32_t *>(img + kMOffTable);
+        C.nc = P->n_classes;
+        C.q0 = P->start_state;
+        C.lane = lane;
+        C.status = &P->g->status;
+
+        if (threadIdx.x == 0) mbar_init(&img_bar, 1);
+        if (lane == 0) {
+            mbar_init(&M.slot[0].bar, 1);
+            mbar_init(&M.slot[1].bar, 1);
+        }
+        for (uint32_t j = lane; j < 16 * 32; j += 32) M.open2[j] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_tx(&img_bar, P->img_bytes);
+            bulk_g2s(img, P->mimg, P->img_bytes, &img_bar);
+        }
+        if (!mbar_wait_bounded(&img_bar, 0, P->limit_ns, C.status)) {
+            mbar_wait_bounded(&img_bar, 0, P->limit_ns, C.status);
             return;
         }
-        ph ^= 1u << s;
-        __syncwarp();
-        segment(C, S, t);
-        if (S.Lt <= (uint32_t)kMaxLW) {
-            encode_single(C, S, t);
-            if (pending) finish_single(C, M.slot[s ^ 1u], t_pend);
-            pending = true;
-            t_pend = t;
-            s ^= 1u;
-        } else {
-            if (pending) finish_single(C, M.slot[s ^ 1u], t_pend);
-            pending = false;
-            process_batched(C, S, t);
+
+        uint32_t ph = 0;  // phase bit of each slot's barrier (bit s)
+        uint32_t s = 0;
+        bool pending = false;
+        uint64_t t_pend = 0;
+        auto finish_pending = [&]() {
+            Ctx Cp = C;
+            Cp.A = &M.slot[s ^ 1u].sv;
+            finish_single(Cp, M.slot[s ^ 1u], t_pend);
+        };
+        for (;;) {
+            unsigned long long tt = 0;
+            if (lane == 0) tt = atomicAdd(&P->g->tile_counter, 1ull);
+            const uint64_t g = __shfl_sync(kFull, tt, 0);
+            if (g >= P->total_tiles) break;
+            Slot &S = M.slot[s];
+            const uint32_t sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g);
+            load_shard(&S.sv, P->one, P->shards, P->n_shards, sh);
+            const uint64_t t = g - S.sv.tile0;  // tile number within the shard
+            Ctx Cs = C;
+            Cs.A = &S.sv;
+            stage_issue(Cs, S, t);
+            if (!mbar_wait_bounded(&S.bar, (ph >> s) & 1u, P->limit_ns, C.status)) {
+                mbar_wait_bounded(&S.bar, (ph >> s) & 1u, P->limit_ns, C.status);
+                return;
+            }
+            ph ^= 1u << s;
+            __syncwarp();
+            segment(Cs, S, t);
+            if (S.Lt <= (uint32_t)kMaxLW) {
+                encode_single(Cs, S, t);
+                if (pending) finish_pending();
+                pending = true;
+                t_pend = t;
+                s ^= 1u;
+            } else {
+                if (pending) finish_pending();
+                pending = false;
+                process_batched(Cs, S, t);
+            }
         }
+        if (pending) finish_pending();
     }
-    if (pending) finish_single(C, M.slot[s ^ 1u], t_pend);
+};
+
+template <class Geo>
+__global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_warp_kernel(const CwArgs P)
+{
+    CW<Geo>::run(&P);
 }
 
-}  // namespace
+// The compiled geometries. Variant 0 (33 lines of 46 bytes per warp tile, 16 warps per SM) is the
+// default; variant 1 keeps long lines (hundreds of bytes) several to a tile; variant 2 sits between.
+using CwV0 = CwGeom<16, 1536, 512, 72, 1024>;
+using CwV1 = CwGeom<8, 4096, 1024, 192, 2368>;
+using CwV2 = CwGeom<12, 2048, 1024, 96, 1536>;
 
-uint64_t compress_warp_tiles(uint64_t n) { return (n + kTW - 1) / kTW; }
-
-size_t compress_warp_smem(const zs_dict *d) { return kMW * sizeof(WarpMem) + d->mlayout.img_bytes; }
-
-cudaError_t launch_compress_warp(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,
-                                 uint64_t out_cap, uint64_t *index, uint64_t index_cap, DevResult *res,
-                                 TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s)
+template <class Geo>
+size_t cw_smem(const zs_dict *d)
 {
-    MArgs a{};
-    a.in = in;
-    a.n = n;
-    a.out = out;
-    a.out_cap = out_cap;
-    a.index = index;
-    a.index_cap = index_cap;
+    return CW<Geo>::kMW * sizeof(typename CW<Geo>::WarpMem) + d->mlayout.img_bytes;
+}
+
+template <class Geo>
+cudaError_t cw_launch(const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s)
+{
+    CwArgs a{};
+    a.one = L.one;
+    a.shards = L.shards;
+    a.n_shards = L.n_shards;
     a.flags = flags;
-    a.in_aligned = (((uintptr_t)in) & 15u) == 0 ? 1u : 0u;
-    a.ntiles = compress_warp_tiles(n);
+    a.total_tiles = L.total_tiles;
     a.mimg = d->d_mimg;
     a.img_bytes = d->mlayout.img_bytes;
     a.n_classes = d->mlayout.n_classes;
     a.start_state = d->mlayout.start;
-    a.res = res;
-    a.tiles = tiles;
-    a.slow = slow;
-    a.slow_cap = slow_cap;
+    a.g = L.g;
+    a.slow = L.slow;
+    a.slow_cap = L.slow_cap;
     a.limit_ns = wait_limit_ns();
     a.stall_tile = injected_stall_tile();
-    const int smem = (int)compress_warp_smem(d);
+    const int smem = (int)cw_smem<Geo>(d);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     static int set_smem = -1;
     if (set_smem != smem) {
-        cudaError_t e = cudaFuncSetAttribute(compress_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(compress_warp_kernel<Geo>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
         if (e != cudaSuccess) return e;
         set_smem = smem;
     }
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compress_warp_kernel, kMNT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compress_warp_kernel<Geo>, CW<Geo>::kMNT, smem);
     if (per < 1) per = 1;
-    uint64_t grid = std::min<uint64_t>((a.ntiles + kMW - 1) / kMW, (uint64_t)per * (uint64_t)sms);
+    uint64_t grid = std::min<uint64_t>((L.total_tiles + Geo::kWarps - 1) / Geo::kWarps, (uint64_t)per * (uint64_t)sms);
     if (grid == 0) grid = 1;
-    compress_warp_kernel<<<(unsigned)grid, kMNT, smem, s>>>(a);
+    compress_warp_kernel<Geo><<<(unsigned)grid, CW<Geo>::kMNT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+struct CwEntry {
+    KernelVariant info;
+    size_t (*smem)(const zs_dict *);
+    cudaError_t (*launch)(const zs_dict *, const TiledLaunch &, unsigned, cudaStream_t);
+};
+
+template <class Geo>
+constexpr CwEntry cw_entry(const char *name)
+{
+    return CwEntry{KernelVariant{name, Geo::kWarps, Geo::kTile}, &cw_smem<Geo>, &cw_launch<Geo>};
+}
+
+const CwEntry kCw[] = {
+    cw_entry<CwV0>("compress w16 t1536"),
+    cw_entry<CwV1>("compress w8 t4096"),
+    cw_entry<CwV2>("compress w12 t2048"),
+};
+constexpr int kNumCw = (int)(sizeof(kCw) / sizeof(kCw[0]));
+
+}  // namespace
+
+int compress_warp_variants() { return kNumCw; }
+
+const KernelVariant *compress_warp_variant(int v) { return (v >= 0 && v < kNumCw) ? &kCw[v].info : nullptr; }
+
+bool compress_warp_fits(int v, const zs_dict *d)
+{
+    if (v < 0 || v >= kNumCw || !d->has_machine) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return kCw[v].smem(d) <= (size_t)optin;
+}
+
+cudaError_t launch_compress_warp(int v, const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s)
+{
+    if (v < 0 || v >= kNumCw) return cudaErrorInvalidValue;
+    return kCw[v].launch(d, L, flags, s);
 }
 
 }  // namespace zs

@@ -248,10 +248,6 @@ int blocks_per_sm(K kernel, int nt, int smem)
 uint64_t index_tiles(uint64_t n) { return (n + kIT - 1) / kIT; }
 uint64_t lines_tiles(uint64_t k) { return (k + kRNT - 1) / kRNT; }
 
-uint64_t decompress_tiles(uint64_t n);
-cudaError_t launch_decompress(const zs_dict *d, const uint8_t *in, uint64_t n, uint8_t *out, uint64_t out_cap,
-                              DevResult *res, TileState *tiles, cudaStream_t s);
-
 cudaError_t launch_line_index(const uint8_t *in, uint64_t n, uint64_t *index, uint64_t index_cap, DevResult *res,
                               TileState *tiles, cudaStream_t s)
 {
@@ -361,7 +357,7 @@ extern "C" zs_status zs_decompress(const zs_dict *d, const uint8_t *d_in, size_t
     zs::DevResult r{};
     st = run(const_cast<zs_dict *>(d)->pool, stream, zs::decompress_tiles(in_len), "zs_decompress",
              [&](zs::DevResult *dr, zs::TileState *tiles, cudaStream_t s) {
-                 return zs::launch_decompress(d, d_in, in_len, d_out, out_cap, dr, tiles, s);
+                 return zs::launch_decompress_single(d, d_in, in_len, d_out, out_cap, dr, tiles, s);
              },
              &r);
     if (st != ZS_OK) return st;

@@ -17,11 +17,6 @@
 
 namespace zs {
 
-cudaError_t launch_decompress(const zs_dict *d, const uint8_t *in, uint64_t n, uint8_t *out, uint64_t out_cap,
-                              DevResult *res, TileState *tiles, cudaStream_t s);
-uint64_t decompress_tiles(uint64_t n);
-uint64_t decompress_tile_bytes();
-
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 8u << 20;
@@ -89,7 +84,7 @@ extern "C" zs_status zs_decompress_noalloc(const zs_dict *d, const uint8_t *d_in
     zs::TileState *tiles = reinterpret_cast<zs::TileState *>(dr + 1);
     // the array keeps the previous call's contents: the counters and look-back records start at zero
     e = cudaMemsetAsync(scratch, 0, sizeof(zs::DevResult) + ntiles * sizeof(zs::TileState), s);
-    if (e == cudaSuccess) e = zs::launch_decompress(d, d_in, in_len, d_out, out_cap, dr, tiles, s);
+    if (e == cudaSuccess) e = zs::launch_decompress_single(d, d_in, in_len, d_out, out_cap, dr, tiles, s);
     zs::DevResult r{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, dr, sizeof r, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

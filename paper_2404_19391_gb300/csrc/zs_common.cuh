@@ -449,5 +449,106 @@ __device__ __forceinline__ void note_error_offset(DevResult *r, uint64_t off)
     atomicMax(&r->err_key, ~(unsigned long long)off);
 }
 
+// One shard of a launch: a whole input stream for the single-stream calls, one entry of the shard table
+// for the batched calls. Tiles are numbered per shard (look-back never crosses a shard); tile0 is the
+// shard's first tile in the launch-wide numbering that warps claim from.
+struct alignas(16) ShardView {
+    const uint8_t *in;
+    uint64_t n;
+    uint8_t *out;
+    uint64_t out_cap;
+    uint64_t *index;      // compress: line index (nullable); unused by decompression
+    uint64_t index_cap;
+    uint64_t tile0;
+    uint64_t ntiles;
+    TileState *tiles;     // look-back records of this shard's tiles
+    DevResult *res;       // out_len, n_lines, err_key of this shard
+    uint32_t in_aligned;  // in is 16-byte aligned (bulk copies allowed)
+    uint32_t _pad[3];
+};
+
+// One launch of a tiled kernel over one shard (`one`, n_shards == 1) or a device shard table.
+struct TiledLaunch {
+    ShardView one;
+    const ShardView *shards = nullptr;
+    uint32_t n_shards = 1;
+    uint64_t total_tiles = 0;
+    DevResult *g = nullptr;  // launch-wide counters and status (the shard's own result when n_shards == 1)
+    uint8_t *slow = nullptr;  // compression's long-line scratch
+    uint64_t slow_cap = 0;
+};
+
+// A compiled geometry of a tiled kernel.
+struct KernelVariant {
+    const char *name;
+    uint32_t warps;       // warps per CTA (one CTA per SM)
+    uint32_t tile_bytes;  // input bytes per warp tile
+};
+
+constexpr int kDefaultVariant = 0;
+
+inline uint64_t tiles_for(uint64_t n, uint32_t tile_bytes) { return (n + tile_bytes - 1) / tile_bytes; }
+
+inline ShardView single_shard(const uint8_t *in, uint64_t n, uint8_t *out, uint64_t out_cap, uint64_t *index,
+                              uint64_t index_cap, TileState *tiles, DevResult *res, uint64_t ntiles)
+{
+    ShardView v{};
+    v.in = in;
+    v.n = n;
+    v.out = out;
+    v.out_cap = out_cap;
+    v.index = index;
+    v.index_cap = index_cap;
+    v.tile0 = 0;
+    v.ntiles = ntiles;
+    v.tiles = tiles;
+    v.res = res;
+    v.in_aligned = (((uintptr_t)in) & 15u) == 0 ? 1u : 0u;
+    return v;
+}
+
+// Compiled variants of the tiled compression (transducer) and decompression kernels.
+int compress_warp_variants();
+const KernelVariant *compress_warp_variant(int v);
+bool compress_warp_fits(int v, const zs_dict *d);
+cudaError_t launch_compress_warp(int v, const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s);
+int decompress_variants();
+const KernelVariant *decompress_variant(int v);
+cudaError_t launch_decompress(int v, const zs_dict *d, const TiledLaunch &L, cudaStream_t s);
+// The default variant over one stream: tiles and launch.
+uint64_t decompress_tiles(uint64_t n);
+uint64_t decompress_tile_bytes();
+cudaError_t launch_decompress_single(const zs_dict *d, const uint8_t *in, uint64_t n, uint8_t *out, uint64_t out_cap,
+                                     DevResult *res, TileState *tiles, cudaStream_t s);
+
+// The shard owning launch-wide tile g: the last shard whose tile0 <= g (called by a whole warp; a
+// 32-way search per round, so two rounds cover 1024 shards). tab[0].tile0 must be 0.
+__device__ __forceinline__ uint32_t find_shard(const ShardView *tab, uint32_t n, uint64_t g)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t idx = lo + lane * step;
+        const bool ok = idx < hi && tab[idx].tile0 <= g;
+        const uint32_t b = __ballot_sync(0xffffffffu, ok);  // lane 0 (idx == lo) always holds
+        lo += (uint32_t)(31 - __clz(b)) * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
+// Copy shard `s` (or the single shard `one`) into a warp's shared-memory view; all lanes call.
+__device__ __forceinline__ void load_shard(ShardView *dst, const ShardView &one, const ShardView *tab, uint32_t n,
+                                           uint32_t s)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t *src = reinterpret_cast<const uint64_t *>(n == 1 ? &one : tab + s);
+    constexpr uint32_t kWords = sizeof(ShardView) / 8;
+    __syncwarp();
+    if (lane < kWords) reinterpret_cast<uint64_t *>(dst)[lane] = src[lane];
+    __syncwarp();
+}
+
 }  // namespace zs
 #endif

@@ -34,6 +34,18 @@ class _Result(ctypes.Structure):
     _fields_ = [("out_len", ctypes.c_uint64), ("n_lines", ctypes.c_uint64), ("err_offset", ctypes.c_uint64)]
 
 
+class _Shard(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("in_len", ctypes.c_size_t), ("out", ctypes.c_void_p),
+                ("out_cap", ctypes.c_size_t), ("line_index", ctypes.c_void_p), ("index_cap", ctypes.c_size_t)]
+
+
+class _PlanOptions(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("use_graph", ctypes.c_int), ("tune_reps", ctypes.c_int)]
+
+
+OP_COMPRESS, OP_DECOMPRESS = 0, 1
+
+
 @dataclass
 class Result:
     out_len: int
@@ -72,6 +84,17 @@ def load_library(rebuild: bool = False) -> ctypes.CDLL:
         "zs_version": (ctypes.c_char_p, []),
         "zs_last_kernel_ms": (ctypes.c_double, []),
         "zs_dictionary_uses_transducer": (ctypes.c_int, [vp]),
+        "zs_kernel_variants": (ctypes.c_int, [ctypes.c_int]),
+        "zs_kernel_variant_name": (ctypes.c_char_p, [ctypes.c_int, ctypes.c_int]),
+        "zs_compress_batch": (ctypes.c_int, [vp, ctypes.POINTER(_Shard), sz, ctypes.c_uint, pres, vp]),
+        "zs_decompress_batch": (ctypes.c_int, [vp, ctypes.POINTER(_Shard), sz, pres, vp]),
+        "zs_plan_create": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_uint, ctypes.POINTER(_Shard), sz,
+                                          ctypes.POINTER(_PlanOptions), ctypes.POINTER(vp)]),
+        "zs_plan_run": (ctypes.c_int, [vp, pres, vp]),
+        "zs_plan_variant": (ctypes.c_int, [vp]),
+        "zs_plan_tuned_ms": (ctypes.c_double, [vp, ctypes.c_int]),
+        "zs_plan_last_ms": (ctypes.c_double, [vp]),
+        "zs_plan_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -191,6 +214,89 @@ def zs_decompress_lines(d: Dictionary, d_comp: torch.Tensor, d_index: torch.Tens
                                   ctypes.byref(res), _stream(stream))
     _check(st, res)
     return Result(res.out_len, res.n_lines, res.err_offset)
+
+
+def _shards(shards) -> "ctypes.Array":
+    """shards: sequence of (in, out, line_index or None) CUDA tensors."""
+    arr = (_Shard * max(1, len(shards)))()
+    for i, (src, dst, idx) in enumerate(shards):
+        arr[i] = _Shard(_ptr(src), src.numel(), _ptr(dst), dst.numel(), _ptr(idx),
+                        0 if idx is None else idx.numel())
+    return arr
+
+
+def _results(res_arr, n) -> list[Result]:
+    return [Result(res_arr[i].out_len, res_arr[i].n_lines, res_arr[i].err_offset) for i in range(n)]
+
+
+def zs_kernel_variants(op: int) -> int:
+    return int(_L().zs_kernel_variants(op))
+
+
+def zs_kernel_variant_name(op: int, v: int) -> str | None:
+    r = _L().zs_kernel_variant_name(op, v)
+    return r.decode() if r is not None else None
+
+
+def zs_compress_batch(d: Dictionary, shards, flags: int = PREPROCESS, stream=None) -> list[Result]:
+    arr = _shards(shards)
+    res = (_Result * max(1, len(shards)))()
+    st = _L().zs_compress_batch(d.handle, arr, len(shards), flags, res, _stream(stream))
+    if st != OK:
+        raise ZsError(st, _L().zs_last_error().decode())
+    return _results(res, len(shards))
+
+
+def zs_decompress_batch(d: Dictionary, shards, stream=None) -> list[Result]:
+    arr = _shards(shards)
+    res = (_Result * max(1, len(shards)))()
+    st = _L().zs_decompress_batch(d.handle, arr, len(shards), res, _stream(stream))
+    if st != OK:
+        raise ZsError(st, _L().zs_last_error().decode())
+    return _results(res, len(shards))
+
+
+class Plan:
+    """zs_plan_create / zs_plan_run / zs_plan_destroy over a fixed list of (in, out, index) tensors."""
+
+    def __init__(self, d: Dictionary, op: int, shards, flags: int = PREPROCESS, variant: int = -1,
+                 use_graph: bool = True, tune_reps: int = 3):
+        self._keep = list(shards)  # the tensors must outlive the plan
+        self.n = len(shards)
+        arr = _shards(shards)
+        opt = _PlanOptions(variant, 1 if use_graph else 0, tune_reps)
+        h = ctypes.c_void_p()
+        _check(_L().zs_plan_create(d.handle, op, flags, arr, self.n, ctypes.byref(opt), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None) -> list[Result]:
+        res = (_Result * max(1, self.n))()
+        st = _L().zs_plan_run(self.handle, res, _stream(stream))
+        if st != OK:
+            raise ZsError(st, _L().zs_last_error().decode())
+        return _results(res, self.n)
+
+    @property
+    def variant(self) -> int:
+        return int(_L().zs_plan_variant(self.handle))
+
+    def tuned_ms(self, v: int) -> float:
+        return float(_L().zs_plan_tuned_ms(self.handle, v))
+
+    @property
+    def last_ms(self) -> float:
+        return float(_L().zs_plan_last_ms(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _L().zs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- conveniences built only from the calls above ----------------------------------------------------
