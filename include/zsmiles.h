@@ -256,6 +256,67 @@ double zs_plan_tuned_ms(const zs_plan *p, int v);  /* median kernel ms of varian
 double zs_plan_last_ms(const zs_plan *p);          /* kernel ms of the last run */
 void zs_plan_destroy(zs_plan *p);
 
+/* ---- Serving form: continuous batching of random-access requests over a resident store -----------
+ *
+ * A server keeps a compressed store and its line index resident in device memory (the caller's
+ * buffers, which must outlive the server) and answers requests for sets of line ids (random access,
+ * Sec. I). Requests queue in arrival order. A scheduler thread admits the queue head as soon as one of
+ * max_inflight slots is free and the output arenas have room for it: every queued request that fits
+ * joins that launch (continuous batching), so requests arriving while others are on the GPU ride the
+ * next launch, and up to max_inflight launches (each with its own stream) overlap. Admission reserves
+ * an upper bound of the request's decoded size (each line's compressed span times the dictionary's
+ * longest pattern, plus its newline) in a device arena and in a pinned host arena; the host bytes stay
+ * reserved until the result is fetched or released. A request's result is exactly what
+ * zs_decompress_lines gives for its ids alone. The batching is not in the paper.
+ */
+typedef struct zs_server zs_server; /* opaque, library-owned */
+
+typedef struct zs_server_options {
+    size_t arena_bytes;   /* device arena and pinned host arena, bytes each (0: 512 MiB) */
+    size_t max_batch_ids; /* ids per launch, and the largest request (0: 1,048,576) */
+    int max_inflight;     /* launches on the GPU at once (0: 4) */
+} zs_server_options;
+
+typedef struct zs_server_stats {
+    uint64_t submitted, completed, batches, ids;
+    double mean_batch_requests; /* requests per launch */
+    int max_inflight;           /* most launches seen in flight at once */
+    double p50_ms, p99_ms;      /* submit-to-result latency of completed requests */
+} zs_server_stats;
+
+/* d_comp/comp_len: the compressed store; d_index: its line index (n_lines + 1 entries, as written by
+ * zs_compress or zs_build_line_index; checked, and copied to the host for admission). opt may be NULL.
+ * Starts the scheduler thread. */
+zs_status zs_server_create(const zs_dict *d, const uint8_t *d_comp, size_t comp_len, const uint64_t *d_index,
+                           size_t n_lines, const zs_server_options *opt, zs_server **out);
+/* Queues a request for the k line ids in ids (host array, copied); returns at once with a ticket.
+ * Thread-safe. ZS_ERR_INVALID_ARG for an id >= n_lines or k > max_batch_ids; ZS_ERR_CAPACITY when the
+ * request's bound exceeds the arena. */
+zs_status zs_server_submit(zs_server *s, const uint64_t *ids, size_t k, uint64_t *ticket);
+/* Waits (timeout_s < 0: without limit) until the request is done; res->out_len = its decoded bytes,
+ * res->n_lines = k. ZS_ERR_TIMEOUT if the time ran out (the request stays queued). */
+zs_status zs_server_wait(zs_server *s, uint64_t ticket, double timeout_s, zs_result *res);
+/* Copies a finished request's lines (out: out_cap bytes; off: k + 1 host offsets, nullable) and
+ * forgets the ticket. */
+zs_status zs_server_fetch(zs_server *s, uint64_t ticket, uint8_t *out, size_t out_cap, uint64_t *off);
+/* Forgets a finished request without copying it. */
+zs_status zs_server_release(zs_server *s, uint64_t ticket);
+zs_status zs_server_get_stats(zs_server *s, zs_server_stats *st);
+/* Stops the scheduler (queued requests fail, launches in flight finish) and frees everything. */
+void zs_server_destroy(zs_server *s);
+
+/* Open-loop load replay. Request r (k[r] ids, consecutive in ids) is submitted at arrival_s[r] seconds
+ * after the call starts (non-decreasing), whether or not earlier ones are done; latency_ms[r] runs
+ * from that scheduled arrival to the request's completion; *makespan_s (nullable) from the start to
+ * the last completion. Results are released, not returned. */
+zs_status zs_server_replay(zs_server *s, const double *arrival_s, const uint64_t *ids, const size_t *k,
+                           size_t n_req, double *latency_ms, double *makespan_s);
+/* The same replay served one request at a time, in arrival order, each by its own random-access launch
+ * with a wait and the copy of its bytes to the host (decompress-per-request, the unbatched baseline). */
+zs_status zs_serial_replay(const zs_dict *d, const uint8_t *d_comp, size_t comp_len, const uint64_t *d_index,
+                           size_t n_lines, const double *arrival_s, const uint64_t *ids, const size_t *k,
+                           size_t n_req, double *latency_ms, double *makespan_s, void *stream);
+
 /* Device time, in milliseconds, of the main kernel of the last successful zs_compress, zs_decompress,
  * zs_build_line_index or zs_decompress_lines on this thread, measured with CUDA events recorded on the
  * call's stream just before and just after the kernel launch (no paper counterpart: instrumentation). */

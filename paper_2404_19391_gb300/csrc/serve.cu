@@ -1,0 +1,832 @@
+// Serving form of random access (Sec. I: any line of a compressed library can be decoded alone): a
+// resident compressed store plus its line index, and a request loop with continuous batching.
+//
+//   - Requests (sets of line ids) are submitted from any host thread and queue in arrival order.
+//   - One scheduler thread admits the queue head into a free in-flight slot as soon as the slot and
+//     the output arenas have room: every queued request that fits (ids per launch, arena bytes) joins
+//     the batch, so requests that arrive while others are on the GPU ride the next launch. A batch is
+//     one random-access launch over the concatenated ids; up to max_inflight batches run at once, each
+//     on its own stream, so their copies and kernels overlap.
+//   - Memory admission: a request reserves an upper bound of its decoded size (compressed span of each
+//     line times the longest pattern, plus its newline) in a device arena and in a pinned host arena.
+//     After the kernel, the exact bytes are copied to the host arena, the device reservation is
+//     released, and the host bytes stay until the request's result is fetched or released.
+//   - Completion is observed by polling CUDA events; latency is arrival to the host copy's completion.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "zs_common.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over [0, size) with coalescing; 256-byte granules.
+class RangeAlloc {
+   public:
+    void reset(size_t size)
+    {
+        free_.clear();
+        if (size) free_[0] = size;
+        size_ = size;
+    }
+    static size_t round(size_t n) { return (std::max<size_t>(n, 1) + 255) & ~(size_t)255; }
+    size_t largest() const
+    {
+        size_t m = 0;
+        for (auto &kv : free_) m = std::max(m, kv.second);
+        return m;
+    }
+    bool alloc(size_t n, size_t *off)
+    {
+        n = round(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            *off = it->first;
+            const size_t rest = it->second - n, at = it->first + n;
+            free_.erase(it);
+            if (rest) free_[at] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t n)
+    {
+        n = round(n);
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + n == next->first) {
+            n += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += n;
+                return;
+            }
+        }
+        free_[off] = n;
+    }
+    size_t size() const { return size_; }
+
+   private:
+    std::map<size_t, size_t> free_;
+    size_t size_ = 0;
+};
+
+struct Batch;
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<uint64_t> ids;
+    size_t bound = 0;
+    Clock::time_point arrival, done_at;
+    int state = 0;  // 0 queued, 1 on the GPU, 2 done, 3 failed
+    zs_status err = ZS_OK;
+    std::shared_ptr<Batch> batch;
+    size_t first = 0;  // index of its first id in the batch
+    uint64_t byte_off = 0, byte_len = 0;
+    std::vector<uint64_t> off;  // k + 1 offsets, from 0
+};
+
+struct Batch {
+    size_t dev_off = 0, host_off = 0, bound = 0;
+    std::vector<Request *> reqs;
+    size_t unfetched = 0;
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    uint64_t *h_ids = nullptr, *d_ids = nullptr, *h_off = nullptr, *d_off = nullptr;
+    void *d_scratch = nullptr;
+    zs::DevResult *h_res = nullptr;
+    int state = 0;  // 0 free, 1 ids + kernel + offsets in flight, 2 bytes in flight
+    std::shared_ptr<Batch> batch;
+    size_t K = 0;
+};
+
+double ms_between(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+double percentile(std::vector<double> v, double q)
+{
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = q * (double)(v.size() - 1);
+    const size_t i = (size_t)pos;
+    const double f = pos - (double)i;
+    return i + 1 < v.size() ? v[i] * (1.0 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+
+struct zs_server {
+    const zs_dict *d = nullptr;
+    int device = -1;
+    const uint8_t *comp = nullptr;
+    size_t comp_len = 0;
+    const uint64_t *index = nullptr;
+    size_t n_lines = 0;
+    std::vector<uint64_t> h_index;  // host copy: admission bounds and id checks
+    zs_server_options opt{};
+
+    uint8_t *d_arena = nullptr;
+    uint8_t *h_arena = nullptr;
+    RangeAlloc dev_alloc, host_alloc;
+    std::vector<Slot> slots;
+    size_t scratch_tiles = 0;
+
+    std::mutex mu;
+    std::condition_variable cv;       // scheduler wake-up (submit, stop)
+    std::condition_variable done_cv;  // request completions
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+    uint64_t next_ticket = 1;
+    uint64_t changes = 0;  // bumped by submit, fetch/release and stop: the idle scheduler waits on it
+    bool stop = false;
+    zs_status fatal = ZS_OK;
+    std::string fatal_msg;
+    std::thread worker;
+
+    // statistics
+    uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, n_ids = 0, batch_reqs = 0;
+    int max_inflight_seen = 0;
+    std::vector<double> lat_ms;
+
+    void loop();
+    bool admit(Slot &s);
+    void stage2(Slot &s);
+    void finish(Slot &s);
+    void fail_batch(Slot &s, zs_status st, const std::string &msg);
+};
+
+namespace {
+
+cudaError_t issue_stage1(zs_server *S, Slot &s)
+{
+    const size_t K = s.K;
+    cudaError_t e = cudaMemcpyAsync(s.d_ids, s.h_ids, K * sizeof(uint64_t), cudaMemcpyHostToDevice, s.st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s.d_scratch, 0,
+                            sizeof(zs::DevResult) + zs::lines_tiles(K) * sizeof(zs::TileState), s.st);
+    zs::DevResult *dr = reinterpret_cast<zs::DevResult *>(s.d_scratch);
+    zs::TileState *tiles = reinterpret_cast<zs::TileState *>(dr + 1);
+    if (e == cudaSuccess)
+        e = zs::launch_lines(S->d, S->comp, S->comp_len, S->index, S->n_lines, s.d_ids, K,
+                             S->d_arena + s.batch->dev_off, s.batch->bound, s.d_off, dr, tiles, s.st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.h_off, s.d_off, (K + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_res, dr, sizeof(zs::DevResult), cudaMemcpyDeviceToHost, s.st);
+    if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
+    return e;
+}
+
+}  // namespace
+
+// Forms a batch from the queue head for free slot s. Caller holds mu.
+bool zs_server::admit(Slot &s)
+{
+    if (queue.empty()) return false;
+    const size_t room = std::min(dev_alloc.largest(), host_alloc.largest());
+    size_t K = 0, bound = 0;
+    std::vector<Request *> take;
+    for (Request *r : queue) {
+        const size_t nb = RangeAlloc::round(bound + r->bound);
+        if (K + r->ids.size() > opt.max_batch_ids || nb > room) break;
+        K += r->ids.size();
+        bound = nb;
+        take.push_back(r);
+    }
+    if (take.empty()) return false;  // the head waits for memory (no overtaking)
+    auto b = std::make_shared<Batch>();
+    b->bound = bound;
+    if (!dev_alloc.alloc(bound, &b->dev_off)) return false;
+    if (!host_alloc.alloc(bound, &b->host_off)) {
+        dev_alloc.release(b->dev_off, bound);
+        return false;
+    }
+    size_t at = 0;
+    for (Request *r : take) {
+        std::memcpy(s.h_ids + at, r->ids.data(), r->ids.size() * sizeof(uint64_t));
+        r->first = at;
+        r->state = 1;
+        r->batch = b;
+        at += r->ids.size();
+        b->reqs.push_back(r);
+        queue.pop_front();
+    }
+    b->unfetched = take.size();
+    s.batch = b;
+    s.K = K;
+    s.state = 1;
+    ++n_batches;
+    batch_reqs += take.size();
+    n_ids += K;
+    cudaError_t e = issue_stage1(this, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail_batch(s, ZS_ERR_CUDA, std::string("zs_server: launch failed: ") + cudaGetErrorString(e));
+    }
+    return true;
+}
+
+void zs_server::fail_batch(Slot &s, zs_status st, const std::string &msg)
+{
+    auto b = s.batch;
+    const Clock::time_point now = Clock::now();
+    for (Request *r : b->reqs) {
+        r->state = 3;
+        r->err = st;
+        r->done_at = now;
+    }
+    dev_alloc.release(b->dev_off, b->bound);
+    if (fatal == ZS_OK && st == ZS_ERR_CUDA) {  // the server takes no more work: fail the queue too
+        fatal = st;
+        fatal_msg = msg;
+        for (Request *r : queue) {
+            r->state = 3;
+            r->err = st;
+            r->done_at = now;
+        }
+        queue.clear();
+    }
+    s.state = 0;
+    s.batch.reset();
+    done_cv.notify_all();
+}
+
+// Offsets arrived: check the launch, hand out per-request offsets, copy the exact bytes back.
+void zs_server::stage2(Slot &s)
+{
+    auto b = s.batch;
+    const zs::DevResult r = *s.h_res;
+    if (r.status & (zs::kStMalformed | zs::kStTimeout)) {
+        fail_batch(s, (r.status & zs::kStTimeout) ? ZS_ERR_TIMEOUT : ZS_ERR_MALFORMED,
+                   "zs_server: the random-access launch reported an error");
+        return;
+    }
+    for (Request *q : b->reqs) {
+        const size_t k = q->ids.size();
+        const uint64_t base = s.h_off[q->first];
+        q->off.resize(k + 1);
+        for (size_t j = 0; j <= k; ++j) q->off[j] = s.h_off[q->first + j] - base;
+        q->byte_off = base;
+        q->byte_len = q->off[k];
+    }
+    cudaError_t e = cudaSuccess;
+    if (r.out_len)
+        e = cudaMemcpyAsync(h_arena + b->host_off, d_arena + b->dev_off, r.out_len, cudaMemcpyDeviceToHost, s.st);
+    if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail_batch(s, ZS_ERR_CUDA, std::string("zs_server: copy failed: ") + cudaGetErrorString(e));
+        return;
+    }
+    s.state = 2;
+}
+
+void zs_server::finish(Slot &s)
+{
+    auto b = s.batch;
+    const Clock::time_point now = Clock::now();
+    for (Request *r : b->reqs) {
+        r->state = 2;
+        r->done_at = now;
+        lat_ms.push_back(ms_between(r->arrival, now));
+        ++n_completed;
+    }
+    dev_alloc.release(b->dev_off, b->bound);
+    s.state = 0;
+    s.batch.reset();
+    done_cv.notify_all();
+}
+
+void zs_server::loop()
+{
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        bool busy = false, progressed = false;
+        for (Slot &s : slots) {
+            if (s.state == 0) continue;
+            busy = true;
+            const cudaError_t q = cudaEventQuery(s.ev);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                fail_batch(s, ZS_ERR_CUDA, std::string("zs_server: ") + cudaGetErrorString(q));
+            } else if (s.state == 1) {
+                stage2(s);
+            } else {
+                finish(s);
+            }
+            progressed = true;
+        }
+        int inflight = 0;
+        for (Slot &s : slots) {
+            if (s.state == 0 && fatal == ZS_OK && admit(s)) progressed = true;
+            inflight += s.state != 0;
+        }
+        max_inflight_seen = std::max(max_inflight_seen, inflight);
+        if (stop && inflight == 0) break;
+        if (progressed) continue;
+        if (busy || inflight) {
+            cv.wait_for(lk, std::chrono::microseconds(20));  // poll the in-flight events
+        } else {
+            const uint64_t seen = changes;  // the queue head waits for arena room or a new request
+            cv.wait(lk, [&] { return stop || changes != seen; });
+        }
+    }
+}
+
+extern "C" zs_status zs_server_create(const zs_dict *d, const uint8_t *d_comp, size_t comp_len,
+                                      const uint64_t *d_index, size_t n_lines, const zs_server_options *opt,
+                                      zs_server **out)
+{
+    zs::clear_error();
+    if (!out || !d || !d_index || (!d_comp && comp_len)) {
+        zs::set_error("zs_server_create: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return zs::cuda_fail(e, "zs_server_create: cudaGetDevice");
+    if (dev != d->device) {
+        zs::set_error("zs_server_create: dictionary was loaded on another device");
+        return ZS_ERR_INVALID_ARG;
+    }
+    auto S = std::make_unique<zs_server>();
+    S->d = d;
+    S->device = dev;
+    S->comp = d_comp;
+    S->comp_len = comp_len;
+    S->index = d_index;
+    S->n_lines = n_lines;
+    S->opt.arena_bytes = opt && opt->arena_bytes ? opt->arena_bytes : (size_t)512 << 20;
+    S->opt.max_batch_ids = opt && opt->max_batch_ids ? opt->max_batch_ids : (size_t)1 << 20;
+    S->opt.max_inflight = opt && opt->max_inflight > 0 ? opt->max_inflight : 4;
+    S->h_index.resize(n_lines + 1);
+    e = cudaMemcpy(S->h_index.data(), d_index, (n_lines + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return zs::cuda_fail(e, "zs_server_create: reading the line index");
+    for (size_t i = 0; i < n_lines; ++i)
+        if (S->h_index[i] > S->h_index[i + 1] || S->h_index[i + 1] > comp_len) {
+            zs::set_error("zs_server_create: line index is not a valid index of the store");
+            return ZS_ERR_INVALID_ARG;
+        }
+    const size_t K = S->opt.max_batch_ids;
+    S->scratch_tiles = zs::lines_tiles(K);
+    e = cudaMalloc(&S->d_arena, S->opt.arena_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&S->h_arena), S->opt.arena_bytes);
+    S->slots.resize(S->opt.max_inflight);
+    for (Slot &s : S->slots) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&s.h_ids), K * sizeof(uint64_t));
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&s.h_off), (K + 1) * sizeof(uint64_t));
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&s.h_res), sizeof(zs::DevResult));
+        if (e == cudaSuccess) e = cudaMalloc(&s.d_ids, K * sizeof(uint64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&s.d_off, (K + 1) * sizeof(uint64_t));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&s.d_scratch, sizeof(zs::DevResult) + S->scratch_tiles * sizeof(zs::TileState));
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        zs_server_destroy(S.release());
+        zs::set_error("zs_server_create: out of memory");
+        return ZS_ERR_OOM;
+    }
+    S->dev_alloc.reset(S->opt.arena_bytes);
+    S->host_alloc.reset(S->opt.arena_bytes);
+    zs_server *raw = S.release();
+    raw->worker = std::thread([raw] { raw->loop(); });
+    *out = raw;
+    return ZS_OK;
+}
+
+extern "C" void zs_server_destroy(zs_server *S)
+{
+    if (!S) return;
+    if (S->worker.joinable()) {
+        {
+            std::lock_guard<std::mutex> g(S->mu);
+            S->stop = true;
+            for (Request *r : S->queue) {  // never started
+                r->state = 3;
+                r->err = ZS_ERR_INVALID_ARG;
+            }
+            S->queue.clear();
+            ++S->changes;
+        }
+        S->cv.notify_all();
+        S->done_cv.notify_all();
+        S->worker.join();
+    }
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (S->device >= 0) cudaSetDevice(S->device);
+    for (Slot &s : S->slots) {
+        if (s.st) cudaStreamSynchronize(s.st);
+        if (s.ev) cudaEventDestroy(s.ev);
+        if (s.st) cudaStreamDestroy(s.st);
+        if (s.h_ids) cudaFreeHost(s.h_ids);
+        if (s.h_off) cudaFreeHost(s.h_off);
+        if (s.h_res) cudaFreeHost(s.h_res);
+        if (s.d_ids) cudaFree(s.d_ids);
+        if (s.d_off) cudaFree(s.d_off);
+        if (s.d_scratch) cudaFree(s.d_scratch);
+    }
+    if (S->d_arena) cudaFree(S->d_arena);
+    if (S->h_arena) cudaFreeHost(S->h_arena);
+    if (cur >= 0) cudaSetDevice(cur);
+    delete S;
+}
+
+extern "C" zs_status zs_server_submit(zs_server *S, const uint64_t *ids, size_t k, uint64_t *ticket)
+{
+    zs::clear_error();
+    if (!S || !ticket || (!ids && k)) {
+        zs::set_error("zs_server_submit: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    const Clock::time_point now = Clock::now();
+    if (k > S->opt.max_batch_ids) {
+        zs::set_error("zs_server_submit: more ids than one launch takes (max_batch_ids)");
+        return ZS_ERR_INVALID_ARG;
+    }
+    auto r = std::make_unique<Request>();
+    r->ids.assign(ids, ids + k);
+    r->arrival = now;
+    size_t bound = 0;
+    const size_t lmax = (size_t)std::max(1, S->d->lmax);
+    for (size_t j = 0; j < k; ++j) {
+        const uint64_t id = ids[j];
+        if (id >= S->n_lines) {
+            zs::set_error("zs_server_submit: line id " + std::to_string(id) + " out of range");
+            return ZS_ERR_INVALID_ARG;
+        }
+        bound += (size_t)(S->h_index[id + 1] - S->h_index[id]) * lmax + 1;
+    }
+    r->bound = bound;
+    if (RangeAlloc::round(bound) > S->opt.arena_bytes) {
+        zs::set_error("zs_server_submit: the request's output bound exceeds the arena");
+        return ZS_ERR_CAPACITY;
+    }
+    std::lock_guard<std::mutex> g(S->mu);
+    if (S->fatal != ZS_OK) {
+        zs::set_error(S->fatal_msg);
+        return S->fatal;
+    }
+    r->ticket = S->next_ticket++;
+    *ticket = r->ticket;
+    ++S->n_submitted;
+    Request *p = r.get();
+    S->reqs[p->ticket] = std::move(r);
+    if (k == 0) {
+        p->state = 2;
+        p->done_at = now;
+        p->off.assign(1, 0);
+        ++S->n_completed;
+        S->lat_ms.push_back(0.0);
+        S->done_cv.notify_all();
+        return ZS_OK;
+    }
+    S->queue.push_back(p);
+    ++S->changes;
+    S->cv.notify_all();
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_server_wait(zs_server *S, uint64_t ticket, double timeout_s, zs_result *res)
+{
+    zs::clear_error();
+    if (!S) {
+        zs::set_error("zs_server_wait: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) {
+        zs::set_error("zs_server_wait: unknown ticket");
+        return ZS_ERR_INVALID_ARG;
+    }
+    Request *r = it->second.get();
+    auto ready = [&] { return r->state >= 2; };
+    if (timeout_s < 0) {
+        S->done_cv.wait(lk, ready);
+    } else if (!S->done_cv.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) {
+        zs::set_error("zs_server_wait: timed out");
+        return ZS_ERR_TIMEOUT;
+    }
+    if (res) {
+        res->out_len = r->byte_len;
+        res->n_lines = r->ids.size();
+        res->err_offset = 0;
+    }
+    if (r->state == 3) {
+        zs::set_error("zs_server_wait: the request failed");
+        return r->err;
+    }
+    return ZS_OK;
+}
+
+namespace {
+
+// Drops a finished request, releasing its batch's host bytes with the batch's last request. Holds mu.
+void drop(zs_server *S, std::unordered_map<uint64_t, std::unique_ptr<Request>>::iterator it)
+{
+    Request *r = it->second.get();
+    if (auto b = r->batch) {
+        if (--b->unfetched == 0) S->host_alloc.release(b->host_off, b->bound);
+        r->batch.reset();
+    }
+    S->reqs.erase(it);
+    ++S->changes;
+    S->cv.notify_all();  // host room may let the queue head in
+}
+
+// Waits for a request, notes when it finished, and drops it.
+zs_status wait_release(zs_server *S, uint64_t ticket, Clock::time_point *done_at)
+{
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return ZS_ERR_INVALID_ARG;
+    Request *r = it->second.get();
+    S->done_cv.wait(lk, [&] { return r->state >= 2; });
+    const zs_status st = r->state == 3 ? r->err : ZS_OK;
+    *done_at = r->done_at;
+    drop(S, it);
+    return st;
+}
+
+void wait_until(Clock::time_point t)
+{
+    if (t - Clock::now() > std::chrono::microseconds(200)) std::this_thread::sleep_until(t - std::chrono::microseconds(100));
+    while (Clock::now() < t) std::this_thread::yield();
+}
+
+}  // namespace
+
+extern "C" zs_status zs_server_fetch(zs_server *S, uint64_t ticket, uint8_t *out, size_t out_cap, uint64_t *off)
+{
+    zs::clear_error();
+    if (!S) {
+        zs::set_error("zs_server_fetch: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) {
+        zs::set_error("zs_server_fetch: unknown ticket");
+        return ZS_ERR_INVALID_ARG;
+    }
+    Request *r = it->second.get();
+    if (r->state < 2) {
+        zs::set_error("zs_server_fetch: the request is not finished (call zs_server_wait first)");
+        return ZS_ERR_INVALID_ARG;
+    }
+    if (r->state == 3) {
+        const zs_status st = r->err;
+        drop(S, it);
+        zs::set_error("zs_server_fetch: the request failed");
+        return st;
+    }
+    if ((r->byte_len && !out) || out_cap < r->byte_len) {
+        zs::set_error("zs_server_fetch: output buffer too small");
+        return ZS_ERR_CAPACITY;
+    }
+    if (r->byte_len) std::memcpy(out, S->h_arena + r->batch->host_off + r->byte_off, r->byte_len);
+    if (off) std::memcpy(off, r->off.data(), r->off.size() * sizeof(uint64_t));
+    drop(S, it);
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_server_release(zs_server *S, uint64_t ticket)
+{
+    zs::clear_error();
+    if (!S) {
+        zs::set_error("zs_server_release: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end() || it->second->state < 2) {
+        zs::set_error("zs_server_release: unknown or unfinished ticket");
+        return ZS_ERR_INVALID_ARG;
+    }
+    drop(S, it);
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_server_get_stats(zs_server *S, zs_server_stats *st)
+{
+    zs::clear_error();
+    if (!S || !st) {
+        zs::set_error("zs_server_get_stats: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> g(S->mu);
+    st->submitted = S->n_submitted;
+    st->completed = S->n_completed;
+    st->batches = S->n_batches;
+    st->ids = S->n_ids;
+    st->mean_batch_requests = S->n_batches ? (double)S->batch_reqs / (double)S->n_batches : 0.0;
+    st->max_inflight = S->max_inflight_seen;
+    st->p50_ms = percentile(S->lat_ms, 0.50);
+    st->p99_ms = percentile(S->lat_ms, 0.99);
+    return ZS_OK;
+}
+
+namespace {
+
+zs_status check_replay_args(const double *arrival_s, const uint64_t *ids, const size_t *k, size_t n_req,
+                            double *latency_ms, const char *what)
+{
+    if ((!arrival_s || !k || !latency_ms) && n_req) {
+        zs::set_error(std::string(what) + ": NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    size_t total = 0;
+    for (size_t r = 0; r < n_req; ++r) {
+        if (r && arrival_s[r] < arrival_s[r - 1]) {
+            zs::set_error(std::string(what) + ": arrival times must not decrease");
+            return ZS_ERR_INVALID_ARG;
+        }
+        total += k[r];
+    }
+    if (total && !ids) {
+        zs::set_error(std::string(what) + ": NULL ids");
+        return ZS_ERR_INVALID_ARG;
+    }
+    return ZS_OK;
+}
+
+}  // namespace
+
+extern "C" zs_status zs_server_replay(zs_server *S, const double *arrival_s, const uint64_t *ids, const size_t *k,
+                                      size_t n_req, double *latency_ms, double *makespan_s)
+{
+    zs::clear_error();
+    if (!S) {
+        zs::set_error("zs_server_replay: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    zs_status st = check_replay_args(arrival_s, ids, k, n_req, latency_ms, "zs_server_replay");
+    if (st != ZS_OK) return st;
+    std::vector<uint64_t> tickets(n_req, 0);
+    std::vector<Clock::time_point> when(n_req);
+    std::mutex tmu;
+    std::condition_variable tcv;
+    size_t posted = 0;
+    zs_status col_st = ZS_OK;
+    Clock::time_point last_done;
+    const Clock::time_point t0 = Clock::now() + std::chrono::milliseconds(2);
+    for (size_t r = 0; r < n_req; ++r)
+        when[r] = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(arrival_s[r]));
+    std::thread collector([&] {
+        cudaSetDevice(S->device);
+        last_done = t0;
+        for (size_t r = 0; r < n_req; ++r) {
+            uint64_t t;
+            {
+                std::unique_lock<std::mutex> lk(tmu);
+                tcv.wait(lk, [&] { return posted > r; });
+                t = tickets[r];
+            }
+            if (t == 0) {  // submission failed; the submitter stops
+                latency_ms[r] = -1.0;
+                continue;
+            }
+            Clock::time_point done;
+            const zs_status s2 = wait_release(S, t, &done);
+            if (s2 != ZS_OK && col_st == ZS_OK) col_st = s2;
+            latency_ms[r] = ms_between(when[r], done);
+            last_done = std::max(last_done, done);
+        }
+    });
+    size_t at = 0;
+    for (size_t r = 0; r < n_req; ++r) {
+        wait_until(when[r]);
+        uint64_t t = 0;
+        if (st == ZS_OK) st = zs_server_submit(S, ids + at, k[r], &t);
+        if (st != ZS_OK) t = 0;
+        at += k[r];
+        {
+            std::lock_guard<std::mutex> g(tmu);
+            tickets[r] = t;
+            posted = r + 1;
+        }
+        tcv.notify_all();
+    }
+    collector.join();
+    if (makespan_s) *makespan_s = std::chrono::duration<double>(last_done - t0).count();
+    if (st == ZS_OK && col_st != ZS_OK) {
+        zs::set_error("zs_server_replay: a request failed");
+        st = col_st;
+    }
+    return st;
+}
+
+extern "C" zs_status zs_serial_replay(const zs_dict *d, const uint8_t *d_comp, size_t comp_len,
+                                      const uint64_t *d_index, size_t n_lines, const double *arrival_s,
+                                      const uint64_t *ids, const size_t *k, size_t n_req, double *latency_ms,
+                                      double *makespan_s, void *stream)
+{
+    zs::clear_error();
+    if (!d || !d_index || (!d_comp && comp_len)) {
+        zs::set_error("zs_serial_replay: NULL argument");
+        return ZS_ERR_INVALID_ARG;
+    }
+    zs_status st = check_replay_args(arrival_s, ids, k, n_req, latency_ms, "zs_serial_replay");
+    if (st != ZS_OK) return st;
+    std::vector<uint64_t> h_index(n_lines + 1);
+    cudaError_t e = cudaMemcpy(h_index.data(), d_index, (n_lines + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return zs::cuda_fail(e, "zs_serial_replay: reading the line index");
+    const size_t lmax = (size_t)std::max(1, d->lmax);
+    size_t kmax = 1, bmax = 1, at = 0;
+    for (size_t r = 0; r < n_req; ++r) {
+        size_t b = 0;
+        for (size_t j = 0; j < k[r]; ++j) {
+            const uint64_t id = ids[at + j];
+            if (id >= n_lines) {
+                zs::set_error("zs_serial_replay: line id out of range");
+                return ZS_ERR_INVALID_ARG;
+            }
+            b += (size_t)(h_index[id + 1] - h_index[id]) * lmax + 1;
+        }
+        at += k[r];
+        kmax = std::max(kmax, k[r]);
+        bmax = std::max(bmax, b);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t *h_ids = nullptr, *d_ids = nullptr, *h_off = nullptr, *d_off = nullptr;
+    uint8_t *h_out = nullptr, *d_out = nullptr;
+    void *d_scr = nullptr;
+    zs::DevResult *h_res = nullptr;
+    const size_t scr = sizeof(zs::DevResult) + zs::lines_tiles(kmax) * sizeof(zs::TileState);
+    e = cudaMallocHost(reinterpret_cast<void **>(&h_ids), kmax * 8);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h_off), (kmax + 1) * 8);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h_out), bmax);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h_res), sizeof(zs::DevResult));
+    if (e == cudaSuccess) e = cudaMalloc(&d_ids, kmax * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_off, (kmax + 1) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, bmax);
+    if (e == cudaSuccess) e = cudaMalloc(&d_scr, scr);
+    const Clock::time_point t0 = Clock::now() + std::chrono::milliseconds(2);
+    Clock::time_point last = t0;
+    at = 0;
+    for (size_t r = 0; r < n_req && e == cudaSuccess; ++r) {
+        const Clock::time_point when =
+            t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(arrival_s[r]));
+        wait_until(when);
+        const size_t K = k[r];
+        if (K) {
+            std::memcpy(h_ids, ids + at, K * 8);
+            zs::DevResult *dr = reinterpret_cast<zs::DevResult *>(d_scr);
+            e = cudaMemcpyAsync(d_ids, h_ids, K * 8, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d_scr, 0, scr, s);
+            if (e == cudaSuccess)
+                e = zs::launch_lines(d, d_comp, comp_len, d_index, n_lines, d_ids, K, d_out, bmax, d_off, dr,
+                                     reinterpret_cast<zs::TileState *>(dr + 1), s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h_off, d_off, (K + 1) * 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h_res, dr, sizeof(zs::DevResult), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess && (h_res->status & (zs::kStMalformed | zs::kStTimeout))) {
+                st = (h_res->status & zs::kStTimeout) ? ZS_ERR_TIMEOUT : ZS_ERR_MALFORMED;
+                break;
+            }
+            if (e == cudaSuccess && h_res->out_len)
+                e = cudaMemcpyAsync(h_out, d_out, h_res->out_len, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        const Clock::time_point done = Clock::now();
+        latency_ms[r] = ms_between(when, done);
+        last = std::max(last, done);
+        at += K;
+    }
+    if (makespan_s) *makespan_s = std::chrono::duration<double>(last - t0).count();
+    const cudaError_t e_run = e;
+    if (h_ids) cudaFreeHost(h_ids);
+    if (h_off) cudaFreeHost(h_off);
+    if (h_out) cudaFreeHost(h_out);
+    if (h_res) cudaFreeHost(h_res);
+    if (d_ids) cudaFree(d_ids);
+    if (d_off) cudaFree(d_off);
+    if (d_out) cudaFree(d_out);
+    if (d_scr) cudaFree(d_scr);
+    if (e_run != cudaSuccess) return zs::cuda_fail(e_run, "zs_serial_replay");
+    if (st != ZS_OK) zs::set_error("zs_serial_replay: the random-access launch reported an error");
+    return st;
+}

@@ -515,6 +515,12 @@ cudaError_t launch_compress_warp(int v, const zs_dict *d, const TiledLaunch &L, 
 int decompress_variants();
 const KernelVariant *decompress_variant(int v);
 cudaError_t launch_decompress(int v, const zs_dict *d, const TiledLaunch &L, cudaStream_t s);
+// Random access (decode.cu): tile records a launch over k requested ids needs, and the launch itself
+// (out_off[k + 1] receives each line's output offset and the total).
+uint64_t lines_tiles(uint64_t k);
+cudaError_t launch_lines(const zs_dict *d, const uint8_t *comp, uint64_t comp_len, const uint64_t *index,
+                         uint64_t n_lines, const uint64_t *ids, uint64_t k, uint8_t *out, uint64_t out_cap,
+                         uint64_t *out_off, DevResult *res, TileState *tiles, cudaStream_t s);
 // The default variant over one stream: tiles and launch.
 uint64_t decompress_tiles(uint64_t n);
 uint64_t decompress_tile_bytes();

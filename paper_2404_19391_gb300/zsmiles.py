@@ -43,6 +43,16 @@ class _PlanOptions(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("use_graph", ctypes.c_int), ("tune_reps", ctypes.c_int)]
 
 
+class _ServerOptions(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_batch_ids", ctypes.c_size_t), ("max_inflight", ctypes.c_int)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("ids", ctypes.c_uint64), ("mean_batch_requests", ctypes.c_double), ("max_inflight", ctypes.c_int),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double)]
+
+
 OP_COMPRESS, OP_DECOMPRESS = 0, 1
 
 
@@ -95,6 +105,16 @@ def load_library(rebuild: bool = False) -> ctypes.CDLL:
         "zs_plan_tuned_ms": (ctypes.c_double, [vp, ctypes.c_int]),
         "zs_plan_last_ms": (ctypes.c_double, [vp]),
         "zs_plan_destroy": (None, [vp]),
+        "zs_server_create": (ctypes.c_int, [vp, vp, sz, vp, sz, ctypes.POINTER(_ServerOptions), ctypes.POINTER(vp)]),
+        "zs_server_submit": (ctypes.c_int, [vp, vp, sz, ctypes.POINTER(u64)]),
+        "zs_server_wait": (ctypes.c_int, [vp, u64, ctypes.c_double, pres]),
+        "zs_server_fetch": (ctypes.c_int, [vp, u64, vp, sz, vp]),
+        "zs_server_release": (ctypes.c_int, [vp, u64]),
+        "zs_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(_ServerStats)]),
+        "zs_server_destroy": (None, [vp]),
+        "zs_server_replay": (ctypes.c_int, [vp, vp, vp, vp, sz, vp, ctypes.POINTER(ctypes.c_double)]),
+        "zs_serial_replay": (ctypes.c_int, [vp, vp, sz, vp, sz, vp, vp, vp, sz, vp, ctypes.POINTER(ctypes.c_double),
+                                            vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,6 +317,95 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _replay_arrays(requests):
+    """requests: list of (arrival seconds, uint64 ids array). Returns the C arrays and the keep-alive list."""
+    import numpy as np
+    arr = np.ascontiguousarray([a for a, _ in requests], dtype=np.float64)
+    ks = np.ascontiguousarray([len(ids) for _, ids in requests], dtype=np.uint64)
+    ids = np.ascontiguousarray(np.concatenate([np.asarray(i, dtype=np.uint64) for _, i in requests])
+                               if requests else np.zeros(1, np.uint64))
+    lat = np.zeros(max(1, len(requests)), dtype=np.float64)
+    return arr, ids, ks, lat
+
+
+class Server:
+    """zs_server_*: continuous-batching random access over a resident store (d_comp + d_index tensors)."""
+
+    def __init__(self, d: Dictionary, d_comp: torch.Tensor, d_index: torch.Tensor, arena_bytes: int = 0,
+                 max_batch_ids: int = 0, max_inflight: int = 0):
+        self._keep = (d, d_comp, d_index)
+        self.n_lines = d_index.numel() - 1
+        opt = _ServerOptions(arena_bytes, max_batch_ids, max_inflight)
+        h = ctypes.c_void_p()
+        _check(_L().zs_server_create(d.handle, _ptr(d_comp), d_comp.numel(), _ptr(d_index), self.n_lines,
+                                     ctypes.byref(opt), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, ids) -> int:
+        import numpy as np
+        a = np.ascontiguousarray(ids, dtype=np.uint64)
+        t = ctypes.c_uint64(0)
+        _check(_L().zs_server_submit(self.handle, a.ctypes.data if a.size else None, a.size, ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_s: float = -1.0) -> Result:
+        res = _Result()
+        st = _L().zs_server_wait(self.handle, ticket, timeout_s, ctypes.byref(res))
+        if st != OK:
+            raise ZsError(st, _L().zs_last_error().decode())
+        return Result(res.out_len, res.n_lines, res.err_offset)
+
+    def fetch(self, ticket: int):
+        """Waits for the request and returns (bytes, uint64 offsets[k + 1])."""
+        import numpy as np
+        r = self.wait(ticket)
+        out = np.empty(max(1, r.out_len), dtype=np.uint8)
+        off = np.empty(r.n_lines + 1, dtype=np.uint64)
+        _check(_L().zs_server_fetch(self.handle, ticket, out.ctypes.data, out.size, off.ctypes.data))
+        return out[: r.out_len].tobytes(), off
+
+    def release(self, ticket: int):
+        _check(_L().zs_server_release(self.handle, ticket))
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(_L().zs_server_get_stats(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+    def replay(self, requests):
+        """Open-loop replay of [(arrival_s, ids)]; returns (latency_ms array, makespan_s)."""
+        arr, ids, ks, lat = _replay_arrays(requests)
+        mk = ctypes.c_double(0.0)
+        st = _L().zs_server_replay(self.handle, arr.ctypes.data, ids.ctypes.data, ks.ctypes.data, len(requests),
+                                   lat.ctypes.data, ctypes.byref(mk))
+        if st != OK:
+            raise ZsError(st, _L().zs_last_error().decode())
+        return lat[: len(requests)], mk.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _L().zs_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def zs_serial_replay(d: Dictionary, d_comp: torch.Tensor, d_index: torch.Tensor, requests, stream=None):
+    """Decompress-per-request baseline over the same open-loop arrivals; returns (latency_ms, makespan_s)."""
+    arr, ids, ks, lat = _replay_arrays(requests)
+    mk = ctypes.c_double(0.0)
+    st = _L().zs_serial_replay(d.handle, _ptr(d_comp), d_comp.numel(), _ptr(d_index), d_index.numel() - 1,
+                               arr.ctypes.data, ids.ctypes.data, ks.ctypes.data, len(requests), lat.ctypes.data,
+                               ctypes.byref(mk), _stream(stream))
+    if st != OK:
+        raise ZsError(st, _L().zs_last_error().decode())
+    return lat[: len(requests)], mk.value
 
 
 # ---- conveniences built only from the calls above ----------------------------------------------------
