@@ -264,9 +264,9 @@ void zs_plan_destroy(zs_plan *p);
  * max_inflight slots is free and the output arenas have room for it: every queued request that fits
  * joins that launch (continuous batching), so requests arriving while others are on the GPU ride the
  * next launch, and up to max_inflight launches (each with its own stream) overlap. Admission reserves
- * an upper bound of the request's decoded size (each line's compressed span times the dictionary's
- * longest pattern, plus its newline) in a device arena and in a pinned host arena; the host bytes stay
- * reserved until the result is fetched or released. A request's result is exactly what
+ * an upper bound of the request's decoded size (k ids times the store's longest decoded line, measured
+ * on the GPU when the server is made) in a device arena and in a pinned host arena; the host bytes
+ * stay reserved until the result is fetched or released. A request's result is exactly what
  * zs_decompress_lines gives for its ids alone. The batching is not in the paper.
  */
 typedef struct zs_server zs_server; /* opaque, library-owned */
@@ -285,8 +285,9 @@ typedef struct zs_server_stats {
 } zs_server_stats;
 
 /* d_comp/comp_len: the compressed store; d_index: its line index (n_lines + 1 entries, as written by
- * zs_compress or zs_build_line_index; checked, and copied to the host for admission). opt may be NULL.
- * Starts the scheduler thread. */
+ * zs_compress or zs_build_line_index). One GPU pass over the store checks that every line decodes
+ * (else ZS_ERR_MALFORMED) and finds the longest decoded line. opt may be NULL. Starts the scheduler
+ * thread. */
 zs_status zs_server_create(const zs_dict *d, const uint8_t *d_comp, size_t comp_len, const uint64_t *d_index,
                            size_t n_lines, const zs_server_options *opt, zs_server **out);
 /* Queues a request for the k line ids in ids (host array, copied); returns at once with a ticket.

@@ -7,11 +7,14 @@
 //     the batch, so requests that arrive while others are on the GPU ride the next launch. A batch is
 //     one random-access launch over the concatenated ids; up to max_inflight batches run at once, each
 //     on its own stream, so their copies and kernels overlap.
-//   - Memory admission: a request reserves an upper bound of its decoded size (compressed span of each
-//     line times the longest pattern, plus its newline) in a device arena and in a pinned host arena.
-//     After the kernel, the exact bytes are copied to the host arena, the device reservation is
-//     released, and the host bytes stay until the request's result is fetched or released.
-//   - Completion is observed by polling CUDA events; latency is arrival to the host copy's completion.
+//   - Memory admission: a request of k ids reserves k times the store's longest decoded line (found
+//     once, on the GPU, when the server is made; O(1) host work per request) in a device arena and in
+//     a pinned, mapped host arena. Behind the random-access kernel, a copy kernel reads the exact decoded size on the device
+//     and streams those bytes into the host arena with coalesced 16-byte stores, so one launch sequence
+//     and one event complete a batch (no host round trip to learn the size). The device reservation is
+//     released when the batch completes; the host bytes stay until the result is fetched or released.
+//   - Completion is observed by polling CUDA events (the scheduler yields between polls while work is
+//     in flight); latency is arrival to the completion of the batch's host copy.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -110,10 +113,60 @@ struct Slot {
     uint64_t *h_ids = nullptr, *d_ids = nullptr, *h_off = nullptr, *d_off = nullptr;
     void *d_scratch = nullptr;
     zs::DevResult *h_res = nullptr;
-    int state = 0;  // 0 free, 1 ids + kernel + offsets in flight, 2 bytes in flight
+    int state = 0;  // 0 free, 1 batch in flight
     std::shared_ptr<Batch> batch;
     size_t K = 0;
 };
+
+// Copies the r->out_len decoded bytes of a batch from the device arena to the mapped host arena (both
+// regions 256-byte aligned): 16-byte loads and stores, grid-stride.
+__global__ void copy_out_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst, const zs::DevResult *r,
+                                uint64_t cap)
+{
+    const uint64_t n = min((uint64_t)r->out_len, cap);
+    const uint64_t n16 = n >> 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint64_t i = tid; i < n16; i += stride)
+        reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+    for (uint64_t i = (n16 << 4) + tid; i < n; i += stride) dst[i] = src[i];
+}
+
+// The longest decoded line of a store (with its '\n'), and a count of index entries or lines that do
+// not decode: one thread per line, the same escape rule as every decoder here (Sec. IV-D2).
+__global__ void line_max_kernel(const uint8_t *__restrict__ comp, uint64_t comp_len, const uint64_t *__restrict__ index,
+                                uint64_t n_lines, const uint8_t *__restrict__ plen, unsigned long long *out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long mx = 0, bad = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_lines; i += stride) {
+        const uint64_t a = index[i];
+        uint64_t b = index[i + 1];
+        if (a > b || b > comp_len) {
+            ++bad;
+            continue;
+        }
+        if (b > a && comp[b - 1] == '\n') --b;
+        uint64_t len = 1;
+        bool lit = false, ok = true;
+        for (uint64_t p = a; p < b; ++p) {
+            const uint8_t c = comp[p];
+            if (lit) {
+                len += 1;
+                lit = false;
+            } else if (c == ' ') {
+                lit = true;
+            } else {
+                ok &= plen[c] != 0;
+                len += plen[c];
+            }
+        }
+        if (!ok || lit) ++bad;
+        mx = max(mx, (unsigned long long)len);
+    }
+    if (mx) atomicMax(out, mx);
+    if (bad) atomicAdd(out + 1, bad);
+}
 
 double ms_between(Clock::time_point a, Clock::time_point b)
 {
@@ -139,11 +192,12 @@ struct zs_server {
     size_t comp_len = 0;
     const uint64_t *index = nullptr;
     size_t n_lines = 0;
-    std::vector<uint64_t> h_index;  // host copy: admission bounds and id checks
+    size_t max_line = 1;  // longest decoded line: a request of k ids reserves k * max_line bytes
     zs_server_options opt{};
 
     uint8_t *d_arena = nullptr;
-    uint8_t *h_arena = nullptr;
+    uint8_t *h_arena = nullptr;     // pinned, mapped
+    uint8_t *h_arena_dev = nullptr;  // its device address
     RangeAlloc dev_alloc, host_alloc;
     std::vector<Slot> slots;
     size_t scratch_tiles = 0;
@@ -167,14 +221,49 @@ struct zs_server {
 
     void loop();
     bool admit(Slot &s);
-    void stage2(Slot &s);
     void finish(Slot &s);
     void fail_batch(Slot &s, zs_status st, const std::string &msg);
 };
 
 namespace {
 
-cudaError_t issue_stage1(zs_server *S, Slot &s)
+unsigned copy_blocks(size_t bound)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    const size_t want = (bound / 16 + 255) / 256;
+    return (unsigned)std::max<size_t>(1, std::min<size_t>(want, (size_t)sms * 4));
+}
+
+// Longest decoded line of the store (checks the index and the store on the way).
+zs_status store_max_line(const zs_dict *d, const uint8_t *comp, size_t comp_len, const uint64_t *index,
+                         size_t n_lines, size_t *max_line, const char *what)
+{
+    unsigned long long *dv = nullptr, hv[2] = {0, 0};
+    cudaError_t e = cudaMalloc(&dv, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(dv, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess && n_lines) {
+        const uint64_t blocks = std::min<uint64_t>((n_lines + 255) / 256, 4096);
+        line_max_kernel<<<(unsigned)blocks, 256>>>(comp, comp_len, index, n_lines, d->d_dec, dv);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(hv, dv, sizeof hv, cudaMemcpyDeviceToHost);
+    if (dv) cudaFree(dv);
+    if (e != cudaSuccess) return zs::cuda_fail(e, what);
+    if (hv[1]) {
+        zs::set_error(std::string(what) + ": " + std::to_string(hv[1]) + " lines of the store do not decode");
+        return ZS_ERR_MALFORMED;
+    }
+    *max_line = std::max<size_t>(1, (size_t)hv[0]);
+    return ZS_OK;
+}
+
+cudaError_t issue_batch(zs_server *S, Slot &s)
 {
     const size_t K = s.K;
     cudaError_t e = cudaMemcpyAsync(s.d_ids, s.h_ids, K * sizeof(uint64_t), cudaMemcpyHostToDevice, s.st);
@@ -186,6 +275,11 @@ cudaError_t issue_stage1(zs_server *S, Slot &s)
     if (e == cudaSuccess)
         e = zs::launch_lines(S->d, S->comp, S->comp_len, S->index, S->n_lines, s.d_ids, K,
                              S->d_arena + s.batch->dev_off, s.batch->bound, s.d_off, dr, tiles, s.st);
+    if (e == cudaSuccess) {
+        copy_out_kernel<<<copy_blocks(s.batch->bound), 256, 0, s.st>>>(
+            S->d_arena + s.batch->dev_off, S->h_arena_dev + s.batch->host_off, dr, s.batch->bound);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s.h_off, s.d_off, (K + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_res, dr, sizeof(zs::DevResult), cudaMemcpyDeviceToHost, s.st);
@@ -234,7 +328,7 @@ bool zs_server::admit(Slot &s)
     ++n_batches;
     batch_reqs += take.size();
     n_ids += K;
-    cudaError_t e = issue_stage1(this, s);
+    cudaError_t e = issue_batch(this, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail_batch(s, ZS_ERR_CUDA, std::string("zs_server: launch failed: ") + cudaGetErrorString(e));
@@ -267,8 +361,8 @@ void zs_server::fail_batch(Slot &s, zs_status st, const std::string &msg)
     done_cv.notify_all();
 }
 
-// Offsets arrived: check the launch, hand out per-request offsets, copy the exact bytes back.
-void zs_server::stage2(Slot &s)
+// The batch's launches are done: check them, hand out per-request offsets and bytes.
+void zs_server::finish(Slot &s)
 {
     auto b = s.batch;
     const zs::DevResult r = *s.h_res;
@@ -277,6 +371,7 @@ void zs_server::stage2(Slot &s)
                    "zs_server: the random-access launch reported an error");
         return;
     }
+    const Clock::time_point now = Clock::now();
     for (Request *q : b->reqs) {
         const size_t k = q->ids.size();
         const uint64_t base = s.h_off[q->first];
@@ -284,27 +379,9 @@ void zs_server::stage2(Slot &s)
         for (size_t j = 0; j <= k; ++j) q->off[j] = s.h_off[q->first + j] - base;
         q->byte_off = base;
         q->byte_len = q->off[k];
-    }
-    cudaError_t e = cudaSuccess;
-    if (r.out_len)
-        e = cudaMemcpyAsync(h_arena + b->host_off, d_arena + b->dev_off, r.out_len, cudaMemcpyDeviceToHost, s.st);
-    if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        fail_batch(s, ZS_ERR_CUDA, std::string("zs_server: copy failed: ") + cudaGetErrorString(e));
-        return;
-    }
-    s.state = 2;
-}
-
-void zs_server::finish(Slot &s)
-{
-    auto b = s.batch;
-    const Clock::time_point now = Clock::now();
-    for (Request *r : b->reqs) {
-        r->state = 2;
-        r->done_at = now;
-        lat_ms.push_back(ms_between(r->arrival, now));
+        q->state = 2;
+        q->done_at = now;
+        lat_ms.push_back(ms_between(q->arrival, now));
         ++n_completed;
     }
     dev_alloc.release(b->dev_off, b->bound);
@@ -327,8 +404,6 @@ void zs_server::loop()
             if (q != cudaSuccess) {
                 cudaGetLastError();
                 fail_batch(s, ZS_ERR_CUDA, std::string("zs_server: ") + cudaGetErrorString(q));
-            } else if (s.state == 1) {
-                stage2(s);
             } else {
                 finish(s);
             }
@@ -342,8 +417,10 @@ void zs_server::loop()
         max_inflight_seen = std::max(max_inflight_seen, inflight);
         if (stop && inflight == 0) break;
         if (progressed) continue;
-        if (busy || inflight) {
-            cv.wait_for(lk, std::chrono::microseconds(20));  // poll the in-flight events
+        if (busy || inflight) {  // poll the in-flight events; let submitters in between polls
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
         } else {
             const uint64_t seen = changes;  // the queue head waits for arena room or a new request
             cv.wait(lk, [&] { return stop || changes != seen; });
@@ -378,18 +455,14 @@ extern "C" zs_status zs_server_create(const zs_dict *d, const uint8_t *d_comp, s
     S->opt.arena_bytes = opt && opt->arena_bytes ? opt->arena_bytes : (size_t)512 << 20;
     S->opt.max_batch_ids = opt && opt->max_batch_ids ? opt->max_batch_ids : (size_t)1 << 20;
     S->opt.max_inflight = opt && opt->max_inflight > 0 ? opt->max_inflight : 4;
-    S->h_index.resize(n_lines + 1);
-    e = cudaMemcpy(S->h_index.data(), d_index, (n_lines + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return zs::cuda_fail(e, "zs_server_create: reading the line index");
-    for (size_t i = 0; i < n_lines; ++i)
-        if (S->h_index[i] > S->h_index[i + 1] || S->h_index[i + 1] > comp_len) {
-            zs::set_error("zs_server_create: line index is not a valid index of the store");
-            return ZS_ERR_INVALID_ARG;
-        }
+    zs_status st = store_max_line(d, d_comp, comp_len, d_index, n_lines, &S->max_line, "zs_server_create");
+    if (st != ZS_OK) return st;
     const size_t K = S->opt.max_batch_ids;
     S->scratch_tiles = zs::lines_tiles(K);
     e = cudaMalloc(&S->d_arena, S->opt.arena_bytes);
-    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&S->h_arena), S->opt.arena_bytes);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void **>(&S->h_arena), S->opt.arena_bytes, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&S->h_arena_dev), S->h_arena, 0);
     S->slots.resize(S->opt.max_inflight);
     for (Slot &s : S->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
@@ -469,16 +542,13 @@ extern "C" zs_status zs_server_submit(zs_server *S, const uint64_t *ids, size_t 
     auto r = std::make_unique<Request>();
     r->ids.assign(ids, ids + k);
     r->arrival = now;
-    size_t bound = 0;
-    const size_t lmax = (size_t)std::max(1, S->d->lmax);
-    for (size_t j = 0; j < k; ++j) {
-        const uint64_t id = ids[j];
-        if (id >= S->n_lines) {
-            zs::set_error("zs_server_submit: line id " + std::to_string(id) + " out of range");
-            return ZS_ERR_INVALID_ARG;
-        }
-        bound += (size_t)(S->h_index[id + 1] - S->h_index[id]) * lmax + 1;
+    uint64_t top = 0;
+    for (size_t j = 0; j < k; ++j) top = std::max(top, ids[j]);
+    if (k && top >= S->n_lines) {
+        zs::set_error("zs_server_submit: line id " + std::to_string(top) + " out of range");
+        return ZS_ERR_INVALID_ARG;
     }
+    const size_t bound = k * S->max_line;
     r->bound = bound;
     if (RangeAlloc::round(bound) > S->opt.arena_bytes) {
         zs::set_error("zs_server_submit: the request's output bound exceeds the arena");
@@ -751,32 +821,28 @@ extern "C" zs_status zs_serial_replay(const zs_dict *d, const uint8_t *d_comp, s
     }
     zs_status st = check_replay_args(arrival_s, ids, k, n_req, latency_ms, "zs_serial_replay");
     if (st != ZS_OK) return st;
-    std::vector<uint64_t> h_index(n_lines + 1);
-    cudaError_t e = cudaMemcpy(h_index.data(), d_index, (n_lines + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return zs::cuda_fail(e, "zs_serial_replay: reading the line index");
-    const size_t lmax = (size_t)std::max(1, d->lmax);
-    size_t kmax = 1, bmax = 1, at = 0;
+    size_t max_line = 1;
+    st = store_max_line(d, d_comp, comp_len, d_index, n_lines, &max_line, "zs_serial_replay");
+    if (st != ZS_OK) return st;
+    size_t kmax = 1, at = 0;
     for (size_t r = 0; r < n_req; ++r) {
-        size_t b = 0;
-        for (size_t j = 0; j < k[r]; ++j) {
-            const uint64_t id = ids[at + j];
-            if (id >= n_lines) {
+        for (size_t j = 0; j < k[r]; ++j)
+            if (ids[at + j] >= n_lines) {
                 zs::set_error("zs_serial_replay: line id out of range");
                 return ZS_ERR_INVALID_ARG;
             }
-            b += (size_t)(h_index[id + 1] - h_index[id]) * lmax + 1;
-        }
         at += k[r];
         kmax = std::max(kmax, k[r]);
-        bmax = std::max(bmax, b);
     }
+    const size_t bmax = kmax * max_line;
+    cudaError_t e = cudaSuccess;
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t *h_ids = nullptr, *d_ids = nullptr, *h_off = nullptr, *d_off = nullptr;
     uint8_t *h_out = nullptr, *d_out = nullptr;
     void *d_scr = nullptr;
     zs::DevResult *h_res = nullptr;
     const size_t scr = sizeof(zs::DevResult) + zs::lines_tiles(kmax) * sizeof(zs::TileState);
-    e = cudaMallocHost(reinterpret_cast<void **>(&h_ids), kmax * 8);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h_ids), kmax * 8);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h_off), (kmax + 1) * 8);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h_out), bmax);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h_res), sizeof(zs::DevResult));
