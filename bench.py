@@ -142,6 +142,24 @@ def dist_env():
     return rank, world, local
 
 
+def rank_first_line(rank: int, lines: int) -> int:
+    """First line of a rank's replica: ranks take consecutive, disjoint line ranges of one synthetic stream."""
+    return rank * lines
+
+
+def reduce_over_ranks(maxes, sums, device):
+    """Max over ranks of the timing values and sum of the work values (identity with one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(x) for x in maxes], [float(x) for x in sums]
+    a = torch.tensor(list(maxes), dtype=torch.float64, device=device)
+    b = torch.tensor(list(sums), dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return a.tolist(), b.tolist()
+
+
 def workload_desc(lines: int, nbytes: int) -> str:
     return (f"plain codec, large single stream: {lines:,} synthetic drug-like SMILES lines "
             f"({nbytes / 1e6:.1f} MB, mean {nbytes / max(1, lines):.1f} B/line incl. newline), one shard per launch")
@@ -211,6 +229,137 @@ def run_reference(args):
 # GPU path
 # ---------------------------------------------------------------------------------------------------------
 
+def _aligned_shards(zs, specs, dev):
+    """Generates [(shape, count)] into one pinned buffer (each shard 16-byte aligned), copies it to the
+    device; returns (device slices, sizes, line counts)."""
+    import torch
+    sizes = [synth.lines_size(sh, 0, c) for sh, c in specs]
+    spans = [(n + 15) & ~15 for n in sizes]
+    host = torch.empty(max(16, sum(spans)), dtype=torch.uint8, pin_memory=True)
+    at = 0
+    for (sh, c), n, sp in zip(specs, sizes, spans):
+        synth.generate_into(sh, 0, c, host.data_ptr() + at, n)
+        at += sp
+    big = host.to(dev)
+    ins, at = [], 0
+    for n, sp in zip(sizes, spans):
+        ins.append(big[at:at + n])
+        at += sp
+    return ins, sizes, [c for _, c in specs]
+
+
+def _time_ms(stream, fn, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_batched(zs, d, dev, reps: int):
+    """64 shards (log-uniform 1k-5M lines, per-shard mean length 25-70) through one autotuned,
+    graph-captured plan, against one zs_compress / zs_decompress launch per shard, same buffers."""
+    import torch
+    specs = synth.batched_shards()
+    ins, sizes, counts = _aligned_shards(zs, specs, dev)
+    outs = [torch.empty(zs.zs_compress_bound(n), dtype=torch.uint8, device=dev) for n in sizes]
+    idxs = [torch.empty(c + 2, dtype=torch.int64, device=dev) for c in counts]
+    shards = list(zip(ins, outs, idxs))
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.time()
+    plan = zs.Plan(d, zs.OP_COMPRESS, shards, flags=zs.PREPROCESS, variant=-1, tune_reps=2)
+    tune_s = time.time() - t0
+    res = plan.run()
+    for _ in range(2):
+        plan.run()
+    ms_b = _time_ms(stream, plan.run, reps)
+    kern_b = plan.last_ms
+    ref = [o[: r.out_len].clone() for o, r in zip(outs, res)]
+
+    def per_shard_c():
+        for x, o, i in shards:
+            zs.zs_compress(d, x, zs.PREPROCESS, o, i)
+    per_shard_c()
+    ms_p = _time_ms(stream, per_shard_c, reps)
+    same_c = all(torch.equal(o[: r.out_len], c) for o, r, c in zip(outs, res, ref))
+    del ref
+    comps = [o[: r.out_len] for o, r in zip(outs, res)]
+    douts = [torch.empty(d.decompress_bound(c.numel()) // 2 + n + 64, dtype=torch.uint8, device=dev)
+             for c, n in zip(comps, sizes)]
+    dsh = [(c, o, None) for c, o in zip(comps, douts)]
+    dplan = zs.Plan(d, zs.OP_DECOMPRESS, dsh, variant=-1, tune_reps=2)
+    dres = dplan.run()
+    ms_db = _time_ms(stream, dplan.run, reps)
+    dref = [o[: r.out_len].clone() for o, r in zip(douts, dres)]
+
+    def per_shard_d():
+        for c, o, _ in dsh:
+            zs.zs_decompress(d, c, o)
+    per_shard_d()
+    ms_dp = _time_ms(stream, per_shard_d, reps)
+    same_d = all(torch.equal(o[: r.out_len], x) for o, r, x in zip(douts, dres, dref))
+    nbytes, cbytes = sum(sizes), sum(c.numel() for c in comps)
+    out = {
+        "workload": f"{len(specs)} shards, {sum(counts):,} synthetic lines, {nbytes / 1e9:.2f} GB, line counts "
+                    "log-uniform 1k-5M, per-shard mean length 25-70",
+        "compress": {"batched_ms": ms_b, "batched_kernel_ms": kern_b, "per_shard_ms": ms_p,
+                     "speedup": ms_p / ms_b, "batched_gbps_in": nbytes / ms_b / 1e6,
+                     "per_shard_gbps_in": nbytes / ms_p / 1e6, "variant": zs.zs_kernel_variant_name(0, plan.variant),
+                     "tuned_ms": {zs.zs_kernel_variant_name(0, v): plan.tuned_ms(v)
+                                  for v in range(zs.zs_kernel_variants(0))},
+                     "autotune_s": tune_s, "identical_output": bool(same_c)},
+        "decompress": {"batched_ms": ms_db, "per_shard_ms": ms_dp, "speedup": ms_dp / ms_db,
+                       "batched_gbps_in": cbytes / ms_db / 1e6, "per_shard_gbps_in": cbytes / ms_dp / 1e6,
+                       "variant": zs.zs_kernel_variant_name(1, dplan.variant),
+                       "tuned_ms": {zs.zs_kernel_variant_name(1, v): dplan.tuned_ms(v)
+                                    for v in range(zs.zs_kernel_variants(1))},
+                       "identical_output": bool(same_d)},
+        "how": "batched = zs_plan_run of an autotuned plan replaying one CUDA graph (clear, one persistent "
+               "launch over all shards, result copy); per-shard = one zs_compress / zs_decompress call per shard; "
+               f"wall time per pass with CUDA events, mean of {reps} passes",
+    }
+    plan.close()
+    dplan.close()
+    return out
+
+
+def bench_serving(zs, d, dev, lines: int, n_req: int, rates):
+    """Open-loop Poisson request streams (1-100,000 random ids per request, log-uniform) against a
+    resident store of `lines` lines: the continuous-batching server vs one launch per request."""
+    import torch
+    nbytes = synth.lines_size(synth.CFG4, 0, lines)
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    synth.generate_into(synth.CFG4, 0, lines, host.data_ptr(), nbytes)
+    x = host.to(dev)
+    comp, idx, _ = zs.compress(d, x)
+    comp, idx = comp.clone(), idx.clone()
+    del x
+    srv = zs.Server(d, comp, idx, arena_bytes=2 << 30, max_inflight=4)
+    rows = []
+    for rate in rates:
+        reqs = synth.requests(n_req, 7, lines, rate=float(rate))
+        nid = sum(len(i) for _, i in reqs)
+        lat, mk = srv.replay(reqs)
+        lat2, mk2 = zs.zs_serial_replay(d, comp, idx, reqs)
+        rows.append({"rate_req_s": rate, "requests": n_req, "ids": nid,
+                     "server": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                "lines_per_s": nid / mk},
+                     "per_request": {"p50_ms": float(np.percentile(lat2, 50)),
+                                     "p99_ms": float(np.percentile(lat2, 99)), "lines_per_s": nid / mk2}})
+    st = srv.stats()
+    srv.close()
+    return {"workload": f"resident store of {lines:,} synthetic lines ({nbytes / 1e9:.2f} GB raw, "
+                        f"{comp.numel() / 1e9:.2f} GB compressed + {idx.numel() * 8 / 1e9:.2f} GB index)",
+            "rates": rows, "mean_requests_per_launch": st["mean_batch_requests"],
+            "max_inflight": st["max_inflight"],
+            "how": "zs_server_replay (continuous batching, 4 launches in flight, memory admission) vs "
+                   "zs_serial_replay (one random-access launch + wait + copy per request, arrival order); "
+                   "latency from scheduled arrival to result bytes in host memory"}
+
+
 def run_gpu(args):
     import torch
     from paper_2404_19391_gb300 import zsmiles as zs
@@ -227,7 +376,7 @@ def run_gpu(args):
 
     shape = synth.CFG1
     lines = args.lines
-    first = rank * lines
+    first = rank_first_line(rank, lines)
     nbytes = synth.lines_size(shape, first, lines)
     host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     synth.generate_into(shape, first, lines, host_in.data_ptr(), nbytes)
@@ -327,17 +476,7 @@ def run_gpu(args):
     clocks.stop()
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
 
-    ms_step = ms_total / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, e2e_ms = float(t[0]), float(t[1])
-        nb = torch.tensor([float(nbytes)], dtype=torch.float64, device=dev)
-        dist.all_reduce(nb, op=dist.ReduceOp.SUM)
-        total_bytes = float(nb[0])
-    else:
-        total_bytes = float(nbytes)
+    (ms_step, e2e_ms), (total_bytes,) = reduce_over_ranks([ms_total / args.steps, e2e_ms], [nbytes], dev)
 
     value = total_bytes / (ms_step * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
@@ -348,7 +487,7 @@ def run_gpu(args):
     dec_bytes = sizes["comp"] + sizes["dec"]                            # read compressed, write decoded
     achieved_c = comp_bytes / (kc * 1e-3) / 1e9
     achieved_d = dec_bytes / (kd * 1e-3) / 1e9
-    traffic = kernel_traffic("compress_kernel")
+    traffic = kernel_traffic("compress_warp_kernel")
 
     if rank == 0:
         line = {
@@ -369,7 +508,7 @@ def run_gpu(args):
                            "decoded stream and random-access output, every step"},
             "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved_c, "peak": peak, "unit": "GB/s",
-                         "frac": achieved_c / peak, "traffic": traffic, "kernel": "compress_kernel",
+                         "frac": achieved_c / peak, "traffic": traffic, "kernel": "compress_warp_kernel",
                          "peak_kind": f"{peak_kind} (copy, MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": comp_bytes, "kernel_ms": kc},
@@ -382,6 +521,11 @@ def run_gpu(args):
             "random_access": {"ids": RA_IDS, "kernel_ms": kl, "lines_per_s": RA_IDS / (kl * 1e-3),
                               "p99_ms": float(np.percentile(kms["lines"], 99))},
         }
+        if world == 1 and not args.no_batched:
+            line["batched"] = bench_batched(zs, d, dev, reps=5)
+        if world == 1 and not args.no_serving:
+            line["serving"] = bench_serving(zs, d, dev, args.serve_lines, args.serve_requests,
+                                            [int(r) for r in args.serve_rates.split(",")])
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_sample_lines, shape)
         print(json.dumps(line), flush=True)
@@ -398,9 +542,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lines", type=int, default=synth.CFG1_LINES)
     ap.add_argument("--e2e-steps", type=int, default=40)
-    ap.add_argument("--cpu-sample-lines", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample-lines", type=int, default=synth.CFG1_LINES)
     ap.add_argument("--ref-sample-lines", type=int, default=400_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-shard batched-form comparison")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-form request replay")
+    ap.add_argument("--serve-lines", type=int, default=synth.CFG4_LINES)
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-rates", default="1000,10000,100000")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
