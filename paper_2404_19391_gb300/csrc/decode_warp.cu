@@ -46,7 +46,9 @@ struct DwArgs {
     int64_t stall_tile;
 };
 
-template <class Geo>
+// NARROW: every pattern is at most 7 bytes, so a pattern and its length fit one 64-bit table entry and
+// the word-wise paths below apply; otherwise the byte loops run.
+template <class Geo, bool NARROW>
 struct DW {
     static constexpr int kDW = Geo::kWarps;
     static constexpr int kDNTW = 32 * kDW;
@@ -76,9 +78,12 @@ struct DW {
         DWarpMem *M;
         const uint8_t *plen;
         const uint8_t *pat;
+        const uint32_t *szt;  // NARROW: decoded size per byte ('\n': 1, ' ': 0, not a symbol: 1 << 16)
+        const uint64_t *pat8;  // NARROW: pattern bytes, length in byte 7 ('\n' -> "\n")
         uint32_t lane;
         uint32_t *status;
     };
+    static constexpr uint32_t kBad = 1u << 16;  // szt entry of a byte that is no symbol
 
     static __device__ __forceinline__ void stage_d(const DCtx &C, DSlot &S, uint64_t t)
     {
@@ -96,30 +101,12 @@ struct DW {
         for (uint32_t j = nbulk + C.lane; j < nown; j += 32) S.in[j] = A.in[base + j];
     }
 
-    // Decoded size of each lane's slice, warp scan, publication of the tile's aggregate.
-    static __device__ __forceinline__ void sizes_d(const DCtx &C, DSlot &S, uint64_t t)
+    // Byte loop over the slice [p0, p1): decoded bytes and newlines, noting malformed bytes.
+    static __device__ __forceinline__ void slice_bytes(const DCtx &C, const DSlot &S, uint64_t base, uint32_t p0,
+                                                       uint32_t p1, bool lit, uint32_t *outb_, uint32_t *nls_,
+                                                       bool *lit_end)
     {
         const ShardView &A = *C.A;
-        const uint32_t lane = C.lane;
-        const uint64_t base = t * (uint64_t)kDTile;
-        const uint32_t nown = S.nown;
-        uint32_t carry = 0;  // spaces immediately before the tile
-        if (lane == 0)
-            while (base > carry && A.in[base - 1 - carry] == kEsc) ++carry;
-        carry = __shfl_sync(kFullD, carry, 0);
-        const uint32_t p0 = min(nown, lane * (uint32_t)kDLane);
-        const uint32_t p1 = min(nown, p0 + (uint32_t)kDLane);
-        uint32_t run = 0;
-        {
-            int q = (int)p0 - 1;
-            while (q >= 0 && S.in[q] == kEsc) {
-                ++run;
-                --q;
-            }
-            if (q < 0) run += carry;
-        }
-        bool lit = (run & 1u) != 0;
-        const bool lit_start = lit;
         uint32_t outb = 0, nls = 0;
         for (uint32_t p = p0; p < p1; ++p) {
             const uint8_t b = S.in[p];
@@ -145,6 +132,78 @@ struct DW {
                 outb += l;
             }
         }
+        *outb_ = outb;
+        *nls_ = nls;
+        *lit_end = lit;
+    }
+
+    // The same sizes a 4-byte word at a time: four table lookups per word without a space; words with a
+    // space (or after an escaping one) go byte by byte. Returns false if the slice holds a malformed byte
+    // (the caller then reruns the byte loop, which notes where).
+    static __device__ __forceinline__ bool slice_words(const DCtx &C, const DSlot &S, uint32_t p0, uint32_t p1,
+                                                       bool lit, uint32_t *outb_, uint32_t *nls_, bool *lit_end)
+    {
+        const uint32_t *szt = C.szt;
+        uint32_t acc = 0, nls = 0;
+        bool bad = false;
+        auto one = [&](uint32_t b) {
+            if (lit) {
+                bad |= (b == kNl);
+                acc += 1;
+                lit = false;
+            } else if (b == kEsc) {
+                lit = true;
+            } else {
+                acc += szt[b];
+            }
+            nls += (b == kNl);
+        };
+        uint32_t p = p0;
+        const uint32_t pw = p0 + ((p1 - p0) & ~3u);
+        for (; p < pw; p += 4) {
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(S.in + p);
+            if (lit || __vcmpeq4(w, 0x20202020u)) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) one((w >> (8 * j)) & 255u);
+                continue;
+            }
+            acc += szt[w & 255u] + szt[(w >> 8) & 255u] + szt[(w >> 16) & 255u] + szt[w >> 24];
+            nls += __popc(__vcmpeq4(w, 0x0A0A0A0Au)) >> 3;
+        }
+        for (; p < p1; ++p) one(S.in[p]);
+        *outb_ = acc & 0xFFFFu;
+        *nls_ = nls;
+        *lit_end = lit;
+        return !bad && (acc >> 16) == 0;
+    }
+
+    // Decoded size of each lane's slice, warp scan, publication of the tile's aggregate.
+    static __device__ __forceinline__ void sizes_d(const DCtx &C, DSlot &S, uint64_t t)
+    {
+        const ShardView &A = *C.A;
+        const uint32_t lane = C.lane;
+        const uint64_t base = t * (uint64_t)kDTile;
+        const uint32_t nown = S.nown;
+        uint32_t carry = 0;  // spaces immediately before the tile
+        if (lane == 0)
+            while (base > carry && A.in[base - 1 - carry] == kEsc) ++carry;
+        carry = __shfl_sync(kFullD, carry, 0);
+        const uint32_t p0 = min(nown, lane * (uint32_t)kDLane);
+        const uint32_t p1 = min(nown, p0 + (uint32_t)kDLane);
+        uint32_t run = 0;
+        {
+            int q = (int)p0 - 1;
+            while (q >= 0 && S.in[q] == kEsc) {
+                ++run;
+                --q;
+            }
+            if (q < 0) run += carry;
+        }
+        const bool lit_start = (run & 1u) != 0;
+        uint32_t outb = 0, nls = 0;
+        bool lit = false;
+        if (!NARROW || !slice_words(C, S, p0, p1, lit_start, &outb, &nls, &lit))
+            slice_bytes(C, S, base, p0, p1, lit_start, &outb, &nls, &lit);
         if (lit && p1 > p0 && base + p1 == A.n) {  // the stream ends in an unpaired escape
             note_error_offset(A.res, A.n - 1);
             atomicOr(C.status, kStMalformed);
@@ -161,6 +220,77 @@ struct DW {
             if ((int64_t)t != C.P->stall_tile) publish(&A.tiles[t], t == 0 ? 2u : 1u, total, totn);
         }
         __syncwarp();
+    }
+
+    // Word-wise expansion into the staging buffer (NARROW). Each lane funnels its pattern bytes into
+    // aligned 32-bit stores. Its first word may start below its own first byte: those low bytes are
+    // written as zeros, and belong to an earlier lane's last, partial word, which every lane writes byte
+    // by byte only after the whole warp's word stores (the caller's second phase, expand_tail).
+    struct Funnel {
+        uint32_t a, n, wpos, head, pos0;
+    };
+
+    static __device__ __forceinline__ void expand_words(const DCtx &C, const DSlot &S, uint32_t p0, uint32_t p1,
+                                                        bool lit, uint32_t pos, Funnel &F)
+    {
+        uint8_t *ost = C.M->ost;
+        const uint64_t *pat8 = C.pat8;
+        uint32_t a = 0, n = pos & 3u, wpos = pos & ~3u;
+        auto push = [&](uint32_t lo, uint32_t hi, uint32_t l) {
+            const uint32_t sh = 8u * n;
+            const uint32_t w0 = a | (lo << sh);
+            const uint32_t w1 = __funnelshift_l(lo, hi, sh);
+            const uint32_t w2 = __funnelshift_l(hi, 0u, sh);
+            const uint32_t tot = n + l;
+            if (tot >= 4) *reinterpret_cast<uint32_t *>(ost + wpos) = w0;
+            if (tot >= 8) *reinterpret_cast<uint32_t *>(ost + wpos + 4) = w1;
+            const uint32_t k = tot >> 2;
+            a = k == 0 ? w0 : (k == 1 ? w1 : w2);
+            n = tot & 3u;
+            wpos += 4u * k;
+        };
+        auto sym = [&](uint32_t b) {
+            const uint64_t e = pat8[b];
+            push((uint32_t)e, (uint32_t)(e >> 32) & 0x00FFFFFFu, (uint32_t)(e >> 56));
+        };
+        auto one = [&](uint32_t b) {
+            if (lit) {
+                push(b, 0u, 1u);
+                lit = false;
+            } else if (b == kEsc) {
+                lit = true;
+            } else {
+                sym(b);
+            }
+        };
+        uint32_t p = p0;
+        const uint32_t pw = p0 + ((p1 - p0) & ~3u);
+        for (; p < pw; p += 4) {
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(S.in + p);
+            if (lit || __vcmpeq4(w, 0x20202020u)) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) one((w >> (8 * j)) & 255u);
+                continue;
+            }
+            sym(w & 255u);
+            sym((w >> 8) & 255u);
+            sym((w >> 16) & 255u);
+            sym(w >> 24);
+        }
+        for (; p < p1; ++p) one(S.in[p]);
+        F.a = a;
+        F.n = n;
+        F.wpos = wpos;
+        F.head = pos & 3u;
+        F.pos0 = pos & ~3u;
+    }
+
+    // Second phase: the lane's last, partial word, byte by byte (never below its own first byte).
+    static __device__ __forceinline__ void expand_tail(const DCtx &C, const Funnel &F)
+    {
+        uint8_t *ost = C.M->ost;
+        const uint32_t j0 = F.wpos == F.pos0 ? F.head : 0u;
+        for (uint32_t j = j0; j < F.n; ++j) ost[F.wpos + j] = (uint8_t)(F.a >> (8 * j));
     }
 
     template <bool STAGED>
@@ -210,8 +340,16 @@ struct DW {
         const uint32_t nown = S.nown;
         const uint32_t p0 = min(nown, lane * (uint32_t)kDLane);
         const uint32_t p1 = min(nown, p0 + (uint32_t)kDLane);
-        if (staged) expand_slice<true>(C, S, p0, p1, S.lit0[lane] != 0, S.lane_off[lane], ea, so);
-        else expand_slice<false>(C, S, p0, p1, S.lit0[lane] != 0, S.lane_off[lane], ea, so);
+        if (NARROW && staged) {
+            Funnel F;
+            expand_words(C, S, p0, p1, S.lit0[lane] != 0, so + S.lane_off[lane], F);
+            __syncwarp();
+            expand_tail(C, F);
+        } else if (staged) {
+            expand_slice<true>(C, S, p0, p1, S.lit0[lane] != 0, S.lane_off[lane], ea, so);
+        } else {
+            expand_slice<false>(C, S, p0, p1, S.lit0[lane] != 0, S.lane_off[lane], ea, so);
+        }
         __syncwarp();
         if (staged) {
             uint8_t *gdst = A.out + ea - so;  // 16-byte aligned
@@ -246,6 +384,8 @@ struct DW {
         C.M = &M;
         C.plen = tab;
         C.pat = tab + 256;
+        C.szt = reinterpret_cast<const uint32_t *>(tab + kDecBytes);
+        C.pat8 = reinterpret_cast<const uint64_t *>(tab + kDecBytes + 1024);
         C.lane = lane;
         C.status = &P->g->status;
         if (threadIdx.x == 0) mbar_init(&tab_bar, 1);
@@ -258,9 +398,27 @@ struct DW {
             mbar_arrive_tx(&tab_bar, kDecBytes);
             bulk_g2s(tab, P->dec, kDecBytes, &tab_bar);
         }
-        if (!mbar_wait_bounded(&tab_bar, 0, P->limit_ns, C.status)) {
+        const bool staged_ok = mbar_wait_bounded(&tab_bar, 0, P->limit_ns, C.status);
+        if (!__syncthreads_and(staged_ok)) {
             mbar_wait_bounded(&tab_bar, 0, P->limit_ns, C.status);
             return;
+        }
+        if (NARROW) {  // word-path tables, built from the staged plen / pat tables
+            uint32_t *szt = reinterpret_cast<uint32_t *>(tab + kDecBytes);
+            uint64_t *pat8 = reinterpret_cast<uint64_t *>(tab + kDecBytes + 1024);
+            for (uint32_t b = threadIdx.x; b < 256; b += blockDim.x) {
+                const uint32_t l = tab[b];
+                uint64_t e = 0;
+                if (b == kNl) {
+                    e = (uint64_t)kNl | (1ull << 56);
+                } else if (l) {
+                    for (uint32_t k = 0; k < l; ++k) e |= (uint64_t)tab[256 + 16 * b + k] << (8 * k);
+                    e |= (uint64_t)l << 56;
+                }
+                szt[b] = b == kNl ? 1u : (l ? l : kBad);
+                pat8[b] = e;
+            }
+            __syncthreads();
         }
         uint32_t ph = 0, s = 0;
         bool pending = false;
@@ -298,16 +456,38 @@ struct DW {
     }
 };
 
-template <class Geo>
+template <class Geo, bool NARROW>
 __global__ void __launch_bounds__(Geo::kWarps * 32, 1) decompress_warp_kernel(const DwArgs P)
 {
-    DW<Geo>::run(&P);
+    DW<Geo, NARROW>::run(&P);
 }
 
 // Compiled geometries; variant 0 is the default.
 using DwV0 = DwGeom<28, 44>;
 using DwV1 = DwGeom<32, 36>;
 using DwV2 = DwGeom<20, 68>;
+
+template <class Geo, bool NARROW>
+cudaError_t dw_launch_as(const DwArgs &a, uint64_t total_tiles, cudaStream_t s)
+{
+    using K = DW<Geo, NARROW>;
+    const int smem = (int)(K::kDW * sizeof(typename K::DWarpMem) + kDecBytes + (NARROW ? 3072 : 0));
+    static int per = -1;
+    if (per < 0) {
+        cudaError_t e = cudaFuncSetAttribute(decompress_warp_kernel<Geo, NARROW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, decompress_warp_kernel<Geo, NARROW>, K::kDNTW, smem);
+        if (per < 1) per = 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t grid = std::max<uint64_t>(
+        1, std::min<uint64_t>((total_tiles + Geo::kWarps - 1) / Geo::kWarps, (uint64_t)per * (uint64_t)sms));
+    decompress_warp_kernel<Geo, NARROW><<<(unsigned)grid, K::kDNTW, smem, s>>>(a);
+    return cudaGetLastError();
+}
 
 template <class Geo>
 cudaError_t dw_launch(const zs_dict *d, const TiledLaunch &L, cudaStream_t s)
@@ -321,22 +501,8 @@ cudaError_t dw_launch(const zs_dict *d, const TiledLaunch &L, cudaStream_t s)
     a.g = L.g;
     a.limit_ns = wait_limit_ns();
     a.stall_tile = injected_stall_tile();
-    const int smem = (int)(DW<Geo>::kDW * sizeof(typename DW<Geo>::DWarpMem) + kDecBytes);
-    static int per = -1;
-    if (per < 0) {
-        cudaError_t e = cudaFuncSetAttribute(decompress_warp_kernel<Geo>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem);
-        if (e != cudaSuccess) return e;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, decompress_warp_kernel<Geo>, DW<Geo>::kDNTW, smem);
-        if (per < 1) per = 1;
-    }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t grid = std::max<uint64_t>(
-        1, std::min<uint64_t>((L.total_tiles + Geo::kWarps - 1) / Geo::kWarps, (uint64_t)per * (uint64_t)sms));
-    decompress_warp_kernel<Geo><<<(unsigned)grid, DW<Geo>::kDNTW, smem, s>>>(a);
-    return cudaGetLastError();
+    return d->max_plen <= 7 ? dw_launch_as<Geo, true>(a, L.total_tiles, s)
+                            : dw_launch_as<Geo, false>(a, L.total_tiles, s);
 }
 
 struct DwEntry {

@@ -444,6 +444,8 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
         return zs::cuda_fail(e, "cudaGetDevice");
     }
     d->lmax = lmax;
+    d->max_plen = 1;
+    for (int b = 0; b < 256; ++b) d->max_plen = std::max(d->max_plen, (int)plen[b]);
     d->layout = L;
     d->mlayout = ML;
     d->has_machine = use_machine;

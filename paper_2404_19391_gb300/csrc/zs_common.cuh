@@ -150,7 +150,8 @@ int64_t injected_stall_tile();
 // The dictionary handle.
 struct zs_dict {
     int device = -1;
-    int lmax = 0;
+    int lmax = 0;      // the file's L_max
+    int max_plen = 0;  // the longest pattern actually present (alphabet singles count as 1)
     zs::EncLayout layout{};
     zs::MachineLayout mlayout{};
     bool has_machine = false;

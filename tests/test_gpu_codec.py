@@ -339,3 +339,38 @@ def test_stalled_tile_times_out(zs, dicts, monkeypatch):
     monkeypatch.delenv("ZS_WAIT_LIMIT_MS")
     r = zs.zs_compress(d, raw, 1, out, None)  # the context is still usable
     assert r.n_lines == 5000
+
+
+# ---- a dictionary with patterns longer than 7 bytes (the byte-wise decoder and, if its transducer is too
+# large, the generic compression kernel) ---------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def long_dicts(zs):
+    from oracle import dictgen
+    train = oracle.preprocess_stream(synth.generate(synth.TRAIN, 0, 3000))
+    learned = [bytes.fromhex(ln.split()[1]) for ln in
+               dictgen.generate(train, T=130, lmin=2, lmax=12).decode().splitlines()[3:]]
+    extra = [b"c0ccccc0C(=O)N", b"C(=O)NCC", b"CCCCCCCCCCCC", b"c0ccc(cc0)", b"C(=O)O)cc0"]
+    data = dictgen.dictionary_text(learned + [e for e in extra if e not in learned], dictgen.SMILES_ALPHABET, 2, 16)
+    od = oracle.Dict(data)
+    longest = max(len(bytes.fromhex(ln.split()[1])) for ln in data.decode().splitlines()[3:])
+    assert longest > 7
+    return zs.Dictionary(data), od
+
+
+def test_long_pattern_dictionary(zs, long_dicts):
+    raw = synth.generate(synth.CFG0, 500, 4000)
+    for flags in (0, 1):
+        _, _, exp_comp, _ = check_compress(zs, long_dicts, raw, flags=flags)
+        check_decompress(zs, long_dicts, exp_comp)
+    for name in ("escapes_only", "cr_tab", "no_trailing_newline", "empty_lines"):
+        _, _, exp_comp, _ = check_compress(zs, long_dicts, EDGE[name])
+        check_decompress(zs, long_dicts, exp_comp)
+    d, od = long_dicts
+    _, _, exp_comp, _ = check_compress(zs, long_dicts, raw)
+    for v in range(zs.zs_kernel_variants(zs.OP_DECOMPRESS)):
+        x = dev(exp_comp)
+        out = torch.full((d.decompress_bound(exp_comp.size) + 16,), 0xEE, dtype=torch.uint8, device="cuda")
+        r = zs.Plan(d, zs.OP_DECOMPRESS, [(x, out[:-16], None)], variant=v).run()[0]
+        assert np.array_equal(out[: r.out_len].cpu().numpy(), oracle.decompress_stream(od, exp_comp))
+        assert torch.all(out[r.out_len:] == 0xEE)
