@@ -76,6 +76,7 @@ struct CW {
     static constexpr int kStW = 16 + kTW + kHW;  // staged bytes: the byte before the tile (index 15), tile, halo
     static constexpr int kMaxLW = Geo::kMaxLines;
     static constexpr int kOutW = Geo::kOut;
+    static constexpr uint32_t kImaskChunks = (kStW + 31) / 16 + 2;
     static_assert(kTW % 512 == 0 && kHW % 16 == 0 && kOutW % 16 == 0 && kMaxLW % 8 == 0 && kMaxLW <= 256,
                   "tile geometry");
 
@@ -100,7 +101,8 @@ struct CW {
         uint16_t tok[kTokMax * 32];  // ring labels of the lane's line: entry k of lane l at [k * 32 + l]
         uint16_t open2[16 * 32];     // open %nn labels (>= 10): slot j of lane l at [j * 32 + l] = label << 8 | token + 1
         uint32_t hist[64];
-        uint16_t imask[(kStW + 31) / 16 + 2];  // per 16-byte chunk of the staged tile: bytes of class < kClsNl
+        uint32_t imask[kImaskChunks];  // per 16-byte chunk of the staged tile: digit bytes (bits 0-15) and the
+                                       // other bytes pre-processing looks at: '%', brackets, space, tab (16-31)
     };
 
     struct Ctx {
@@ -182,7 +184,7 @@ struct CW {
     // more than 16 open %nn rings). *modified: some ring label was rewritten. An invalid line (unclosed ring
     // or bracket, bad %) is left as it is. tok, open2: this lane's columns (stride 32). Token entry: position
     // in the line (bits 0-10), %nn flag (bit 11), new label (bits 12-15).
-    static __device__ __forceinline__ int preprocess_classes(uint8_t *st, const uint16_t *imask, uint32_t a, uint32_t n,
+    static __device__ __forceinline__ int preprocess_classes(uint8_t *st, const uint32_t *imask, uint32_t a, uint32_t n,
                                                       uint16_t *tok, uint16_t *open2, bool *modified)
     {
         *modified = false;
@@ -201,7 +203,7 @@ struct CW {
         uint32_t c = a >> 4;
         auto chunk_mask = [&](uint32_t cc) -> uint32_t {
             const uint32_t cb = cc << 4;
-            uint32_t mm = imask[cc];
+            uint32_t mm = (imask[cc] | (imask[cc] >> 16)) & 0xFFFFu;
             if (cb < a) mm &= 0xFFFFu << (a - cb);
             if (cb + 16 > end) mm &= (1u << (end - cb)) - 1u;
             return mm;
@@ -297,10 +299,18 @@ struct CW {
         if (need_slow) return -1;
         if (bad || in_br || dopen != 0 || nopen2 != 0 || ntok == 0) return (int)n;  // left as it is
         *modified = true;
+        return write_labels(st, a, n, tok, ntok, any_pct);
+    }
+
+    // Writes the new labels of a valid line back into its class codes (the class of digit d is d); %nn
+    // labels shrink to one digit, so the line is compacted then. Returns the new length.
+    static __device__ __forceinline__ int write_labels(uint8_t *st, uint32_t a, uint32_t n, const uint16_t *tok,
+                                                       uint32_t ntok, bool any_pct)
+    {
         if (!any_pct) {
             for (uint32_t k = 0; k < ntok; ++k) {
                 const uint32_t e = tok[k * 32];
-                st[a + (e & 0x7FFu)] = (uint8_t)(e >> 12);  // the class of digit d is d
+                st[a + (e & 0x7FFu)] = (uint8_t)(e >> 12);
             }
             return (int)n;
         }
@@ -317,6 +327,155 @@ struct CW {
         return (int)w;
     }
 
+    // Bits below window position t in word k of a 128-bit window (t - 32k clamped to [0, 32]).
+    static __device__ __forceinline__ uint32_t below(int t, int k)
+    {
+        return __funnelshift_lc(0xFFFFFFFFu, 0u, (uint32_t)max(t - 32 * k, 0));
+    }
+
+    // A 128-bit bit set in four registers (no array, so it never lands in local memory).
+    struct Bits128 {
+        uint32_t w0, w1, w2, w3;
+        __device__ __forceinline__ bool any() const { return (w0 | w1 | w2 | w3) != 0; }
+        __device__ __forceinline__ uint32_t count() const { return __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3); }
+        // Removes and returns the lowest set bit (an empty set returns 127 and stays empty).
+        __device__ __forceinline__ int pop()
+        {
+            const bool z0 = w0 == 0, z1 = w1 == 0, z2 = w2 == 0;
+            const uint32_t w = !z0 ? w0 : (!z1 ? w1 : (!z2 ? w2 : w3));
+            const int base = !z0 ? 0 : (!z1 ? 32 : (!z2 ? 64 : 96));
+            const uint32_t c = w & (w - 1u);
+            w0 = !z0 ? c : w0;
+            w1 = (z0 && !z1) ? c : w1;
+            w2 = (z0 && z1 && !z2) ? c : w2;
+            w3 = (z0 && z1 && z2) ? c : w3;
+            return w ? base + __ffs(w) - 1 : 127;
+        }
+        __device__ __forceinline__ void keep_below(int t)
+        {
+            w0 &= below(t, 0);
+            w1 &= below(t, 1);
+            w2 &= below(t, 2);
+            w3 &= below(t, 3);
+        }
+        __device__ __forceinline__ void clear_range(int lo_b, int hi_b)  // [lo_b, hi_b)
+        {
+            w0 &= ~below(hi_b, 0) | below(lo_b, 0);
+            w1 &= ~below(hi_b, 1) | below(lo_b, 1);
+            w2 &= ~below(hi_b, 2) | below(lo_b, 2);
+            w3 &= ~below(hi_b, 3) | below(lo_b, 3);
+        }
+    };
+
+    // Pre-processing of a line of at most kBitMax bytes without '%' (the usual drug-like line), from bit
+    // masks and with the lanes in lockstep over the ring tokens.
+    //   - The digit and other-flag masks of the line's chunks form two 128-bit register windows (window bit
+    //     i = staged byte 16 * (a / 16) + i). The few other flags (brackets, the end of the first field)
+    //     are walked first: they remove the digits inside brackets and after the field. What remains are
+    //     the ring tokens.
+    //   - The tokens are then visited in order by every lane at once, as many steps as the lane with the
+    //     most tokens, each step predicated rather than branched. lc (latest close position + 1 of each
+    //     label, positions < 128) lives in the byte lanes of three registers, so finding the smallest
+    //     label free since the ring opened is three SIMD byte compares.
+    // Returns as preprocess_classes, or -2 when the line holds a '%' (the caller then runs
+    // preprocess_classes). Every lane of the calling group must call it.
+    static constexpr uint32_t kBitMax = 112;
+
+    static __device__ __forceinline__ int preprocess_bits(uint8_t *st, const uint32_t *imask, uint32_t nchunks,
+                                                          uint32_t a, uint32_t n, bool eligible, uint16_t *tok,
+                                                          bool *modified)
+    {
+        *modified = false;
+        const uint32_t am = __activemask();
+        int result = 0x7FFFFFFF;  // decided early: the line's result; else the token pass decides
+        uint32_t ntok = 0;
+        Bits128 D{0u, 0u, 0u, 0u};
+        const uint32_t lo = a & 15u;
+        if (!eligible) {
+            result = -2;
+        } else {
+            const uint32_t c0 = a >> 4;
+            const int hi = (int)(lo + n);  // the line is window bits [lo, hi), hi <= 127
+            uint32_t m[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m[k] = c0 + k < nchunks ? imask[c0 + k] : 0u;
+            D = Bits128{(m[0] & 0xFFFFu) | (m[1] << 16), (m[2] & 0xFFFFu) | (m[3] << 16),
+                        (m[4] & 0xFFFFu) | (m[5] << 16), (m[6] & 0xFFFFu) | (m[7] << 16)};
+            Bits128 O{(m[0] >> 16) | (m[1] & 0xFFFF0000u), (m[2] >> 16) | (m[3] & 0xFFFF0000u),
+                      (m[4] >> 16) | (m[5] & 0xFFFF0000u), (m[6] >> 16) | (m[7] & 0xFFFF0000u)};
+            D.keep_below(hi);
+            O.keep_below(hi);
+            D.w0 &= 0xFFFFFFFFu << lo;
+            O.w0 &= 0xFFFFFFFFu << lo;
+            bool in_br = false;
+            int obr = 0;
+            while (O.any()) {
+                const int wb = O.pop();
+                const uint32_t c = st[a + (uint32_t)wb - lo];
+                if (c == kClsPct) {
+                    result = -2;
+                    break;
+                }
+                if (c == kClsSpace || c == kClsTab) {  // the first field ends here
+                    D.keep_below(wb);
+                    break;
+                }
+                if (c == kClsLbr) {
+                    if (!in_br) obr = wb;
+                    in_br = true;
+                } else if (in_br) {  // ']' closes the bracket atom: its digits are no ring labels
+                    D.clear_range(obr + 1, wb);
+                    in_br = false;
+                }
+            }
+            ntok = D.count();
+            if (result == 0x7FFFFFFF) {
+                if (in_br || ntok == 0) result = (int)n;       // unclosed bracket, or no ring: left as it is
+                else if (ntok > (uint32_t)kTokMax) result = -1;  // too many tokens for the fast path
+            }
+        }
+        const uint32_t my_steps = result == 0x7FFFFFFF ? ntok : 0u;
+        const uint32_t steps = __reduce_max_sync(am, my_steps);
+        uint32_t lc0 = 0u, lc1 = 0u, lc2 = 0xFFFF0000u;  // labels 0-3, 4-7, 8-9 (bytes 10, 11 never free)
+        uint64_t dmap = 0;
+        uint32_t dopen = 0;
+        bool need_slow = false;
+        for (uint32_t it = 0; it < steps; ++it) {
+            const bool act = it < my_steps;
+            const int wb = D.pop();
+            const uint32_t rel = (uint32_t)wb - lo;
+            const uint32_t label = act ? st[a + rel] : 0u;
+            const bool open = (dopen >> label) & 1u;
+            const uint32_t ko = open ? (uint32_t)(dmap >> (5 * label)) & 31u : 0u;
+            const uint32_t eo = tok[ko * 32];
+            const uint32_t t = ((eo & 0x7Fu) + 1u) * 0x01010101u;  // lc <= open position + 1: free
+            const uint32_t fr = pack4(__vcmpleu4(lc0, t)) | (pack4(__vcmpleu4(lc1, t)) << 4) |
+                                (pack4(__vcmpleu4(lc2, t)) << 8);
+            const bool closing = act && open;
+            const int nl = __ffs(fr) - 1;
+            need_slow = need_slow || (closing && fr == 0u);  // would need a two-digit label
+            const bool upd = closing && fr != 0u;
+            const uint32_t val = (rel + 1u) << (8 * (nl & 3));
+            const uint32_t clr = ~(0xFFu << (8 * (nl & 3)));
+            lc0 = (upd && (nl >> 2) == 0) ? ((lc0 & clr) | val) : lc0;
+            lc1 = (upd && (nl >> 2) == 1) ? ((lc1 & clr) | val) : lc1;
+            lc2 = (upd && (nl >> 2) == 2) ? ((lc2 & clr) | val) : lc2;
+            if (upd) tok[ko * 32] = (uint16_t)(eo | ((uint32_t)nl << 12));
+            if (act) tok[it * 32] = (uint16_t)(upd ? (rel | ((uint32_t)nl << 12)) : rel);
+            const bool opening = act && !open;
+            dmap = opening ? ((dmap & ~(31ull << (5 * label))) | ((uint64_t)it << (5 * label))) : dmap;
+            dopen ^= act ? (1u << label) : 0u;
+        }
+        if (result != 0x7FFFFFFF) return result;
+        if (need_slow) return -1;
+        if (dopen != 0) return (int)n;  // an unclosed ring: left as it is
+        *modified = true;
+        return write_labels(st, a, n, tok, ntok, false);
+    }
+
+    // Packs the 0x00 / 0xFF byte lanes of x into 4 bits (byte i -> bit i).
+    static __device__ __forceinline__ uint32_t pack4(uint32_t x) { return ((x & 0x01010101u) * 0x01020408u) >> 24; }
+
     // Replace the staged bytes by their classes (coalesced 16-byte chunks, lane-replicated table) and flag,
     // per chunk, the bytes pre-processing has to look at.
     static __device__ __forceinline__ void to_classes(const Ctx &C, Slot &S, uint32_t stage_end)
@@ -325,17 +484,19 @@ struct CW {
         for (uint32_t c = C.lane; c < nchunks; c += 32) {
             const uint4 v = *reinterpret_cast<const uint4 *>(S.st + c * 16);
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-            uint32_t o[4], mask = 0;
+            uint32_t o[4], dmask = 0, omask = 0;
     #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const uint32_t b0 = cls_of(C.clsrep, w[i] & 255u, C.lane), b1 = cls_of(C.clsrep, (w[i] >> 8) & 255u, C.lane);
                 const uint32_t b2 = cls_of(C.clsrep, (w[i] >> 16) & 255u, C.lane), b3 = cls_of(C.clsrep, w[i] >> 24, C.lane);
                 o[i] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-                mask |= ((uint32_t)(b0 < kClsNl) | ((uint32_t)(b1 < kClsNl) << 1) | ((uint32_t)(b2 < kClsNl) << 2) |
-                         ((uint32_t)(b3 < kClsNl) << 3)) << (4 * i);
+                const uint32_t dig = __vcmpltu4(o[i], 0x0A0A0A0Au);  // 0xFF per digit byte
+                const uint32_t flg = __vcmpltu4(o[i], kClsNl * 0x01010101u);
+                dmask |= pack4(dig) << (4 * i);
+                omask |= pack4(flg & ~dig) << (4 * i);
             }
             *reinterpret_cast<uint4 *>(S.st + c * 16) = make_uint4(o[0], o[1], o[2], o[3]);
-            C.M->imask[c] = (uint16_t)mask;
+            C.M->imask[c] = dmask | (omask << 16);
         }
         __syncwarp();
     }
@@ -504,7 +665,10 @@ struct CW {
             if (!slow) {
                 bool modified = false;
                 int m = (int)n;
-                if (C.P->flags & ZS_PREPROCESS) m = preprocess_classes(st, M.imask, a, n, M.tok + lane, M.open2 + lane, &modified);
+                if (C.P->flags & ZS_PREPROCESS) {
+                    m = preprocess_bits(st, M.imask, kImaskChunks, a, n, n <= kBitMax, M.tok + lane, &modified);
+                    if (m == -2) m = preprocess_classes(st, M.imask, a, n, M.tok + lane, M.open2 + lane, &modified);
+                }
                 if (m < 0) {
                     slow = true;
                 } else {
@@ -785,9 +949,9 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_warp_kernel(cons
 
 // The compiled geometries. Variant 0 (33 lines of 46 bytes per warp tile, 16 warps per SM) is the
 // default; variant 1 keeps long lines (hundreds of bytes) several to a tile; variant 2 sits between.
-using CwV0 = CwGeom<16, 1536, 512, 72, 1024>;
-using CwV1 = CwGeom<8, 4096, 1024, 192, 2368>;
-using CwV2 = CwGeom<12, 2048, 1024, 96, 1536>;
+using CwV0 = CwGeom<16, 1536, 512, 72, 960>;
+using CwV1 = CwGeom<8, 4096, 1024, 192, 1728>;
+using CwV2 = CwGeom<12, 2048, 1024, 96, 1472>;
 
 template <class Geo>
 size_t cw_smem(const zs_dict *d)

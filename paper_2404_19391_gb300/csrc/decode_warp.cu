@@ -1,12 +1,12 @@
-// zs_decompress (Sec. IV-D2) with one warp per 1408-byte tile of compressed input.
+// zs_decompress (Sec. IV-D2) with one warp per tile of compressed input (default 2176 bytes).
 //
 //   - Each warp of a persistent CTA claims tiles in launch order, stages its tile with one bulk (TMA)
 //     copy and works on it alone: no CTA-wide barrier is on the per-tile path.
 //   - Escapes without a sequential scan: a byte is verbatim exactly when the run of ' ' bytes just before
 //     it has odd length (every unescaped ' ' escapes the byte after it, and a run always starts
-//     unescaped), so each lane decodes its own 44-byte slice after counting the spaces in front of it
+//     unescaped), so each lane decodes its own slice (default 68 bytes) after counting the spaces in front of it
 //     (an odd number of words per slice keeps the lanes' shared-memory reads on distinct banks).
-//   - Small tiles and 28 warps per SM: the per-lane loops are chains of dependent shared-memory loads,
+//   - Small tiles and 20-32 warps per SM: the per-lane loops are chains of dependent shared-memory loads,
 //     so the kernel is bound by latency, and the warp count is what hides it.
 //   - Sizes phase: per lane, the decoded size of its slice (pattern lengths from a shared table), then a
 //     warp scan; the tile's aggregate is published for the decoupled look-back.
@@ -463,9 +463,9 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) decompress_warp_kernel(co
 }
 
 // Compiled geometries; variant 0 is the default.
-using DwV0 = DwGeom<28, 44>;
+using DwV0 = DwGeom<20, 68>;
 using DwV1 = DwGeom<32, 36>;
-using DwV2 = DwGeom<20, 68>;
+using DwV2 = DwGeom<28, 44>;
 
 template <class Geo, bool NARROW>
 cudaError_t dw_launch_as(const DwArgs &a, uint64_t total_tiles, cudaStream_t s)
@@ -517,9 +517,9 @@ constexpr DwEntry dw_entry(const char *name)
 }
 
 const DwEntry kDwv[] = {
-    dw_entry<DwV0>("decompress w28 t1408"),
+    dw_entry<DwV0>("decompress w20 t2176"),
     dw_entry<DwV1>("decompress w32 t1152"),
-    dw_entry<DwV2>("decompress w20 t2176"),
+    dw_entry<DwV2>("decompress w28 t1408"),
 };
 constexpr int kNumDw = (int)(sizeof(kDwv) / sizeof(kDwv[0]));
 
