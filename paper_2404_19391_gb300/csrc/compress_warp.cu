@@ -77,7 +77,7 @@ struct CW {
     static constexpr int kMaxLW = Geo::kMaxLines;
     static constexpr int kOutW = Geo::kOut;
     static constexpr uint32_t kImaskChunks = (kStW + 31) / 16 + 2;
-    static_assert(kTW % 512 == 0 && kHW % 16 == 0 && kOutW % 16 == 0 && kMaxLW % 8 == 0 && kMaxLW <= 256,
+    static_assert(kTW % 16 == 0 && kHW % 16 == 0 && kOutW % 16 == 0 && kMaxLW % 8 == 0 && kMaxLW <= 256,
                   "tile geometry");
 
     struct alignas(16) Slot {
@@ -545,7 +545,7 @@ struct CW {
         const uint32_t first_start = (st[15] == kClsNl && nown > 0) ? 1u : 0u;
         uint32_t Lt = first_start;
     #pragma unroll
-        for (int it = 0; it < kTW / 512; ++it)
+        for (int it = 0; it < (kTW + 511) / 512; ++it)
             Lt += __reduce_add_sync(kFull, __popc(nl_bits_masked(st, 16u + it * 512u + C.lane * 16u, lim)));
         uint32_t last_end = 0, last_nl = 0, last_long = 0;
         if (Lt > 0) {
@@ -604,7 +604,7 @@ struct CW {
         {
             uint32_t rank = first_start;
     #pragma unroll 1
-            for (int it = 0; it < kTW / 512; ++it) {
+            for (int it = 0; it < (kTW + 511) / 512; ++it) {
                 const uint32_t p0 = 16u + it * 512u + lane * 16u;
                 uint32_t bits = nl_bits_masked(st, p0, lim);
                 const uint32_t c = __popc(bits);

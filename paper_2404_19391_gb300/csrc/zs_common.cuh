@@ -76,13 +76,14 @@ constexpr uint32_t kDecBytes = 256 + 256 * kMaxPat;
 // ------------------------------------------------------------------------------------------------
 // Per-call device scratch
 // ------------------------------------------------------------------------------------------------
-struct alignas(16) TileState {
-    uint32_t flag;   // 0: nothing yet, 1: aggregate published, 2: inclusive prefix published
-    uint32_t _pad;
-    uint64_t agg_a, agg_b;  // this tile's totals (a: bytes, b: lines)
-    uint64_t inc_a, inc_b;  // totals of tiles [0, this] (valid when flag == 2)
-    uint64_t _pad2;
+// Look-back record of one tile. Every word carries its own validity (bit 63 set once written; the record
+// starts zeroed), so a reader learns what is published and its value from the same load, and reads a whole
+// record in one round trip.
+struct alignas(32) TileState {
+    unsigned long long agg_a, agg_b;  // this tile's totals (a: bytes, b: lines)
+    unsigned long long inc_a, inc_b;  // totals of tiles [0, this]
 };
+constexpr unsigned long long kValidBit = 1ull << 63;
 
 enum : uint32_t {
     kStTimeout = 1u,       // a bounded wait expired
@@ -176,16 +177,35 @@ __device__ __forceinline__ uint64_t gtime()
     return t;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+// A pair of 64-bit words, written and read at gpu scope (each word is single-copy atomic on its own).
+__device__ __forceinline__ void st_pair(unsigned long long *p, unsigned long long x, unsigned long long y)
 {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(x), "l"(y) : "memory");
 }
 
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+__device__ __forceinline__ void ld_pair(const unsigned long long *p, unsigned long long *x, unsigned long long *y)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(*x), "=l"(*y) : "l"(p) : "memory");
+}
+
+// One tile's record: 2 = inclusive prefix published (values in *a, *b), 1 = aggregate only, 0 = nothing yet.
+__device__ __forceinline__ uint32_t read_tile(const TileState *ts, uint64_t *a, uint64_t *b)
+{
+    unsigned long long ga, gb, ia, ib;
+    ld_pair(&ts->agg_a, &ga, &gb);
+    ld_pair(&ts->inc_a, &ia, &ib);
+    if (ia & ib & kValidBit) {
+        *a = ia & ~kValidBit;
+        *b = ib & ~kValidBit;
+        return 2u;
+    }
+    if (ga & gb & kValidBit) {
+        *a = ga & ~kValidBit;
+        *b = gb & ~kValidBit;
+        return 1u;
+    }
+    *a = *b = 0;
+    return 0u;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -349,7 +369,8 @@ __device__ __forceinline__ void lookback(TileState *tiles, uint64_t t, uint64_t 
     uint64_t t0 = 0;
     bool timed = false;
     while (p >= 0) {
-        uint32_t f = ld_acquire(&tiles[p].flag);
+        uint64_t va, vb;
+        const uint32_t f = read_tile(&tiles[p], &va, &vb);
         if (f == 0) {
             if (*((volatile uint32_t *)status) & kStTimeout) break;
             if (!timed) {
@@ -362,13 +383,9 @@ __device__ __forceinline__ void lookback(TileState *tiles, uint64_t t, uint64_t 
             __nanosleep(64);
             continue;
         }
-        if (f == 2) {
-            a += tiles[p].inc_a;
-            b += tiles[p].inc_b;
-            break;
-        }
-        a += tiles[p].agg_a;
-        b += tiles[p].agg_b;
+        a += va;
+        b += vb;
+        if (f == 2) break;
         --p;
         timed = false;
     }
@@ -376,8 +393,8 @@ __device__ __forceinline__ void lookback(TileState *tiles, uint64_t t, uint64_t 
     *eb = b;
 }
 
-// Decoupled look-back by a whole warp: each round, lane j inspects tile t-1-j, so one round trip to L2
-// covers 32 predecessors. Sums aggregates from the nearest predecessor back to (and including) the
+// Decoupled look-back by a whole warp: each round, lane j reads the record of tile t-1-j, so one round trip
+// to L2 covers 32 predecessors. Sums aggregates from the nearest predecessor back to (and including) the
 // nearest one that has published its inclusive prefix. Called by all 32 lanes; every lane returns the
 // same sums. Waits are bounded (kStTimeout on expiry).
 __device__ __forceinline__ void lookback_warp(TileState *tiles, uint64_t t, uint64_t *ea, uint64_t *eb,
@@ -387,38 +404,27 @@ __device__ __forceinline__ void lookback_warp(TileState *tiles, uint64_t t, uint
     uint64_t a = 0, b = 0;
     int64_t top = (int64_t)t - 1;
     uint64_t t0 = 0;
-    bool timed = false, gave_up = false;
-    while (top >= 0 && !gave_up) {
+    bool timed = false;
+    while (top >= 0) {
         const int64_t p = top - (int64_t)lane;
-        uint32_t f = p >= 0 ? ld_acquire(&tiles[p].flag) : 2u;
-        while (__any_sync(0xffffffffu, f == 0)) {
-            if (*((volatile uint32_t *)status) & kStTimeout) {
-                gave_up = true;
-                break;
-            }
+        uint64_t va = 0, vb = 0;
+        const uint32_t f = p >= 0 ? read_tile(&tiles[p], &va, &vb) : 2u;  // before tile 0: a zero prefix
+        const uint32_t incl = __ballot_sync(0xffffffffu, f == 2u);
+        const int stop = incl ? __ffs(incl) - 1 : 32;  // nearest lane holding an inclusive prefix
+        if (__any_sync(0xffffffffu, (int)lane < stop && f == 0u)) {  // a nearer tile has published nothing
+            if (*((volatile uint32_t *)status) & kStTimeout) break;
             if (!timed) {
                 t0 = gtime();
                 timed = true;
             } else if (gtime() - t0 > limit_ns) {
                 if (lane == 0) atomicOr(status, kStTimeout);
-                gave_up = true;
                 break;
             }
-            __nanosleep(256);
-            if (f == 0) f = ld_acquire(&tiles[p].flag);
+            __nanosleep(128);
+            continue;
         }
-        if (gave_up) break;
         timed = false;
-        const uint32_t incl = __ballot_sync(0xffffffffu, f == 2u);
-        const int stop = incl ? __ffs(incl) - 1 : 32;  // nearest lane holding an inclusive prefix
-        uint64_t va = 0, vb = 0;
-        if ((int)lane < stop && p >= 0) {
-            va = tiles[p].agg_a;
-            vb = tiles[p].agg_b;
-        } else if ((int)lane == stop && p >= 0) {
-            va = tiles[p].inc_a;
-            vb = tiles[p].inc_b;
-        }
+        if ((int)lane > stop) va = vb = 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             va += __shfl_xor_sync(0xffffffffu, va, o);
@@ -435,14 +441,8 @@ __device__ __forceinline__ void lookback_warp(TileState *tiles, uint64_t t, uint
 
 __device__ __forceinline__ void publish(TileState *ts, uint32_t flag, uint64_t a, uint64_t b)
 {
-    if (flag == 1) {
-        ts->agg_a = a;
-        ts->agg_b = b;
-    } else {
-        ts->inc_a = a;
-        ts->inc_b = b;
-    }
-    st_release(&ts->flag, flag);
+    if (flag == 1) st_pair(&ts->agg_a, a | kValidBit, b | kValidBit);
+    else st_pair(&ts->inc_a, a | kValidBit, b | kValidBit);
 }
 
 __device__ __forceinline__ void note_error_offset(DevResult *r, uint64_t off)

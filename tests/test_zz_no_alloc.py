@@ -15,7 +15,7 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-MAX_INPUT = 174761 * 2176  # tile records in the 8 MiB scratch x compressed bytes per tile
+MAX_INPUT = 262142 * 2176  # tile records in the 8 MiB scratch x compressed bytes per tile
 
 
 class _Result(ctypes.Structure):
