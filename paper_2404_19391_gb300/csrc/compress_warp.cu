@@ -789,19 +789,8 @@ struct CW {
             }
         }
         __syncwarp();
-        if (staged) {
-            uint8_t *gdst = A.out + out_at - so;  // 16-byte aligned
-            const uint32_t nchunks = (uint32_t)((so + btotal + 15) >> 4);
-            for (uint32_t c = lane; c < nchunks; c += 32) {
-                const uint32_t lo_b = c * 16u, hi_b = lo_b + 16u;
-                if (lo_b >= so && hi_b <= so + btotal && out_at - so + hi_b <= A.out_cap) {
-                    *reinterpret_cast<uint4 *>(gdst + lo_b) = *reinterpret_cast<const uint4 *>(M.ost + lo_b);
-                } else {
-                    for (uint32_t k = lo_b; k < hi_b; ++k)
-                        if (k >= so && k < so + btotal && out_at - so + k < A.out_cap) gdst[k] = M.ost[k];
-                }
-            }
-        }
+        if (staged)
+            warp_copy_out(M.ost, so, btotal, A.out + out_at, A.out_cap > out_at ? A.out_cap - out_at : 0);
         __syncwarp();
     }
 

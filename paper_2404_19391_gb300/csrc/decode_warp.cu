@@ -351,19 +351,7 @@ struct DW {
             expand_slice<false>(C, S, p0, p1, S.lit0[lane] != 0, S.lane_off[lane], ea, so);
         }
         __syncwarp();
-        if (staged) {
-            uint8_t *gdst = A.out + ea - so;  // 16-byte aligned
-            const uint32_t nchunks = (uint32_t)((so + total + 15) >> 4);
-            for (uint32_t c = lane; c < nchunks; c += 32) {
-                const uint32_t lo = c * 16u, hi = lo + 16u;
-                if (lo >= so && hi <= so + total && ea - so + hi <= A.out_cap) {
-                    *reinterpret_cast<uint4 *>(gdst + lo) = *reinterpret_cast<const uint4 *>(C.M->ost + lo);
-                } else {
-                    for (uint32_t k = lo; k < hi; ++k)
-                        if (k >= so && k < so + total && ea - so + k < A.out_cap) gdst[k] = C.M->ost[k];
-                }
-            }
-        }
+        if (staged) warp_copy_out(C.M->ost, so, total, A.out + ea, A.out_cap > ea ? A.out_cap - ea : 0);
         if (lane == 0 && t == A.ntiles - 1) {
             A.res->out_len = ea + total;
             A.res->n_lines = eb + totn + ((A.in[A.n - 1] != kNl) ? 1u : 0u);

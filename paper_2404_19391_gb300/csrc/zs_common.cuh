@@ -445,6 +445,23 @@ __device__ __forceinline__ void publish(TileState *ts, uint32_t flag, uint64_t a
     else st_pair(&ts->inc_a, a | kValidBit, b | kValidBit);
 }
 
+// Copies a warp's staged output to global memory: staged bytes [so, so + len) go to dst[0, len), where
+// dst - so is 16-byte aligned and bytes at or past cap (relative to dst) are not written. Whole 16-byte
+// chunks go as one store each; the partial chunks at either end byte by byte. Called by all 32 lanes.
+__device__ __forceinline__ void warp_copy_out(const uint8_t *stage, uint32_t so, uint64_t len, uint8_t *dst,
+                                              uint64_t cap)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint8_t *g = dst - so;
+    const uint32_t end = so + (uint32_t)min(len, cap);  // staged bytes [so, end) are written
+    const uint32_t c0 = (so + 15u) >> 4, c1 = end >> 4;  // whole chunks [c0, c1)
+    for (uint32_t c = c0 + lane; c < c1; c += 32)
+        reinterpret_cast<uint4 *>(g)[c] = reinterpret_cast<const uint4 *>(stage)[c];
+    const uint32_t h1 = min(c0 * 16u, end);
+    for (uint32_t k = so + lane; k < h1; k += 32) g[k] = stage[k];
+    for (uint32_t k = max(c1 * 16u, h1) + lane; k < end; k += 32) g[k] = stage[k];
+}
+
 __device__ __forceinline__ void note_error_offset(DevResult *r, uint64_t off)
 {
     atomicMax(&r->err_key, ~(unsigned long long)off);
