@@ -98,8 +98,8 @@ struct CW {
     struct alignas(16) WarpMem {
         Slot slot[2];
         uint8_t ost[kOutW + 32];
-        uint16_t tok[kTokMax * 32];  // ring labels of the lane's line: entry k of lane l at [k * 32 + l]
-        uint16_t open2[16 * 32];     // open %nn labels (>= 10): slot j of lane l at [j * 32 + l] = label << 8 | token + 1
+        uint16_t tok[kTokMax * 32];  // per lane (entry k of lane l at [k * 32 + l]): the ring tokens of the
+                                     // lane's line (bit-mask path) or its open rings (in-place path)
         uint32_t hist[64];
         uint32_t imask[kImaskChunks];  // per 16-byte chunk of the staged tile: digit bytes (bits 0-15) and the
                                        // other bytes pre-processing looks at: '%', brackets, space, tab (16-31)
@@ -175,17 +175,22 @@ struct CW {
     }
 
     // Pre-processing of the class codes st[a, a+n) in place (Sec. IV-A), in one pass over the bytes flagged
-    // in imask (digits, '%', brackets, space, tab). Rings are labelled in the order they close, each with
-    // the smallest label that no ring closed since it opened still holds: lc[x] = position + 1 of the latest
-    // close that took label x. A ring open under a label below 10 is found through dmap (5 bits of token
-    // index per label, in registers); %nn labels of 10 and more through the small open2 table. New labels
-    // are kept in the token entries and written only once the line is known to be valid.
-    // Returns the new length, or -1 for the slow path (a label >= 10 needed, more than 32 ring labels or
-    // more than 16 open %nn rings). *modified: some ring label was rewritten. An invalid line (unclosed ring
-    // or bracket, bad %) is left as it is. tok, open2: this lane's columns (stride 32). Token entry: position
-    // in the line (bits 0-10), %nn flag (bit 11), new label (bits 12-15).
+    // in imask (digits, '%', brackets, space, tab), for any line the bit-mask path does not take. Rings
+    // are labelled in the order they close, each with the smallest label that no ring closed since it
+    // opened still holds: lc[x] = position + 1 of the latest close that took label x. Both label bytes of
+    // a ring are written when it closes (a %nn label's '%' becomes the digit and its two digits a deletion
+    // mark, squeezed out at the end), so only the open rings are remembered, in the lane's column of `opn`
+    // (stride 32): slot x < 10 = position + 1 of the open label x, slots 10 + 2j / 11 + 2j = (label + 1,
+    // position) of up to 8 open %nn labels. A line found invalid at its end (unclosed ring or bracket, bad
+    // %) is restored from its raw bytes and left as it is.
+    // Returns the new length, or -1 for the slow path (a label >= 10 needed, more than 8 open %nn labels,
+    // or more than kFastMax bytes). *modified: some ring label was rewritten.
+    static constexpr uint8_t kClsDel = 0xFE;  // a deleted byte (the digits of a rewritten %nn label)
+    static constexpr int kOpen2 = 8;
+
     static __device__ __forceinline__ int preprocess_classes(uint8_t *st, const uint32_t *imask, uint32_t a, uint32_t n,
-                                                      uint16_t *tok, uint16_t *open2, bool *modified)
+                                                             const uint8_t *raw, const Ctx &C, uint16_t *opn,
+                                                             bool *modified)
     {
         *modified = false;
         if (n > (uint32_t)kFastMax) return -1;
@@ -194,11 +199,9 @@ struct CW {
         uint32_t lc[10];
     #pragma unroll
         for (int x = 0; x < 10; ++x) lc[x] = 0;
-        uint64_t dmap = 0;
-        uint32_t dopen = 0, nopen2 = 0, ntok = 0, skipto = 0;
-        bool in_br = false, bad = false, any_pct = false, done = false, need_slow = false;
-        // one flat loop over the flagged bytes of the line (lanes of a warp then pay for the longest list of
-        // flagged bytes, not for the busiest chunk of each step)
+        for (int x = 0; x < 10 + 2 * kOpen2; ++x) opn[x * 32] = 0;
+        uint32_t dopen = 0, nopen2 = 0, skipto = 0;
+        bool in_br = false, bad = false, any_pct = false, done = false, need_slow = false, wrote = false;
         const uint32_t clast = (end - 1) >> 4;
         uint32_t c = a >> 4;
         auto chunk_mask = [&](uint32_t cc) -> uint32_t {
@@ -208,98 +211,107 @@ struct CW {
             if (cb + 16 > end) mm &= (1u << (end - cb)) - 1u;
             return mm;
         };
-        uint32_t m = chunk_mask(c);
-        {
-            for (;;) {
-                while (m == 0 && c < clast) m = chunk_mask(++c);
-                if (m == 0 || done) break;
-                const uint32_t p = (c << 4) + (uint32_t)(__ffs(m) - 1);
-                m &= m - 1;
-                const uint32_t k = st[p];
-                const bool live = p >= skipto;  // not one of the two digits of a %nn label
-                const bool ws = live & ((k == kClsSpace) | (k == kClsTab));
-                done = ws;  // the SMILES field ends at the first space or tab
-                const bool lb = live & !ws & !in_br & (k == kClsLbr);
-                const bool rb = live & in_br & (k == kClsRbr);
-                const bool ring = live & !in_br & (k <= kClsPct);  // a digit or a '%'
-                in_br = (in_br | lb) & !rb;
-                if (!ring) continue;
-                uint32_t label = k, pct = 0;
-                if (k == kClsPct) {  // %nn: two digits must follow inside the line
-                    if (p + 2 >= end || st[p + 1] >= 10 || st[p + 2] >= 10) {
-                        bad = true;
-                        done = true;
-                        break;
-                    }
-                    label = st[p + 1] * 10u + st[p + 2];
-                    pct = 1;
-                    any_pct = true;
-                    skipto = p + 3;
-                }
-                if (ntok == (uint32_t)kTokMax) {
-                    need_slow = true;
-                    done = true;
-                    break;
-                }
-                const uint32_t me = ntok++;
-                tok[me * 32] = (uint16_t)((p - a) | (pct << 11));
-                int ko = -1;
-                if (label < 10) {
-                    if ((dopen >> label) & 1u) {
-                        ko = (int)((dmap >> (5 * label)) & 31u);
-                        dopen &= ~(1u << label);
-                    } else {
-                        dmap = (dmap & ~(31ull << (5 * label))) | ((uint64_t)me << (5 * label));
-                        dopen |= 1u << label;
-                    }
-                } else {
-                    int hit = -1, empty = -1;
-                    for (int j = 0; j < 16; ++j) {
-                        const uint32_t v = open2[j * 32];
-                        if (v == 0) {
-                            if (empty < 0) empty = j;
-                        } else if ((v >> 8) == label) {
-                            hit = j;
-                        }
-                    }
-                    if (hit >= 0) {
-                        ko = (int)(open2[hit * 32] & 0xFFu) - 1;
-                        open2[hit * 32] = 0;
-                        --nopen2;
-                    } else if (empty >= 0) {
-                        open2[empty * 32] = (uint16_t)((label << 8) | (me + 1));
-                        ++nopen2;
-                    } else {
-                        need_slow = true;
-                        done = true;
-                        break;
-                    }
-                }
-                if (ko < 0) continue;
-                const uint32_t eo = tok[ko * 32];
-                const uint32_t po = eo & 0x7FFu;
-                int nl = -1;
-    #pragma unroll
-                for (int x = 9; x >= 0; --x)
-                    if (lc[x] <= po + 1) nl = x;
-                if (nl < 0) {  // needs a two-digit label
-                    need_slow = true;
-                    done = true;
-                    break;
-                }
-    #pragma unroll
-                for (int x = 0; x < 10; ++x)
-                    if (x == nl) lc[x] = (p - a) + 1;
-                tok[ko * 32] = (uint16_t)(eo | ((uint32_t)nl << 12));
-                tok[me * 32] = (uint16_t)(tok[me * 32] | ((uint32_t)nl << 12));
+        // writes new label nl at line position q (a %nn token: the '%' becomes the digit, its digits go)
+        auto put = [&](uint32_t q, uint32_t nl, bool pct) {
+            st[a + q] = (uint8_t)nl;  // the class of digit d is d
+            if (pct) {
+                st[a + q + 1] = kClsDel;
+                st[a + q + 2] = kClsDel;
             }
+        };
+        uint32_t m = chunk_mask(c);
+        for (;;) {
+            while (m == 0 && c < clast) m = chunk_mask(++c);
+            if (m == 0 || done) break;
+            const uint32_t p = (c << 4) + (uint32_t)(__ffs(m) - 1);
+            m &= m - 1;
+            const uint32_t k = st[p];
+            const bool live = p >= skipto;  // not one of the two digits of a %nn label
+            const bool ws = live & ((k == kClsSpace) | (k == kClsTab));
+            done = ws;  // the SMILES field ends at the first space or tab
+            const bool lb = live & !ws & !in_br & (k == kClsLbr);
+            const bool rb = live & in_br & (k == kClsRbr);
+            const bool ring = live & !in_br & (k <= kClsPct);  // a digit or a '%'
+            in_br = (in_br | lb) & !rb;
+            if (!ring) continue;
+            uint32_t label = k;
+            bool pct = false;
+            if (k == kClsPct) {  // %nn: two digits must follow inside the line
+                if (p + 2 >= end || st[p + 1] >= 10 || st[p + 2] >= 10) {
+                    bad = true;
+                    break;
+                }
+                label = st[p + 1] * 10u + st[p + 2];
+                pct = true;
+                any_pct = true;
+                skipto = p + 3;
+            }
+            const uint32_t q = p - a;
+            int po = -1;  // position of the ring's open token, if this token closes it
+            bool opct = false;
+            if (label < 10) {
+                if ((dopen >> label) & 1u) {
+                    po = (int)opn[label * 32] - 1;
+                    dopen &= ~(1u << label);
+                } else {
+                    opn[label * 32] = (uint16_t)(q + 1);
+                    dopen |= 1u << label;
+                }
+            } else {
+                int hit = -1, empty = -1;
+                for (int j = 0; j < kOpen2; ++j) {
+                    const uint32_t v = opn[(10 + 2 * j) * 32];
+                    if (v == 0) {
+                        if (empty < 0) empty = j;
+                    } else if (v == label + 1) {
+                        hit = j;
+                    }
+                }
+                if (hit >= 0) {
+                    po = (int)opn[(11 + 2 * hit) * 32];
+                    opct = true;
+                    opn[(10 + 2 * hit) * 32] = 0;
+                    --nopen2;
+                } else if (empty >= 0) {
+                    opn[(10 + 2 * empty) * 32] = (uint16_t)(label + 1);
+                    opn[(11 + 2 * empty) * 32] = (uint16_t)q;
+                    ++nopen2;
+                } else {
+                    need_slow = true;
+                    break;
+                }
+            }
+            if (po < 0) continue;
+            if (label < 10) opct = false;
+            int nl = -1;
+    #pragma unroll
+            for (int x = 9; x >= 0; --x)
+                if (lc[x] <= (uint32_t)po + 1) nl = x;
+            if (nl < 0) {  // needs a two-digit label
+                need_slow = true;
+                break;
+            }
+    #pragma unroll
+            for (int x = 0; x < 10; ++x)
+                if (x == nl) lc[x] = q + 1;
+            put((uint32_t)po, (uint32_t)nl, opct);
+            put(q, (uint32_t)nl, pct);
+            wrote = true;
         }
-        if (any_pct && nopen2 > 0)
-            for (int j = 0; j < 16; ++j) open2[j * 32] = 0;
         if (need_slow) return -1;
-        if (bad || in_br || dopen != 0 || nopen2 != 0 || ntok == 0) return (int)n;  // left as it is
+        if (bad || in_br || dopen != 0 || nopen2 != 0 || !wrote) {  // left as it is
+            if (wrote)
+                for (uint32_t i = 0; i < n; ++i) st[a + i] = (uint8_t)cls_of(C.clsrep, raw[i], C.lane);
+            return (int)n;
+        }
         *modified = true;
-        return write_labels(st, a, n, tok, ntok, any_pct);
+        if (!any_pct) return (int)n;
+        uint32_t w = 0;
+        for (uint32_t r = 0; r < n; ++r) {
+            const uint8_t v = st[a + r];
+            if (v != kClsDel) st[a + w++] = v;
+        }
+        return (int)w;
     }
 
     // Writes the new labels of a valid line back into its class codes (the class of digit d is d); %nn
@@ -431,7 +443,7 @@ struct CW {
             ntok = D.count();
             if (result == 0x7FFFFFFF) {
                 if (in_br || ntok == 0) result = (int)n;       // unclosed bracket, or no ring: left as it is
-                else if (ntok > (uint32_t)kTokMax) result = -1;  // too many tokens for the fast path
+                else if (ntok > (uint32_t)kTokMax) result = -2;  // more tokens than the lane's column holds
             }
         }
         const uint32_t my_steps = result == 0x7FFFFFFF ? ntok : 0u;
@@ -599,6 +611,7 @@ struct CW {
         const uint32_t nb = r1 - r0, Lt = S.Lt, first_start = S.first_start;
         const uint32_t lim = 15u + S.nown;
         const uint64_t base = tile_base(t);
+        const uint8_t *gbase = A.in + base - 16;  // global address of staged byte 0
 
         if (lane == 0 && first_start && r0 == 0) S.start[0] = 16;
         {
@@ -667,7 +680,8 @@ struct CW {
                 int m = (int)n;
                 if (C.P->flags & ZS_PREPROCESS) {
                     m = preprocess_bits(st, M.imask, kImaskChunks, a, n, n <= kBitMax, M.tok + lane, &modified);
-                    if (m == -2) m = preprocess_classes(st, M.imask, a, n, M.tok + lane, M.open2 + lane, &modified);
+                    if (m == -2)
+                        m = preprocess_classes(st, M.imask, a, n, gbase + a, C, M.tok + lane, &modified);
                 }
                 if (m < 0) {
                     slow = true;
@@ -875,7 +889,6 @@ struct CW {
             mbar_init(&M.slot[0].bar, 1);
             mbar_init(&M.slot[1].bar, 1);
         }
-        for (uint32_t j = lane; j < 16 * 32; j += 32) M.open2[j] = 0;
         __syncthreads();
         if (threadIdx.x == 0) {
             mbar_arrive_tx(&img_bar, P->img_bytes);
