@@ -122,9 +122,11 @@ struct CW {
     }
 
     // One transducer step (last byte first): returns the chosen symbol, updates state and cost.
+    // q is the current state's row offset (state * classes).
     static __device__ __forceinline__ uint32_t step(const uint32_t *T, uint32_t nc, uint32_t k, uint32_t &q, int32_t &cost)
     {
-        const uint32_t t = T[q * nc + k];
+        (void)nc;
+        const uint32_t t = T[q + k];
         q = t & 0xFFFFu;
         cost += (int32_t)((t >> 16) & 31u) - 16;
         return t >> 24;
@@ -513,10 +515,12 @@ struct CW {
         __syncwarp();
     }
 
-    static __device__ __forceinline__ uint32_t nl_bits_masked(const uint8_t *st, uint32_t p0, uint32_t lim)
+    // Newline bits of the 16 staged bytes at p0 (nl: the newline byte, raw or as its class), below lim.
+    static __device__ __forceinline__ uint32_t nl_bits_masked(const uint8_t *st, uint32_t p0, uint32_t lim,
+                                                              uint32_t nl = kClsNl)
     {
         if (p0 >= lim) return 0;
-        uint32_t bits = eq_bits16(*reinterpret_cast<const uint4 *>(st + p0), kClsNl * 0x01010101u);
+        uint32_t bits = eq_bits16(*reinterpret_cast<const uint4 *>(st + p0), nl * 0x01010101u);
         if (p0 + 16 > lim) bits &= (1u << (lim - p0)) - 1u;
         return bits;
     }
@@ -544,6 +548,9 @@ struct CW {
     }
 
     // Segmentation of the staged tile: line count, first start, end of the last line.
+    // Segmentation of the staged tile on its raw bytes: line count, first start, end of the last line.
+    // Then only the bytes the tile's lines cover (the owned bytes and the last line's overhang into the
+    // halo) are turned into classes.
     static __device__ __forceinline__ void segment(const Ctx &C, Slot &S, uint64_t t)
     {
         const ShardView &A = *C.A;
@@ -551,18 +558,18 @@ struct CW {
         const uint32_t nown = (uint32_t)(min(A.n, base + kTW) - base);
         const uint64_t stage_hi = min(A.n, base + (uint64_t)kTW + kHW);
         const uint32_t stage_end = (uint32_t)(stage_hi - base) + 16u;
-        to_classes(C, S, stage_end);
         const uint8_t *st = S.st;
         const uint32_t lim = 15u + nown;
-        const uint32_t first_start = (st[15] == kClsNl && nown > 0) ? 1u : 0u;
+        const uint32_t first_start = (st[15] == kNl && nown > 0) ? 1u : 0u;
         uint32_t Lt = first_start;
     #pragma unroll
         for (int it = 0; it < (kTW + 511) / 512; ++it)
-            Lt += __reduce_add_sync(kFull, __popc(nl_bits_masked(st, 16u + it * 512u + C.lane * 16u, lim)));
+            Lt += __reduce_add_sync(kFull, __popc(nl_bits_masked(st, 16u + it * 512u + C.lane * 16u, lim, kNl)));
         uint32_t last_end = 0, last_nl = 0, last_long = 0;
+        uint32_t conv_end = 16u + nown;  // staged bytes [0, conv_end) become classes
         if (Lt > 0) {
             uint32_t end = 0xFFFFFFFFu;
-            if (st[15 + nown] == kClsNl) {
+            if (st[15 + nown] == kNl) {
                 end = 15 + nown;
             } else {
                 for (uint32_t off = 16 + nown; off < stage_end && end == 0xFFFFFFFFu; off += 512) {
@@ -570,10 +577,10 @@ struct CW {
                     uint32_t bits = 0;
                     if (p0 < stage_end) {
                         if (p0 + 16 <= stage_end && (p0 & 15u) == 0) {
-                            bits = eq_bits16(*reinterpret_cast<const uint4 *>(st + p0), kClsNl * 0x01010101u);
+                            bits = eq_bits16(*reinterpret_cast<const uint4 *>(st + p0), kNl * 0x01010101u);
                         } else {
                             for (uint32_t q = 0; q < 16 && p0 + q < stage_end; ++q)
-                                if (st[p0 + q] == kClsNl) bits |= 1u << q;
+                                if (st[p0 + q] == kNl) bits |= 1u << q;
                         }
                     }
                     const uint32_t cand = bits ? p0 + (uint32_t)(__ffs(bits) - 1) : 0xFFFFFFFFu;
@@ -583,12 +590,15 @@ struct CW {
             if (end != 0xFFFFFFFFu) {
                 last_end = end;
                 last_nl = 1;
+                conv_end = max(conv_end, end + 1u);
             } else if (stage_hi == A.n) {
                 last_end = stage_end;
+                conv_end = stage_end;
             } else {
-                last_long = 1;
+                last_long = 1;  // the slow path reads this line from global memory
             }
         }
+        to_classes(C, S, conv_end);
         if (C.lane == 0) {
             S.Lt = Lt;
             S.first_start = first_start;

@@ -422,7 +422,7 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
     if (use_machine) {
         ML.n_states = (uint32_t)mach.states;
         ML.n_classes = (uint32_t)n_classes;
-        ML.start = (uint32_t)mach.start;
+        ML.start = (uint32_t)mach.start * (uint32_t)n_classes;  // row offset of the start state
         ML.off_table = zs::kMOffTable;
         ML.img_bytes = zs::kMOffTable + (uint32_t)(mach.table.size() * 4);
         ML.img_bytes = (ML.img_bytes + 15u) & ~15u;
@@ -430,7 +430,11 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
         for (int c = 0; c < 256; ++c)
             for (int ln = 0; ln < 32; ++ln) mimg[zs::kMOffClsRep + ((c >> 2) * 32 + ln) * 4 + (c & 3)] = cls[c];
         for (auto &en : entries) mimg[zs::kMOffPlen + en.sym] = (uint8_t)en.pat.size();
-        memcpy(mimg.data() + zs::kMOffTable, mach.table.data(), mach.table.size() * 4);
+        // the image stores each next state as its row offset (state * classes, < 2^16 within the table
+        // budget), so the kernel's per-byte lookup needs no multiply
+        std::vector<uint32_t> rows(mach.table);
+        for (uint32_t &e : rows) e = (e & 0xFFFF0000u) | ((e & 0xFFFFu) * (uint32_t)n_classes);
+        memcpy(mimg.data() + zs::kMOffTable, rows.data(), rows.size() * 4);
     }
 
     std::vector<uint8_t> dec(zs::kDecBytes, 0);

@@ -58,7 +58,7 @@ constexpr uint8_t kClsPct = 10, kClsLbr = 11, kClsRbr = 12, kClsSpace = 13, kCls
 //   [0, 8192)          class of each byte, replicated for the 32 lanes: byte c of lane l is at
 //                      ((c >> 2) * 32 + l) * 4 + (c & 3), so a warp-wide lookup never conflicts on a bank
 //   [8192, 8448)       plen[256]: symbol -> pattern length
-//   [8448, ...)        table[states][classes] (u32): next state | (delta + 16) << 16 | symbol << 24
+//   [8448, ...)        table[states][classes] (u32): next state * classes | (delta + 16) << 16 | symbol << 24
 struct MachineLayout {
     uint32_t n_states;
     uint32_t n_classes;
