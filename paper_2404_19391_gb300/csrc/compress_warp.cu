@@ -959,9 +959,10 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_warp_kernel(cons
     CW<Geo>::run(&P);
 }
 
-// The compiled geometries. Variant 0 (33 lines of 46 bytes per warp tile, 17 warps per SM) is the
-// default; variant 1 keeps long lines (hundreds of bytes) several to a tile; variant 2 sits between.
-using CwV0 = CwGeom<17, 1536, 512, 72, 1024>;
+// The compiled geometries. Variant 0 (about 30 lines of 46 bytes per warp tile, so mostly one lane round;
+// 18 warps per SM) is the default; variant 1 keeps long lines (hundreds of bytes) several to a tile;
+// variant 2 sits between.
+using CwV0 = CwGeom<18, 1408, 512, 64, 960>;
 using CwV1 = CwGeom<8, 4096, 1024, 192, 1728>;
 using CwV2 = CwGeom<12, 2048, 1024, 96, 1472>;
 
@@ -1022,7 +1023,7 @@ constexpr CwEntry cw_entry(const char *name)
 }
 
 const CwEntry kCw[] = {
-    cw_entry<CwV0>("compress w17 t1536"),
+    cw_entry<CwV0>("compress w18 t1408"),
     cw_entry<CwV1>("compress w8 t4096"),
     cw_entry<CwV2>("compress w12 t2048"),
 };
