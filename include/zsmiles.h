@@ -256,6 +256,30 @@ double zs_plan_tuned_ms(const zs_plan *p, int v);  /* median kernel ms of varian
 double zs_plan_last_ms(const zs_plan *p);          /* kernel ms of the last run */
 void zs_plan_destroy(zs_plan *p);
 
+/* ---- Host-to-host pipelines ------------------------------------------------------------------------
+ *
+ * zs_compress / zs_decompress take device buffers. These take HOST buffers and hide the copies: the stream
+ * is cut into chunks at line ends (lines are independent, Sec. I, so the chunks' outputs concatenated are
+ * the output of the whole stream), and up to n_streams chunks are in flight at once, each on its own
+ * stream: host-to-device copy, kernel, then its output and line index copied to their place in the
+ * caller's buffers. Copies in both directions overlap the kernels of other chunks. Output, line index,
+ * errors and capacities are exactly those of zs_compress / zs_decompress on the same bytes. The buffers
+ * should be page-locked (cudaMallocHost / cudaHostRegister) for the copies to overlap; pageable memory
+ * works but serialises them. Calls on one dictionary run one at a time (the pipeline's device buffers
+ * belong to the dictionary and are kept for the next call). A line longer than chunk_bytes returns
+ * ZS_ERR_CAPACITY (raise chunk_bytes). Not in the paper.
+ */
+typedef struct zs_pipeline_options {
+    size_t chunk_bytes; /* input bytes per chunk (0: 32 MiB; at least 4 KiB) */
+    int n_streams;      /* chunks in flight (0: 4; at most 16) */
+} zs_pipeline_options;
+
+zs_status zs_compress_host(const zs_dict *d, const uint8_t *h_in, size_t in_len, unsigned flags, uint8_t *h_out,
+                           size_t out_cap, uint64_t *h_line_index, size_t index_cap, zs_result *res,
+                           const zs_pipeline_options *opt);
+zs_status zs_decompress_host(const zs_dict *d, const uint8_t *h_in, size_t in_len, uint8_t *h_out, size_t out_cap,
+                             zs_result *res, const zs_pipeline_options *opt);
+
 /* ---- Serving form: continuous batching of random-access requests over a resident store -----------
  *
  * A server keeps a compressed store and its line index resident in device memory (the caller's

@@ -482,6 +482,7 @@ extern "C" void zs_free_dictionary(zs_dict *d)
     cudaGetDevice(&cur);
     cudaSetDevice(d->device);
     d->pool.release_all();
+    zs::free_pipes(d);
     if (d->d_enc) cudaFree(d->d_enc);
     if (d->d_dec) cudaFree(d->d_dec);
     if (d->d_mimg) cudaFree(d->d_mimg);

@@ -162,7 +162,16 @@ struct zs_dict {
     uint8_t plen[256];
     uint8_t pat[256][zs::kMaxPat];
     zs::ScratchPool pool;
+    struct zs_pipes *pipes = nullptr;  // host-to-host pipelines (pipeline.cu), made on first use
 };
+
+namespace zs {
+void free_pipes(zs_dict *d);
+uint64_t compress_scratch_tiles(const zs_dict *d, uint64_t n);
+cudaError_t launch_compress_any(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,
+                                uint64_t out_cap, uint64_t *index, uint64_t index_cap, DevResult *res,
+                                TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s);
+}  // namespace zs
 
 // ------------------------------------------------------------------------------------------------
 // Device helpers

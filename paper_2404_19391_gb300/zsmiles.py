@@ -53,6 +53,10 @@ class _ServerStats(ctypes.Structure):
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double)]
 
 
+class _PipelineOptions(ctypes.Structure):
+    _fields_ = [("chunk_bytes", ctypes.c_size_t), ("n_streams", ctypes.c_int)]
+
+
 OP_COMPRESS, OP_DECOMPRESS = 0, 1
 
 
@@ -115,6 +119,9 @@ def load_library(rebuild: bool = False) -> ctypes.CDLL:
         "zs_server_replay": (ctypes.c_int, [vp, vp, vp, vp, sz, vp, ctypes.POINTER(ctypes.c_double)]),
         "zs_serial_replay": (ctypes.c_int, [vp, vp, sz, vp, sz, vp, vp, vp, sz, vp, ctypes.POINTER(ctypes.c_double),
                                             vp]),
+        "zs_compress_host": (ctypes.c_int, [vp, vp, sz, ctypes.c_uint, vp, sz, vp, sz, pres,
+                                            ctypes.POINTER(_PipelineOptions)]),
+        "zs_decompress_host": (ctypes.c_int, [vp, vp, sz, vp, sz, pres, ctypes.POINTER(_PipelineOptions)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -406,6 +413,40 @@ def zs_serial_replay(d: Dictionary, d_comp: torch.Tensor, d_index: torch.Tensor,
     if st != OK:
         raise ZsError(st, _L().zs_last_error().decode())
     return lat[: len(requests)], mk.value
+
+
+def _host_ptr(t) -> tuple[int | None, int]:
+    """(address, length) of a host buffer: a CPU torch tensor or a contiguous numpy array."""
+    if isinstance(t, torch.Tensor):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        return (t.data_ptr() if t.numel() else None), t.numel()
+    if not t.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a contiguous array")
+    return (t.ctypes.data if t.size else None), t.size
+
+
+def zs_compress_host(d: Dictionary, h_in, flags: int, h_out, h_line_index=None, chunk_bytes: int = 0,
+                     n_streams: int = 0) -> Result:
+    """Host buffers in and out (uint8 input/output, uint64/int64 index); pinned memory lets copies overlap."""
+    pi, ni = _host_ptr(h_in)
+    po, no = _host_ptr(h_out)
+    px, nx = _host_ptr(h_line_index) if h_line_index is not None else (None, 0)
+    opt = _PipelineOptions(chunk_bytes, n_streams)
+    res = _Result()
+    st = _L().zs_compress_host(d.handle, pi, ni, flags, po, no, px, nx, ctypes.byref(res), ctypes.byref(opt))
+    _check(st, res)
+    return Result(res.out_len, res.n_lines, res.err_offset)
+
+
+def zs_decompress_host(d: Dictionary, h_in, h_out, chunk_bytes: int = 0, n_streams: int = 0) -> Result:
+    pi, ni = _host_ptr(h_in)
+    po, no = _host_ptr(h_out)
+    opt = _PipelineOptions(chunk_bytes, n_streams)
+    res = _Result()
+    st = _L().zs_decompress_host(d.handle, pi, ni, po, no, ctypes.byref(res), ctypes.byref(opt))
+    _check(st, res)
+    return Result(res.out_len, res.n_lines, res.err_offset)
 
 
 # ---- conveniences built only from the calls above ----------------------------------------------------
