@@ -360,6 +360,53 @@ def bench_serving(zs, d, dev, lines: int, n_req: int, rates):
                    "latency from scheduled arrival to result bytes in host memory"}
 
 
+ABLATION = [  # (dictionary file, what it varies), the paper's sweeps (Sec. V-C) on the synthetic stream
+    ("zs_default.zsd", "L_max 8, SMILES alphabet pre-populated, trained on pre-processed lines (default)"),
+    ("zs_lmax5.zsd", "L_max 5"),
+    ("zs_lmax15.zsd", "L_max 15"),
+    ("zs_no_alphabet.zsd", "no pre-populated alphabet"),
+    ("zs_raw_train.zsd", "trained on lines without ring-ID renumbering"),
+]
+
+
+def run_ablation(args):
+    """Compression ratio and kernel times of each ablation dictionary on the benchmark stream, with and
+    without pre-processing (one JSON line)."""
+    import torch
+    from paper_2404_19391_gb300 import zsmiles as zs
+    zs.load_library()
+    lines = args.lines
+    nbytes = synth.lines_size(synth.CFG1, 0, lines)
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    synth.generate_into(synth.CFG1, 0, lines, host.data_ptr(), nbytes)
+    x = host.cuda()
+    out = torch.empty(zs.zs_compress_bound(nbytes), dtype=torch.uint8, device="cuda")
+    idx = torch.empty(lines + 2, dtype=torch.int64, device="cuda")
+    rows = []
+    for fname, what in ABLATION:
+        d = zs.Dictionary(path=os.path.join(ROOT, "paper_2404_19391_gb300", "data", fname))
+        dec = torch.empty(d.decompress_bound(zs.zs_compress_bound(nbytes)) // 4 + nbytes, dtype=torch.uint8,
+                          device="cuda")
+        for flags in (zs.PREPROCESS, 0):
+            for _ in range(2):
+                r = zs.zs_compress(d, x, flags, out, idx)
+            kc = []
+            for _ in range(5):
+                r = zs.zs_compress(d, x, flags, out, idx)
+                kc.append(zs.zs_last_kernel_ms())
+            comp = out[: r.out_len]
+            kd = []
+            for _ in range(3):
+                rd = zs.zs_decompress(d, comp, dec)
+                kd.append(zs.zs_last_kernel_ms())
+            rows.append({"dictionary": fname, "varies": what, "preprocess": bool(flags), "lmax": d.lmax,
+                         "transducer": d.uses_transducer, "ratio": r.out_len / nbytes,
+                         "compress_ms": float(np.median(kc)), "compress_gbps_in": nbytes / np.median(kc) / 1e6,
+                         "decompress_ms": float(np.median(kd)), "decoded_bytes": rd.out_len})
+        d.close()
+    print(json.dumps({"ablation": rows, "workload": workload_desc(lines, nbytes)}), flush=True)
+
+
 def run_gpu(args):
     import torch
     from paper_2404_19391_gb300 import zsmiles as zs
@@ -549,9 +596,13 @@ def main():
     ap.add_argument("--serve-lines", type=int, default=synth.CFG4_LINES)
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rates", default="1000,10000,100000")
+    ap.add_argument("--ablation", action="store_true",
+                    help="instead of the benchmark line: ratio and kernel times of the ablation dictionaries")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.ablation:
+        run_ablation(args)
     else:
         run_gpu(args)
 

@@ -6,6 +6,13 @@ SMILES-alphabet pre-population (Sec. IV-B), L_min = 2 (Sec. IV-C), L_max = 8 (th
 generator are used.
 
     python -m oracle.make_dictionary [--lmax 8] [--out paper_2404_19391_gb300/data/zs_default.zsd]
+
+The ablation dictionaries next to it vary one choice each (the paper's sweeps, Sec. V-C):
+
+    python -m oracle.make_dictionary --lmax 5  --out paper_2404_19391_gb300/data/zs_lmax5.zsd
+    python -m oracle.make_dictionary --lmax 15 --out paper_2404_19391_gb300/data/zs_lmax15.zsd
+    python -m oracle.make_dictionary --no-alphabet --out paper_2404_19391_gb300/data/zs_no_alphabet.zsd
+    python -m oracle.make_dictionary --no-preprocess --out paper_2404_19391_gb300/data/zs_raw_train.zsd
 """
 from __future__ import annotations
 
@@ -35,8 +42,11 @@ def main() -> None:
     ap.add_argument("--lmax", type=int, default=8)
     ap.add_argument("--T", type=int, default=146)
     ap.add_argument("--out", default=os.path.join(_ROOT, "paper_2404_19391_gb300", "data", "zs_default.zsd"))
+    ap.add_argument("--no-alphabet", action="store_true", help="no pre-populated SMILES alphabet (Sec. IV-B)")
+    ap.add_argument("--no-preprocess", action="store_true", help="train on lines without ring-ID renumbering")
     args = ap.parse_args()
-    text = build_default(lmax=args.lmax, T=args.T)
+    text = build_default(lmax=args.lmax, T=args.T, alphabet=b"" if args.no_alphabet else dictgen.SMILES_ALPHABET,
+                         preprocess=not args.no_preprocess)
     with open(args.out, "wb") as f:
         f.write(text)
     print(args.out, len(text), hashlib.sha256(text).hexdigest())

@@ -640,15 +640,15 @@ __global__ void __launch_bounds__(kNT) compress_kernel(CompressArgs A)
                     const uint32_t m = reinterpret_cast<const uint32_t *>(ws)[1];
                     const SlowLayout sl = slow_layout(glen);
                     GlobalSink sink{A.out, out_at + loff, A.out_cap};
-                    emit_line(ws + sl.chs, ws + sl.text, m, plen_tab, sink);
+                    emit_line<false>(ws + sl.chs, ws + sl.text, m, plen_tab, sink);
                     if (fl & kLfNl) sink.put(kNl);
                 } else if (staged) {
                     SmemSink sink{ost + so + loff};
-                    emit_line(st + a, gbase + a, s_plen[r], plen_tab, sink);
+                    emit_line<false>(st + a, gbase + a, s_plen[r], plen_tab, sink);
                     if (fl & kLfNl) sink.put(kNl);
                 } else {
                     GlobalSink sink{A.out, out_at + loff, A.out_cap};
-                    emit_line(st + a, gbase + a, s_plen[r], plen_tab, sink);
+                    emit_line<false>(st + a, gbase + a, s_plen[r], plen_tab, sink);
                     if (fl & kLfNl) sink.put(kNl);
                 }
             }

@@ -125,15 +125,17 @@ static __device__ uint32_t preprocess_slow(const uint8_t *s, uint32_t n, uint8_t
     return w;
 }
 
-// Emission of one line: walk the choices front to back.
-template <class CP, class TP, class Sink>
+// Emission of one line: walk the choices front to back. A ' ' choice escapes the input byte at that
+// position. With ESC_DIGITS (the dictionary has no symbol byte below 0x20, so every choice up to ' ' is an
+// escape), a choice 1 + d (d = 0..9) is an escaped digit d, written as such.
+template <bool ESC_DIGITS, class CP, class TP, class Sink>
 __device__ __forceinline__ void emit_line(CP choice, TP raw, uint32_t n, const uint8_t *plen, Sink &out)
 {
     for (uint32_t i = 0; i < n;) {
         uint8_t s = choice[i];
-        if (s == kEsc) {
+        if (ESC_DIGITS ? (s <= kEsc) : (s == kEsc)) {
             out.put(kEsc);
-            out.put(raw[i]);
+            out.put((ESC_DIGITS && s != kEsc) ? (uint8_t)('0' + s - 1) : raw[i]);
             i += 1;
         } else {
             out.put(s);

@@ -59,7 +59,7 @@ struct CwArgs {
     uint32_t img_bytes;
     uint32_t n_classes;
     uint32_t start_state;
-    uint32_t _pad;
+    uint32_t esc_digits;      // the table codes an escaped digit d as choice 1 + d (MachineLayout::esc_digits)
     DevResult *g;             // tile counter, status bits, long-line scratch use
     uint8_t *slow;
     uint64_t slow_cap;
@@ -133,7 +133,9 @@ struct CW {
     }
 
     // Transducer walk over the class codes st[a, a+n) in place (last byte first); each code is replaced by
-    // the symbol chosen at that byte. Whole 4-byte words where the word belongs to the line.
+    // the symbol chosen at that byte. Whole 4-byte words where the word belongs to the line. *esc: the line
+    // has an escape the input bytes must supply (an escaped digit, when the table codes it as 1 + d, does not
+    // count: see MachineLayout::esc_digits).
     static __device__ __forceinline__ uint32_t parse_classes(uint8_t *st, uint32_t a, uint32_t n, const Ctx &C, bool *esc)
     {
         uint32_t q = C.q0, e = 0;
@@ -698,7 +700,9 @@ struct CW {
                 } else {
                     bool esc = false;
                     cost = parse_classes(st, a, (uint32_t)m, C, &esc);
-                    if (esc && modified) slow = true;  // escapes are emitted from the input bytes
+                    // escapes of other bytes are emitted from the input bytes, whose positions a compacted
+                    // (%nn-shortened) line no longer matches
+                    if (esc && modified && (!C.P->esc_digits || m != (int)n)) slow = true;
                     n = (uint32_t)m;
                 }
             }
@@ -800,15 +804,18 @@ struct CW {
                 const uint32_t m = reinterpret_cast<const uint32_t *>(ws)[1];
                 const SlowLayout sl = slow_layout(glen);
                 GlobalSink sink{A.out, out_at + loff, A.out_cap};
-                emit_line(ws + sl.chs, ws + sl.text, m, C.plen_tab, sink);
+                if (C.P->esc_digits) emit_line<true>(ws + sl.chs, ws + sl.text, m, C.plen_tab, sink);
+                else emit_line<false>(ws + sl.chs, ws + sl.text, m, C.plen_tab, sink);
                 if (fl & kLfNl) sink.put(kNl);
             } else if (staged) {
                 SmemSink sink{M.ost + so + loff};
-                emit_line(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
+                if (C.P->esc_digits) emit_line<true>(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
+                else emit_line<false>(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
                 if (fl & kLfNl) sink.put(kNl);
             } else {
                 GlobalSink sink{A.out, out_at + loff, A.out_cap};
-                emit_line(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
+                if (C.P->esc_digits) emit_line<true>(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
+                else emit_line<false>(S.st + a, gbase + a, S.plen[r], C.plen_tab, sink);
                 if (fl & kLfNl) sink.put(kNl);
             }
         }
@@ -985,6 +992,7 @@ cudaError_t cw_launch(const zs_dict *d, const TiledLaunch &L, unsigned flags, cu
     a.img_bytes = d->mlayout.img_bytes;
     a.n_classes = d->mlayout.n_classes;
     a.start_state = d->mlayout.start;
+    a.esc_digits = d->mlayout.esc_digits;
     a.g = L.g;
     a.slow = L.slow;
     a.slow_cap = L.slow_cap;

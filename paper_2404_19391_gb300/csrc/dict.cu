@@ -434,6 +434,14 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
         // budget), so the kernel's per-byte lookup needs no multiply
         std::vector<uint32_t> rows(mach.table);
         for (uint32_t &e : rows) e = (e & 0xFFFF0000u) | ((e & 0xFFFFu) * (uint32_t)n_classes);
+        ML.esc_digits = 1;  // needs every symbol byte above ' ' (so choices up to ' ' are escapes)
+        for (auto &en : entries)
+            if (en.sym < 0x20) ML.esc_digits = 0;
+        if (ML.esc_digits)  // an escape chosen at digit class d becomes the choice 1 + d
+            for (size_t i = 0; i < rows.size(); ++i) {
+                const uint32_t k = (uint32_t)(i % (size_t)n_classes);
+                if (k < 10 && (rows[i] >> 24) == (uint32_t)' ') rows[i] = (rows[i] & 0x00FFFFFFu) | ((1u + k) << 24);
+            }
         memcpy(mimg.data() + zs::kMOffTable, rows.data(), rows.size() * 4);
     }
 

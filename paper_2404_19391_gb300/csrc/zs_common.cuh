@@ -65,7 +65,11 @@ struct MachineLayout {
     uint32_t start;
     uint32_t off_table;
     uint32_t img_bytes;
-    uint32_t _pad[3];
+    // 1 when every symbol byte is above ' ': the table then codes an escape chosen at a digit d (class d)
+    // as the choice 1 + d, so the emitter writes the digit itself (a new ring label that the input bytes no
+    // longer show) rather than the input byte
+    uint32_t esc_digits;
+    uint32_t _pad[2];
 };
 constexpr uint32_t kMOffClsRep = 0, kMOffPlen = 8192, kMOffTable = 8448;
 constexpr uint32_t kMaxMachineBytes = 64u * 1024u;  // transition table budget in shared memory

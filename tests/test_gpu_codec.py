@@ -374,3 +374,14 @@ def test_long_pattern_dictionary(zs, long_dicts):
         r = zs.Plan(d, zs.OP_DECOMPRESS, [(x, out[:-16], None)], variant=v).run()[0]
         assert np.array_equal(out[: r.out_len].cpu().numpy(), oracle.decompress_stream(od, exp_comp))
         assert torch.all(out[r.out_len:] == 0xEE)
+
+
+@pytest.mark.parametrize("name", ["zs_lmax5.zsd", "zs_lmax15.zsd", "zs_no_alphabet.zsd", "zs_raw_train.zsd"])
+def test_ablation_dictionaries(zs, name):
+    """Every ablation dictionary (L_max 5 / 15, no alphabet, raw training) codes exactly like the oracle."""
+    data = open(os.path.join(ROOT, "paper_2404_19391_gb300", "data", name), "rb").read()
+    pair = (zs.Dictionary(data), oracle.Dict(data))
+    raw = synth.generate(synth.CFG0, 900, 3000)
+    for flags in (0, 1):
+        _, _, exp_comp, _ = check_compress(zs, pair, raw, flags=flags)
+        check_decompress(zs, pair, exp_comp)

@@ -110,3 +110,19 @@ def test_dictionary_file_validation():
     for b in bad:
         with pytest.raises(oracle.OracleError):
             oracle.Dict(b)
+
+
+def test_ablation_dictionaries_load():
+    """The committed ablation dictionaries (one varied choice each) are valid files with the stated settings."""
+    import os
+    data_dir = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2404_19391_gb300",
+                            "data")
+    want = {"zs_lmax5.zsd": (5, True), "zs_lmax15.zsd": (15, True), "zs_no_alphabet.zsd": (8, False),
+            "zs_raw_train.zsd": (8, True)}
+    for name, (lmax, alpha) in want.items():
+        text = open(os.path.join(data_dir, name), "rb").read()
+        lines = text.decode().splitlines()
+        assert lines[0] == "ZSDICT 1"
+        assert int(lines[1].split()[1]) == lmax
+        assert (lines[2] != "alphabet -") == alpha
+        oracle.Dict(text)  # parses and validates
