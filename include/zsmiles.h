@@ -256,6 +256,35 @@ double zs_plan_tuned_ms(const zs_plan *p, int v);  /* median kernel ms of varian
 double zs_plan_last_ms(const zs_plan *p);          /* kernel ms of the last run */
 void zs_plan_destroy(zs_plan *p);
 
+/* ---- Dictionary generation (Algorithm 1, Eq. 1; Sec. IV-B, IV-C) -------------------------------------
+ *
+ * Trains a dictionary on a device training stream ('\n'-separated lines; no zero bytes) and writes the
+ * .zsd file text to `out` (host, out_cap bytes; *out_len receives its size, also on ZS_ERR_CAPACITY).
+ *
+ * Steps:
+ *   - with ZS_PREPROCESS, the lines are ring-ID pre-processed first (Sec. IV-A);
+ *   - every substring of lmin..lmax bytes that holds no ' ' and no '\n' is counted on the GPU, overlapping
+ *     occurrences included;
+ *   - then T patterns are picked greedily by occ * (len - overlap) (Eq. 1), where overlap is the largest
+ *     overlap with a pattern already picked: |p| if p lies inside it, its length if it lies inside p, else
+ *     the longest suffix/prefix overlap either way;
+ *   - ties go to the higher count, then the longer pattern, then the bytewise smaller one; selection stops
+ *     once the best rank is <= 0.
+ *
+ * Symbols: the pre-populated SMILES alphabet (unless no_alphabet) maps each of its characters to itself;
+ * picks take the free printable bytes 0x21-0x7E, then 0xA1-0xFF, in pick order. Patterns are at most 8
+ * bytes here. Not in the paper: how overlap, ties and the symbol bytes are chosen (readings of Sec. IV-C).
+ */
+typedef struct zs_train_options {
+    int lmin;        /* shortest pattern (0: 2) */
+    int lmax;        /* longest pattern, <= 8 (0: 8) */
+    int T;           /* patterns to pick (0 or more than the free symbol bytes: all free symbol bytes) */
+    int no_alphabet; /* nonzero: no pre-populated alphabet */
+} zs_train_options;
+
+zs_status zs_train_dictionary(const uint8_t *d_train, size_t n, unsigned flags, const zs_train_options *opt,
+                              uint8_t *out, size_t out_cap, size_t *out_len, void *stream);
+
 /* ---- Host-to-host pipelines ------------------------------------------------------------------------
  *
  * zs_compress / zs_decompress take device buffers. These take HOST buffers and hide the copies: the stream

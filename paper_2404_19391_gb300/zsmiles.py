@@ -57,6 +57,10 @@ class _PipelineOptions(ctypes.Structure):
     _fields_ = [("chunk_bytes", ctypes.c_size_t), ("n_streams", ctypes.c_int)]
 
 
+class _TrainOptions(ctypes.Structure):
+    _fields_ = [("lmin", ctypes.c_int), ("lmax", ctypes.c_int), ("T", ctypes.c_int), ("no_alphabet", ctypes.c_int)]
+
+
 OP_COMPRESS, OP_DECOMPRESS = 0, 1
 
 
@@ -122,6 +126,8 @@ def load_library(rebuild: bool = False) -> ctypes.CDLL:
         "zs_compress_host": (ctypes.c_int, [vp, vp, sz, ctypes.c_uint, vp, sz, vp, sz, pres,
                                             ctypes.POINTER(_PipelineOptions)]),
         "zs_decompress_host": (ctypes.c_int, [vp, vp, sz, vp, sz, pres, ctypes.POINTER(_PipelineOptions)]),
+        "zs_train_dictionary": (ctypes.c_int, [vp, sz, ctypes.c_uint, ctypes.POINTER(_TrainOptions), vp, sz,
+                                               ctypes.POINTER(sz), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -447,6 +453,24 @@ def zs_decompress_host(d: Dictionary, h_in, h_out, chunk_bytes: int = 0, n_strea
     st = _L().zs_decompress_host(d.handle, pi, ni, po, no, ctypes.byref(res), ctypes.byref(opt))
     _check(st, res)
     return Result(res.out_len, res.n_lines, res.err_offset)
+
+
+def zs_train_dictionary(d_train: torch.Tensor, flags: int = PREPROCESS, lmin: int = 2, lmax: int = 8, T: int = 0,
+                        no_alphabet: bool = False, stream=None) -> bytes:
+    """Algorithm 1 on a device training stream; returns the .zsd file bytes."""
+    opt = _TrainOptions(lmin, lmax, T, 1 if no_alphabet else 0)
+    cap = 1 << 16
+    for _ in range(2):
+        buf = ctypes.create_string_buffer(cap)
+        n = ctypes.c_size_t(0)
+        st = _L().zs_train_dictionary(_ptr(d_train), d_train.numel(), flags, ctypes.byref(opt), buf, cap,
+                                      ctypes.byref(n), _stream(stream))
+        if st == ERR_CAPACITY:
+            cap = n.value
+            continue
+        _check(st)
+        return buf.raw[: n.value]
+    raise ZsError(ERR_CAPACITY, "dictionary text did not fit")
 
 
 # ---- conveniences built only from the calls above ----------------------------------------------------
