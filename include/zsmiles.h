@@ -49,7 +49,13 @@ typedef enum {
 } zs_status;
 
 /* zs_compress flags */
-enum { ZS_PREPROCESS = 1u }; /* renumber ring IDs before encoding (Sec. IV-A); "optionally", Sec. IV-D */
+enum {
+    ZS_PREPROCESS = 1u,      /* renumber ring IDs before encoding (Sec. IV-A); "optionally", Sec. IV-D */
+    ZS_PREPROCESS_OUTER = 2u /* with ZS_PREPROCESS only: the other reading of Sec. IV-A, kept as an
+                              * experiment - rings are labelled in the order they open, each with the
+                              * smallest ID held by no ring open at that point (the outermost of a nest
+                              * then gets the lower ID). Alone it is ZS_ERR_INVALID_ARG. */
+};
 
 typedef struct {
     uint64_t out_len;    /* bytes written to the output (or needed, on ZS_ERR_CAPACITY) */
@@ -105,7 +111,8 @@ size_t zs_decompress_bound(const zs_dict *d, size_t in_len);
  * Per line: if flags has ZS_PREPROCESS, renumber ring IDs (Sec. IV-A: IDs restart at 0, are reused once
  * a ring closes, and among overlapping rings the one that closes first - the innermost - gets the lower
  * ID; only the first space/tab-free field is touched; a line with an unclosed ring or bracket, a bad %
- * label, or one needing an ID above 99 is left as is). Then write the minimum-length sequence of
+ * label, or one needing an ID above 99 is left as is). ZS_PREPROCESS | ZS_PREPROCESS_OUTER labels the
+ * rings in opening order instead (see the flag). Then write the minimum-length sequence of
  * dictionary symbols (cost 1) and escapes (' ' + raw byte, cost 2) that spells the line (Sec. IV-D1);
  * among equally short encodings the one taking the longest piece at each step, front to back. Each
  * output line ends with '\n' exactly when its input line did.

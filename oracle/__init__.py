@@ -24,6 +24,7 @@ _lib = None
 
 OK, ERR_INVALID_ARG, ERR_BAD_DICT, ERR_CAPACITY, ERR_MALFORMED = 0, 1, 2, 3, 4
 PREPROCESS = 1
+PREPROCESS_OUTER = 2  # with PREPROCESS: label rings in opening order (the other reading of Sec. IV-A)
 
 
 class OracleError(RuntimeError):
@@ -56,12 +57,14 @@ def _L():
                 "oz_dict_lmax": (ctypes.c_int, [vp]),
                 "oz_dict_entries": (ctypes.c_int, [vp]),
                 "oz_preprocess_line": (sz, [vp, sz, vp]),
+                "oz_preprocess_line_ex": (sz, [vp, sz, vp, ctypes.c_int]),
                 "oz_compress_line": (sz, [vp, vp, sz, vp]),
                 "oz_parse_cost": (sz, [vp, vp, sz]),
                 "oz_decompress_line": (ctypes.c_int, [vp, vp, sz, vp, psz, psz]),
                 "oz_count_lines": (sz, [vp, sz]),
                 "oz_line_index": (sz, [vp, sz, vp]),
                 "oz_preprocess_stream": (ctypes.c_int, [vp, sz, vp, sz, psz]),
+                "oz_preprocess_stream_ex": (ctypes.c_int, [vp, sz, ctypes.c_int, vp, sz, psz]),
                 "oz_compress_stream": (ctypes.c_int, [vp, vp, sz, u, vp, sz, vp, psz, psz]),
                 "oz_decompress_stream": (ctypes.c_int, [vp, vp, sz, vp, sz, psz, psz]),
                 "oz_decompress_lines": (ctypes.c_int, [vp, vp, sz, vp, sz, vp, sz, vp, sz, vp, psz, psz]),
@@ -98,9 +101,10 @@ class Dict:
         return ctypes.cast(self._mem, ctypes.c_void_p)
 
 
-def preprocess_line(line: bytes) -> bytes:
+def preprocess_line(line: bytes, outer: bool = False) -> bytes:
+    """Ring-ID pre-processing of one line (Sec. IV-A); outer=True takes the opening-order reading."""
     out = ctypes.create_string_buffer(3 * len(line) + 1)
-    n = _L().oz_preprocess_line(line, len(line), out)
+    n = _L().oz_preprocess_line_ex(line, len(line), out, int(bool(outer)))
     return out.raw[:n]
 
 
@@ -136,11 +140,11 @@ def line_index(data) -> np.ndarray:
     return idx
 
 
-def preprocess_stream(data) -> np.ndarray:
+def preprocess_stream(data, outer: bool = False) -> np.ndarray:
     a, p = _buf(data)
     out = np.empty(3 * a.size + 16, dtype=np.uint8)
     n = ctypes.c_size_t(0)
-    st = _L().oz_preprocess_stream(p, a.size, out.ctypes.data, out.size, ctypes.byref(n))
+    st = _L().oz_preprocess_stream_ex(p, a.size, int(bool(outer)), out.ctypes.data, out.size, ctypes.byref(n))
     if st != OK:
         raise OracleError(st)
     return out[: n.value].copy()
@@ -234,12 +238,12 @@ def decompress_stream_parallel(d: Dict, data, threads: int | None = None) -> np.
     return np.concatenate(parts)
 
 
-def preprocess_stream_parallel(data, threads: int | None = None) -> np.ndarray:
+def preprocess_stream_parallel(data, threads: int | None = None, outer: bool = False) -> np.ndarray:
     a, _ = _buf(data)
     threads = threads or (os.cpu_count() or 1)
     ranges = split_at_lines(a, threads)
     if len(ranges) <= 1:
-        return preprocess_stream(a)
+        return preprocess_stream(a, outer)
     with ThreadPoolExecutor(len(ranges)) as ex:
-        parts = list(ex.map(lambda r: preprocess_stream(a[r[0]:r[1]]), ranges))
+        parts = list(ex.map(lambda r: preprocess_stream(a[r[0]:r[1]], outer), ranges))
     return np.concatenate(parts)

@@ -13,6 +13,11 @@ The ablation dictionaries next to it vary one choice each (the paper's sweeps, S
     python -m oracle.make_dictionary --lmax 15 --out paper_2404_19391_gb300/data/zs_lmax15.zsd
     python -m oracle.make_dictionary --no-alphabet --out paper_2404_19391_gb300/data/zs_no_alphabet.zsd
     python -m oracle.make_dictionary --no-preprocess --out paper_2404_19391_gb300/data/zs_raw_train.zsd
+
+and one varies the reading of Sec. IV-A: the training lines are pre-processed with rings labelled in
+opening order (the outermost of a nest gets the lower ID):
+
+    python -m oracle.make_dictionary --outer --out paper_2404_19391_gb300/data/zs_outer_train.zsd
 """
 from __future__ import annotations
 
@@ -31,9 +36,9 @@ import synth  # noqa: E402
 
 
 def build_default(lmax: int = 8, lmin: int = 2, T: int = 146, lines: int = synth.TRAIN_LINES,
-                  alphabet: bytes = dictgen.SMILES_ALPHABET, preprocess: bool = True) -> bytes:
+                  alphabet: bytes = dictgen.SMILES_ALPHABET, preprocess: bool = True, outer: bool = False) -> bytes:
     raw = synth.generate(synth.TRAIN, 0, lines)
-    pre = oracle.preprocess_stream(raw) if preprocess else raw
+    pre = oracle.preprocess_stream(raw, outer=outer) if preprocess else raw
     return dictgen.generate(pre, T=T, lmin=lmin, lmax=lmax, alphabet=alphabet)
 
 
@@ -44,9 +49,10 @@ def main() -> None:
     ap.add_argument("--out", default=os.path.join(_ROOT, "paper_2404_19391_gb300", "data", "zs_default.zsd"))
     ap.add_argument("--no-alphabet", action="store_true", help="no pre-populated SMILES alphabet (Sec. IV-B)")
     ap.add_argument("--no-preprocess", action="store_true", help="train on lines without ring-ID renumbering")
+    ap.add_argument("--outer", action="store_true", help="renumber ring IDs in opening order (outermost lower)")
     args = ap.parse_args()
     text = build_default(lmax=args.lmax, T=args.T, alphabet=b"" if args.no_alphabet else dictgen.SMILES_ALPHABET,
-                         preprocess=not args.no_preprocess)
+                         preprocess=not args.no_preprocess, outer=args.outer)
     with open(args.out, "wb") as f:
         f.write(text)
     print(args.out, len(text), hashlib.sha256(text).hexdigest())

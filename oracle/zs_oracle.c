@@ -19,6 +19,9 @@
  *     that would need a label above 99, is left unchanged;
  *   - "innermost gets the lower ID" = intervals are labelled in ascending order of their closing
  *     token, each with the smallest label not held by an already-labelled interval overlapping it;
+ *   - the other reading of that sentence, kept as an experiment (flags bit 1): intervals are labelled in
+ *     ascending order of their opening token by the same rule, so among nested rings the outermost gets
+ *     the lower label;
  *   - parse tie-break: among minimum-cost parses, at each step take the longest piece (an escape is a
  *     piece of length 1 and loses every tie);
  *   - an escape is written as ' ' followed by the raw byte (the decoder reads the space first).
@@ -220,8 +223,9 @@ static size_t copy_unchanged(const uint8_t *s, size_t n, uint8_t *out)
     return n;
 }
 
-/* Pre-process one line (no '\n'); out needs 3*n bytes. Returns the new length. */
-size_t oz_preprocess_line(const uint8_t *s, size_t n, uint8_t *out)
+/* Pre-process one line (no '\n'); out needs 3*n bytes. Returns the new length. outer = 0: intervals are
+ * labelled in closing order (the default reading); outer = 1: in opening order. */
+size_t oz_preprocess_line_ex(const uint8_t *s, size_t n, uint8_t *out, int outer)
 {
     size_t f = 0;
     while (f < n && s[f] != ' ' && s[f] != '\t') ++f;
@@ -279,13 +283,28 @@ size_t oz_preprocess_line(const uint8_t *s, size_t n, uint8_t *out)
             if (open_tok[l] >= 0) ok = 0;
     }
 
-    /* intervals were recorded in ascending closing position; label each with the smallest label not
-     * held by an already-labelled interval that overlaps it */
+    /* visiting order: intervals were recorded in ascending closing position; for the opening-order
+     * reading, visit them by ascending opening position instead (the opening tokens, left to right) */
+    size_t *order = (size_t *)malloc((niv + 1) * sizeof(size_t));
     if (ok) {
-        for (size_t k = 0; k < niv && ok; ++k) {
+        if (!outer) {
+            for (size_t k = 0; k < niv; ++k) order[k] = k;
+        } else {
+            size_t q = 0;
+            for (size_t k = 0; k < nt; ++k)
+                if (tok[k].ring && iv[tok[k].interval].o == k) order[q++] = (size_t)tok[k].interval;
+        }
+    }
+
+    /* label each interval, in that order, with the smallest label not held by an already-labelled
+     * interval that overlaps it */
+    if (ok) {
+        for (size_t q = 0; q < niv && ok; ++q) {
+            size_t k = order[q];
             int used[101];
             memset(used, 0, sizeof used);
-            for (size_t j = 0; j < k; ++j) {
+            for (size_t p = 0; p < q; ++p) {
+                size_t j = order[p];
                 int overlap = iv[j].o < iv[k].c && iv[k].o < iv[j].c;
                 if (overlap && iv[j].label <= 100) used[iv[j].label] = 1;
             }
@@ -295,6 +314,7 @@ size_t oz_preprocess_line(const uint8_t *s, size_t n, uint8_t *out)
             iv[k].label = lab;
         }
     }
+    free(order);
 
     size_t m;
     if (!ok) {
@@ -323,6 +343,8 @@ size_t oz_preprocess_line(const uint8_t *s, size_t n, uint8_t *out)
     free(iv);
     return m;
 }
+
+size_t oz_preprocess_line(const uint8_t *s, size_t n, uint8_t *out) { return oz_preprocess_line_ex(s, n, out, 0); }
 
 /* ------------------------------------------------------------------------------------------------ */
 /* Compression of one line (Sec. IV-D1): shortest path, match cost 1, escape cost 2                  */
@@ -434,15 +456,15 @@ size_t oz_line_index(const uint8_t *s, size_t n, uint64_t *index)
 size_t oz_preprocess_bound(size_t n) { return 3 * n + 16; }
 size_t oz_compress_bound(size_t n) { return 6 * n + 16; }
 
-/* Pre-process every line of a stream. */
-int oz_preprocess_stream(const uint8_t *in, size_t n, uint8_t *out, size_t cap, size_t *out_len)
+/* Pre-process every line of a stream; outer selects the opening-order reading. */
+int oz_preprocess_stream_ex(const uint8_t *in, size_t n, int outer, uint8_t *out, size_t cap, size_t *out_len)
 {
     size_t m = 0, i = 0;
     while (i < n) {
         size_t j = i;
         while (j < n && in[j] != '\n') ++j;
         if (m + 3 * (j - i) + 1 > cap) return OZ_ERR_CAPACITY;
-        m += oz_preprocess_line(in + i, j - i, out + m);
+        m += oz_preprocess_line_ex(in + i, j - i, out + m, outer);
         if (j < n) out[m++] = '\n';
         i = j + 1;
     }
@@ -450,12 +472,18 @@ int oz_preprocess_stream(const uint8_t *in, size_t n, uint8_t *out, size_t cap, 
     return OZ_OK;
 }
 
-/* Compress a stream; flags bit 0 = pre-process each line first. index (nullable) gets n_lines+1
- * offsets into the output. */
+int oz_preprocess_stream(const uint8_t *in, size_t n, uint8_t *out, size_t cap, size_t *out_len)
+{
+    return oz_preprocess_stream_ex(in, n, 0, out, cap, out_len);
+}
+
+/* Compress a stream; flags bit 0 = pre-process each line first, bit 1 (with bit 0) = in the
+ * opening-order reading. index (nullable) gets n_lines+1 offsets into the output. */
 int oz_compress_stream(const oz_dict *d, const uint8_t *in, size_t n, unsigned flags, uint8_t *out, size_t cap,
                        uint64_t *index, size_t *out_len, size_t *n_lines)
 {
     size_t m = 0, i = 0, k = 0;
+    if ((flags & ~3u) || (flags & 3u) == 2u) return OZ_ERR_INVALID_ARG;
     uint8_t *pre = (uint8_t *)malloc(3 * 65536);
     size_t pre_cap = 3 * 65536;
     while (i < n) {
@@ -467,7 +495,7 @@ int oz_compress_stream(const oz_dict *d, const uint8_t *in, size_t n, unsigned f
             pre = (uint8_t *)realloc(pre, pre_cap);
         }
         size_t pn;
-        if (flags & 1u) pn = oz_preprocess_line(in + i, ln, pre);
+        if (flags & 1u) pn = oz_preprocess_line_ex(in + i, ln, pre, (flags & 2u) != 0);
         else { memcpy(pre, in + i, ln); pn = ln; }
         if (m + 2 * pn + 1 > cap) { free(pre); return OZ_ERR_CAPACITY; }
         if (index) index[k] = m;

@@ -311,8 +311,8 @@ extern "C" zs_status zs_plan_create(const zs_dict *d, zs_op op, unsigned flags, 
         zs::set_error("zs_plan_create: unknown operation");
         return ZS_ERR_INVALID_ARG;
     }
-    if (flags & ~(unsigned)ZS_PREPROCESS) {
-        zs::set_error("zs_plan_create: unknown flag bits");
+    if (!zs::compress_flags_ok(flags)) {
+        zs::set_error("zs_plan_create: unknown flag bits, or ZS_PREPROCESS_OUTER without ZS_PREPROCESS");
         return ZS_ERR_INVALID_ARG;
     }
     if (n_shards > (size_t)ZS_MAX_SHARDS) {

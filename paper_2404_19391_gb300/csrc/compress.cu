@@ -137,11 +137,14 @@ __device__ __forceinline__ uint64_t block_excl_u64(uint64_t v, uint64_t *tmp, ui
 // interval that closed after it opened, so label x is taken iff the latest interval labelled x closed
 // after this one opened. lc[x] keeps (that close position + 1). The opening token is written as a
 // placeholder and patched when its ring closes; %nn labels shrink to one digit as they are copied.
+// With outer (rings labelled in opening order), an opening ring takes at once the smallest label no open
+// ring holds (held: bit x set while label x is held) and its closing token copies it.
 // Returns the new length, or -1 when the line needs the slow path (label >= 10, more than kSlowOpen
 // open rings). *modified is set if any ring label was rewritten (the line no longer equals its input
 // bytes). Invalid lines are restored from global memory.
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ int preprocess_inplace(uint8_t *st, int a, int n, const uint8_t *gsrc, bool *modified)
+__device__ __forceinline__ int preprocess_inplace(uint8_t *st, int a, int n, const uint8_t *gsrc, bool *modified,
+                                                  bool outer)
 {
     const uint32_t kEmpty = 0xFFFFFFFFu;
     uint32_t slot[kSlowOpen];
@@ -151,6 +154,7 @@ __device__ __forceinline__ int preprocess_inplace(uint8_t *st, int a, int n, con
 #pragma unroll
     for (int k = 0; k < 10; ++k) lc[k] = 0;
     int nopen = 0;
+    uint32_t held = 0;
     int w = 0, r = 0;
     bool in_br = false, bad = false;
     *modified = false;
@@ -189,7 +193,15 @@ __device__ __forceinline__ int preprocess_inplace(uint8_t *st, int a, int n, con
                     hit = k;
                     o = slot[k] >> 8;
                 }
-            if (hit >= 0) {  // closes the ring opened at write position o
+            if (hit >= 0 && outer) {  // closes the ring opened at write position o: same label
+                const uint32_t nl = (uint32_t)(st[a + (int)o] - '0');
+                st[a + w] = (uint8_t)('0' + nl);
+                held &= ~(1u << nl);
+#pragma unroll
+                for (int k = 0; k < kSlowOpen; ++k)
+                    if (k == hit) slot[k] = kEmpty;
+                --nopen;
+            } else if (hit >= 0) {  // closes the ring opened at write position o
                 int nl = -1;
 #pragma unroll
                 for (int x = 9; x >= 0; --x)
@@ -214,7 +226,15 @@ __device__ __forceinline__ int preprocess_inplace(uint8_t *st, int a, int n, con
                         done = true;
                     }
                 ++nopen;
-                st[a + w] = '0';
+                if (outer) {
+                    const uint32_t fr = ~held & 0x3FFu;
+                    if (fr == 0) return -1;  // needs a two-digit label
+                    const int nl = __ffs(fr) - 1;
+                    held |= 1u << nl;
+                    st[a + w] = (uint8_t)('0' + nl);
+                } else {
+                    st[a + w] = '0';
+                }
             }
             w += 1;
             r += tl;
@@ -520,7 +540,9 @@ __global__ void __launch_bounds__(kNT) compress_kernel(CompressArgs A)
                 if (!slow) {
                     bool modified = false;
                     int m = (int)n;
-                    if (A.flags & ZS_PREPROCESS) m = preprocess_inplace(st, (int)a, (int)n, gbase + a, &modified);
+                    if (A.flags & ZS_PREPROCESS)
+                        m = preprocess_inplace(st, (int)a, (int)n, gbase + a, &modified,
+                                               (A.flags & ZS_PREPROCESS_OUTER) != 0);
                     if (m < 0) {
                         slow = true;
                     } else {
@@ -559,7 +581,8 @@ __global__ void __launch_bounds__(kNT) compress_kernel(CompressArgs A)
                             if (A.flags & ZS_PREPROCESS) {
                                 m = preprocess_slow(A.in + gs, (uint32_t)glen, ws + sl.text, ws + sl.tok,
                                                     reinterpret_cast<int32_t *>(ws + sl.tables),
-                                                    reinterpret_cast<int32_t *>(ws + sl.tables) + 100);
+                                                    reinterpret_cast<int32_t *>(ws + sl.tables) + 100,
+                                                    (A.flags & ZS_PREPROCESS_OUTER) != 0);
                             } else {
                                 for (uint32_t i = 0; i < glen; ++i) ws[sl.text + i] = A.in[gs + i];
                                 m = (uint32_t)glen;
@@ -820,8 +843,8 @@ extern "C" zs_status zs_compress(const zs_dict *d, const uint8_t *d_in, size_t i
         zs::set_error("zs_compress: NULL argument");
         return ZS_ERR_INVALID_ARG;
     }
-    if (flags & ~(unsigned)ZS_PREPROCESS) {
-        zs::set_error("zs_compress: unknown flag bits");
+    if (!zs::compress_flags_ok(flags)) {
+        zs::set_error("zs_compress: unknown flag bits, or ZS_PREPROCESS_OUTER without ZS_PREPROCESS");
         return ZS_ERR_INVALID_ARG;
     }
     int dev = -1;

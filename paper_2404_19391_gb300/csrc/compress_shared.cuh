@@ -24,11 +24,15 @@ __device__ __forceinline__ uint32_t nl_bits16(uint4 v) { return eq_bits16(v, 0x0
 
 // ------------------------------------------------------------------------------------------------
 // Pre-processing, slow path: any line, work space in global memory. Two passes: label every ring
-// token (same streaming rule, labels up to 99), then write the relabelled line (1- or 3-byte labels).
+// token (labels up to 99), then write the relabelled line (1- or 3-byte labels).
+//   - closing order (the default): a ring that closes takes the smallest label whose latest ring closed
+//     before this one opened; lcv[x] = (latest close of label x) + 1;
+//   - opening order (outer): a ring that opens takes the smallest label no open ring holds, and its
+//     closing token repeats it; lcv[x] = 1 while label x is held.
 // tok: one byte per ring token; lcv/open_tok: 100 ints each. Returns the new length.
 // ------------------------------------------------------------------------------------------------
 static __device__ uint32_t preprocess_slow(const uint8_t *s, uint32_t n, uint8_t *out, uint8_t *tok, int32_t *lcv,
-                                    int32_t *open_tok)
+                                           int32_t *open_tok, bool outer)
 {
     for (int k = 0; k < 100; ++k) {
         lcv[k] = 0;
@@ -62,7 +66,25 @@ static __device__ uint32_t preprocess_slow(const uint8_t *s, uint32_t n, uint8_t
         } else if (c >= '0' && c <= '9') {
             lab = c - '0';
         }
-        if (lab >= 0) {
+        if (lab >= 0 && outer) {
+            if (open_tok[lab] < 0) {
+                int nl = 0;
+                while (nl < 100 && lcv[nl] != 0) ++nl;
+                if (nl > 99) {
+                    ok = false;
+                    break;
+                }
+                lcv[nl] = 1;
+                tok[ord] = (uint8_t)nl;
+                open_tok[lab] = ord;
+            } else {
+                const uint8_t nl = tok[open_tok[lab]];
+                tok[ord] = nl;
+                lcv[nl] = 0;
+                open_tok[lab] = -1;
+            }
+            ++ord;
+        } else if (lab >= 0) {
             if (open_tok[lab] < 0) {
                 open_tok[lab] = ord;
             } else {

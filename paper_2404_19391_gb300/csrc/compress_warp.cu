@@ -67,7 +67,9 @@ struct CwArgs {
     int64_t stall_tile;
 };
 
-template <class Geo>
+// OUTER: ring IDs renumbered in opening order (ZS_PREPROCESS_OUTER) instead of closing order; a template
+// parameter so that the default kernel carries none of the other reading's code.
+template <class Geo, bool OUTER>
 struct CW {
     static constexpr int kMW = Geo::kWarps;
     static constexpr int kMNT = 32 * kMW;
@@ -184,7 +186,7 @@ struct CW {
     // opened still holds: lc[x] = position + 1 of the latest close that took label x. Both label bytes of
     // a ring are written when it closes (a %nn label's '%' becomes the digit and its two digits a deletion
     // mark, squeezed out at the end), so only the open rings are remembered, in the lane's column of `opn`
-    // (stride 32): slot x < 10 = position + 1 of the open label x, slots 10 + 2j / 11 + 2j = (label + 1,
+    // (stride 32): slot x < 10 = position + 1 of the open label x (bit 15 set if it was written %0x), slots 10 + 2j / 11 + 2j = (label + 1,
     // position) of up to 8 open %nn labels. A line found invalid at its end (unclosed ring or bracket, bad
     // %) is restored from its raw bytes and left as it is.
     // Returns the new length, or -1 for the slow path (a label >= 10 needed, more than 8 open %nn labels,
@@ -204,7 +206,7 @@ struct CW {
     #pragma unroll
         for (int x = 0; x < 10; ++x) lc[x] = 0;
         for (int x = 0; x < 10 + 2 * kOpen2; ++x) opn[x * 32] = 0;
-        uint32_t dopen = 0, nopen2 = 0, skipto = 0;
+        uint32_t dopen = 0, nopen2 = 0, skipto = 0, held = 0;
         bool in_br = false, bad = false, any_pct = false, done = false, need_slow = false, wrote = false;
         const uint32_t clast = (end - 1) >> 4;
         uint32_t c = a >> 4;
@@ -253,12 +255,14 @@ struct CW {
             const uint32_t q = p - a;
             int po = -1;  // position of the ring's open token, if this token closes it
             bool opct = false;
-            if (label < 10) {
+            if (label < 10) {  // a digit, or %0d; bit 15 of the slot: the opening token was %0d
                 if ((dopen >> label) & 1u) {
-                    po = (int)opn[label * 32] - 1;
+                    const uint32_t v = opn[label * 32];
+                    po = (int)(v & 0x7FFFu) - 1;
+                    opct = (v >> 15) != 0;
                     dopen &= ~(1u << label);
                 } else {
-                    opn[label * 32] = (uint16_t)(q + 1);
+                    opn[label * 32] = (uint16_t)((q + 1) | (pct ? 0x8000u : 0u));
                     dopen |= 1u << label;
                 }
             } else {
@@ -285,8 +289,25 @@ struct CW {
                     break;
                 }
             }
+            if (OUTER) {  // opening order: an opening ring takes the smallest free label at once
+                if (po < 0) {
+                    const uint32_t fr = ~held & 0x3FFu;
+                    if (fr == 0) {  // needs a two-digit label
+                        need_slow = true;
+                        break;
+                    }
+                    const uint32_t nl = (uint32_t)__ffs(fr) - 1u;
+                    held |= 1u << nl;
+                    put(q, nl, pct);
+                } else {
+                    const uint32_t nl = st[a + (uint32_t)po];
+                    held &= ~(1u << nl);
+                    put(q, nl, pct);
+                }
+                wrote = true;
+                continue;
+            }
             if (po < 0) continue;
-            if (label < 10) opct = false;
             int nl = -1;
     #pragma unroll
             for (int x = 9; x >= 0; --x)
@@ -456,6 +477,7 @@ struct CW {
         uint64_t dmap = 0;
         uint32_t dopen = 0;
         bool need_slow = false;
+        uint32_t held = 0;  // opening order: bit x set while label x is held
         for (uint32_t it = 0; it < steps; ++it) {
             const bool act = it < my_steps;
             const int wb = D.pop();
@@ -464,6 +486,18 @@ struct CW {
             const bool open = (dopen >> label) & 1u;
             const uint32_t ko = open ? (uint32_t)(dmap >> (5 * label)) & 31u : 0u;
             const uint32_t eo = tok[ko * 32];
+            if (OUTER) {  // an opening ring takes the smallest free label, its closing token repeats it
+                const bool opening = act && !open, closing = act && open;
+                const uint32_t fr = ~held & 0x3FFu;
+                need_slow = need_slow || (opening && fr == 0u);  // would need a two-digit label
+                const uint32_t nl = closing ? (eo >> 12) : (fr ? (uint32_t)__ffs(fr) - 1u : 0u);
+                held = (opening && fr != 0u) ? (held | (1u << nl)) : held;
+                held = closing ? (held & ~(1u << nl)) : held;
+                if (act) tok[it * 32] = (uint16_t)(rel | (nl << 12));
+                dmap = opening ? ((dmap & ~(31ull << (5 * label))) | ((uint64_t)it << (5 * label))) : dmap;
+                dopen ^= act ? (1u << label) : 0u;
+                continue;
+            }
             const uint32_t t = ((eo & 0x7Fu) + 1u) * 0x01010101u;  // lc <= open position + 1: free
             const uint32_t fr = pack4(__vcmpleu4(lc0, t)) | (pack4(__vcmpleu4(lc1, t)) << 4) |
                                 (pack4(__vcmpleu4(lc2, t)) << 8);
@@ -691,7 +725,8 @@ struct CW {
                 bool modified = false;
                 int m = (int)n;
                 if (C.P->flags & ZS_PREPROCESS) {
-                    m = preprocess_bits(st, M.imask, kImaskChunks, a, n, n <= kBitMax, M.tok + lane, &modified);
+                    m = preprocess_bits(st, M.imask, kImaskChunks, a, n, n <= kBitMax, M.tok + lane,
+                                               &modified);
                     if (m == -2)
                         m = preprocess_classes(st, M.imask, a, n, gbase + a, C, M.tok + lane, &modified);
                 }
@@ -733,7 +768,8 @@ struct CW {
                         if (C.P->flags & ZS_PREPROCESS) {
                             m = preprocess_slow(A.in + gs, (uint32_t)glen, ws + sl.text, ws + sl.tok,
                                                 reinterpret_cast<int32_t *>(ws + sl.tables),
-                                                reinterpret_cast<int32_t *>(ws + sl.tables) + 100);
+                                                reinterpret_cast<int32_t *>(ws + sl.tables) + 100,
+                                                OUTER);
                         } else {
                             for (uint32_t i = 0; i < glen; ++i) ws[sl.text + i] = A.in[gs + i];
                             m = (uint32_t)glen;
@@ -960,10 +996,10 @@ struct CW {
     }
 };
 
-template <class Geo>
+template <class Geo, bool OUTER>
 __global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_warp_kernel(const CwArgs P)
 {
-    CW<Geo>::run(&P);
+    CW<Geo, OUTER>::run(&P);
 }
 
 // The compiled geometries. Variant 0 (about 30 lines of 46 bytes per warp tile, so mostly one lane round;
@@ -976,11 +1012,11 @@ using CwV2 = CwGeom<12, 2048, 1024, 96, 1472>;
 template <class Geo>
 size_t cw_smem(const zs_dict *d)
 {
-    return CW<Geo>::kMW * sizeof(typename CW<Geo>::WarpMem) + d->mlayout.img_bytes;
+    return CW<Geo, false>::kMW * sizeof(typename CW<Geo, false>::WarpMem) + d->mlayout.img_bytes;
 }
 
-template <class Geo>
-cudaError_t cw_launch(const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s)
+template <class Geo, bool OUTER>
+cudaError_t cw_launch_as(const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s)
 {
     CwArgs a{};
     a.one = L.one;
@@ -1004,18 +1040,26 @@ cudaError_t cw_launch(const zs_dict *d, const TiledLaunch &L, unsigned flags, cu
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     static int set_smem = -1;
     if (set_smem != smem) {
-        cudaError_t e = cudaFuncSetAttribute(compress_warp_kernel<Geo>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem);
+        cudaError_t e = cudaFuncSetAttribute(compress_warp_kernel<Geo, OUTER>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         set_smem = smem;
     }
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compress_warp_kernel<Geo>, CW<Geo>::kMNT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compress_warp_kernel<Geo, OUTER>, CW<Geo, OUTER>::kMNT,
+                                                  smem);
     if (per < 1) per = 1;
     uint64_t grid = std::min<uint64_t>((L.total_tiles + Geo::kWarps - 1) / Geo::kWarps, (uint64_t)per * (uint64_t)sms);
     if (grid == 0) grid = 1;
-    compress_warp_kernel<Geo><<<(unsigned)grid, CW<Geo>::kMNT, smem, s>>>(a);
+    compress_warp_kernel<Geo, OUTER><<<(unsigned)grid, CW<Geo, OUTER>::kMNT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <class Geo>
+cudaError_t cw_launch(const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s)
+{
+    return (flags & ZS_PREPROCESS_OUTER) ? cw_launch_as<Geo, true>(d, L, flags, s)
+                                         : cw_launch_as<Geo, false>(d, L, flags, s);
 }
 
 struct CwEntry {

@@ -153,8 +153,8 @@ zs_status run_pipeline(const zs_dict *dc, zs_op op, const uint8_t *h_in, size_t 
         zs::set_error(std::string(what) + ": NULL argument");
         return ZS_ERR_INVALID_ARG;
     }
-    if (flags & ~(unsigned)ZS_PREPROCESS) {
-        zs::set_error(std::string(what) + ": unknown flag bits");
+    if (!zs::compress_flags_ok(flags)) {
+        zs::set_error(std::string(what) + ": unknown flag bits, or ZS_PREPROCESS_OUTER without ZS_PREPROCESS");
         return ZS_ERR_INVALID_ARG;
     }
     int dev = -1;

@@ -200,8 +200,8 @@ extern "C" zs_status zs_train_dictionary(const uint8_t *d_train, size_t n, unsig
         return ZS_ERR_INVALID_ARG;
     }
     *out_len = 0;
-    if (flags & ~(unsigned)ZS_PREPROCESS) {
-        zs::set_error("zs_train_dictionary: unknown flag bits");
+    if (!zs::compress_flags_ok(flags)) {
+        zs::set_error("zs_train_dictionary: unknown flag bits, or ZS_PREPROCESS_OUTER without ZS_PREPROCESS");
         return ZS_ERR_INVALID_ARG;
     }
     const int lmin = opt && opt->lmin > 0 ? opt->lmin : 2;
@@ -250,7 +250,7 @@ extern "C" zs_status zs_train_dictionary(const uint8_t *d_train, size_t n, unsig
             st = ZS_ERR_OOM;
         }
         zs_result r{};
-        if (st == ZS_OK) st = zs_compress(alpha, d_train, n, ZS_PREPROCESS, comp, ccap, nullptr, 0, &r, stream);
+        if (st == ZS_OK) st = zs_compress(alpha, d_train, n, flags, comp, ccap, nullptr, 0, &r, stream);
         zs_result r2{};
         if (st == ZS_OK) st = zs_decompress(alpha, comp, r.out_len, pre, pcap, &r2, stream);
         if (alpha) zs_free_dictionary(alpha);

@@ -170,6 +170,12 @@ struct zs_dict {
 };
 
 namespace zs {
+// zs_compress flags: ZS_PREPROCESS, optionally with ZS_PREPROCESS_OUTER; nothing else.
+inline bool compress_flags_ok(unsigned flags)
+{
+    return (flags & ~(unsigned)(ZS_PREPROCESS | ZS_PREPROCESS_OUTER)) == 0 &&
+           (!(flags & ZS_PREPROCESS_OUTER) || (flags & ZS_PREPROCESS));
+}
 void free_pipes(zs_dict *d);
 uint64_t compress_scratch_tiles(const zs_dict *d, uint64_t n);
 cudaError_t launch_compress_any(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,

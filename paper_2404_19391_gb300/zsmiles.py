@@ -19,6 +19,7 @@ OK, ERR_INVALID_ARG, ERR_BAD_DICT, ERR_CAPACITY, ERR_MALFORMED, ERR_CUDA, ERR_TI
 STATUS_NAMES = ["ZS_OK", "ZS_ERR_INVALID_ARG", "ZS_ERR_BAD_DICT", "ZS_ERR_CAPACITY", "ZS_ERR_MALFORMED",
                 "ZS_ERR_CUDA", "ZS_ERR_TIMEOUT", "ZS_ERR_OOM"]
 PREPROCESS = 1
+PREPROCESS_OUTER = 2  # with PREPROCESS: rings labelled in opening order (the other reading of Sec. IV-A)
 
 DEFAULT_DICTIONARY = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "zs_default.zsd")
 

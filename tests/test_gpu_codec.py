@@ -39,7 +39,7 @@ def dicts(zs, request):
 
 
 def dev(a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint8)).cuda()
+    return torch.from_numpy(np.array(a, dtype=np.uint8, copy=True)).cuda()
 
 
 def check_compress(zs, dicts, raw, flags=1, offset_in=0, offset_out=0):
@@ -133,6 +133,7 @@ EDGE = {
     "cr_tab": b"C1CC1\r\nCCO\tname 1\nC C\n",
     "invalid_rings": b"C1CC\nC[NH3+C1CC1\nC%1CC\nC%(12)CC%(12)\n",
     "percent_labels": b"C%12CC%12\nC%45C%67CC%67C%45\n",
+    "percent_low_labels": b"C%05CC5\nC5CC%05\nC%01CC%01\nC%00C%09CC%09C%00\nC%07C%12CC7C%12\n",
     "bracket_digits": b"[13CH3]C1CC1\n[NH3+]C5CC5\n",
     "space_field": b"C1CC1 id12 C2\n",
 }
@@ -376,12 +377,14 @@ def test_long_pattern_dictionary(zs, long_dicts):
         assert torch.all(out[r.out_len:] == 0xEE)
 
 
-@pytest.mark.parametrize("name", ["zs_lmax5.zsd", "zs_lmax15.zsd", "zs_no_alphabet.zsd", "zs_raw_train.zsd"])
+@pytest.mark.parametrize("name", ["zs_lmax5.zsd", "zs_lmax15.zsd", "zs_no_alphabet.zsd", "zs_raw_train.zsd",
+                                  "zs_outer_train.zsd"])
 def test_ablation_dictionaries(zs, name):
-    """Every ablation dictionary (L_max 5 / 15, no alphabet, raw training) codes exactly like the oracle."""
+    """Every ablation dictionary (L_max 5 / 15, no alphabet, raw training, opening-order training) codes
+    exactly like the oracle, with pre-processing off and in either reading."""
     data = open(os.path.join(ROOT, "paper_2404_19391_gb300", "data", name), "rb").read()
     pair = (zs.Dictionary(data), oracle.Dict(data))
     raw = synth.generate(synth.CFG0, 900, 3000)
-    for flags in (0, 1):
+    for flags in (0, 1, 3):
         _, _, exp_comp, _ = check_compress(zs, pair, raw, flags=flags)
         check_decompress(zs, pair, exp_comp)

@@ -118,7 +118,7 @@ def test_ablation_dictionaries_load():
     data_dir = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2404_19391_gb300",
                             "data")
     want = {"zs_lmax5.zsd": (5, True), "zs_lmax15.zsd": (15, True), "zs_no_alphabet.zsd": (8, False),
-            "zs_raw_train.zsd": (8, True)}
+            "zs_raw_train.zsd": (8, True), "zs_outer_train.zsd": (8, True)}
     for name, (lmax, alpha) in want.items():
         text = open(os.path.join(data_dir, name), "rb").read()
         lines = text.decode().splitlines()
