@@ -420,7 +420,8 @@ extern "C" double zs_plan_last_ms(const zs_plan *p) { return p ? (double)p->last
 extern "C" zs_status zs_compress_batch(const zs_dict *d, const zs_shard *shards, size_t n_shards, unsigned flags,
                                        zs_result *res, void *stream)
 {
-    zs_plan_options o{zs::kDefaultVariant, 0, 0};
+    const int v = d ? zs::compress_default_variant(d) : -1;
+    zs_plan_options o{v >= 0 ? v : zs::kDefaultVariant, 0, 0};
     zs_plan *p = nullptr;
     zs_status st = zs_plan_create(d, ZS_OP_COMPRESS, flags, shards, n_shards, &o, &p);
     if (st != ZS_OK) return st;

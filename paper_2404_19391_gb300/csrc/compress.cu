@@ -774,9 +774,17 @@ cudaError_t launch_compress(const zs_dict *d, const uint8_t *in, uint64_t n, uns
 
 uint64_t compress_tiles(uint64_t n) { return (n + kTB - 1) / kTB; }
 
-// The transducer kernel runs when the dictionary has a transducer and its tables fit in shared memory;
-// otherwise the generic kernel (automaton + window scan per byte) runs.
-bool use_transducer(const zs_dict *d) { return compress_warp_fits(kDefaultVariant, d); }
+// The transducer kernel's geometry for a dictionary: variant 0 (19 warps per SM) when its transducer
+// image leaves room for them, else variant 1 (the same tile, 18 warps); -1 when neither fits, and the
+// generic kernel (automaton + window scan per byte) runs.
+int compress_default_variant(const zs_dict *d)
+{
+    for (int v = 0; v <= 1; ++v)
+        if (compress_warp_fits(v, d)) return v;
+    return -1;
+}
+
+bool use_transducer(const zs_dict *d) { return compress_default_variant(d) >= 0; }
 
 }  // namespace zs
 
@@ -786,24 +794,25 @@ namespace zs {
 
 uint64_t compress_scratch_tiles(const zs_dict *d, uint64_t n)
 {
-    return use_transducer(d) ? tiles_for(n, compress_warp_variant(kDefaultVariant)->tile_bytes) : compress_tiles(n);
+    const int v = compress_default_variant(d);
+    return v >= 0 ? tiles_for(n, compress_warp_variant(v)->tile_bytes) : compress_tiles(n);
 }
 
 cudaError_t launch_compress_any(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,
                                 uint64_t out_cap, uint64_t *index, uint64_t index_cap, DevResult *res,
                                 TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s)
 {
-    if (!use_transducer(d))
-        return launch_compress(d, in, n, flags, out, out_cap, index, index_cap, res, tiles, slow, slow_cap, s);
+    const int v = compress_default_variant(d);
+    if (v < 0) return launch_compress(d, in, n, flags, out, out_cap, index, index_cap, res, tiles, slow, slow_cap, s);
     TiledLaunch L{};
     L.one = single_shard(in, n, out, out_cap, index, index_cap, tiles, res,
-                         tiles_for(n, compress_warp_variant(kDefaultVariant)->tile_bytes));
+                         tiles_for(n, compress_warp_variant(v)->tile_bytes));
     L.n_shards = 1;
     L.total_tiles = L.one.ntiles;
     L.g = res;
     L.slow = slow;
     L.slow_cap = slow_cap;
-    return launch_compress_warp(kDefaultVariant, d, L, flags, s);
+    return launch_compress_warp(v, d, L, flags, s);
 }
 
 }  // namespace zs

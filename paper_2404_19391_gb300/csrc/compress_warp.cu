@@ -42,7 +42,8 @@ struct CwGeom {
     static constexpr int kOut = OUTW;       // staged output bytes per tile
 };
 
-constexpr int kTokMax = 32;           // ring labels per line on the fast path
+constexpr int kTokMax = 26;           // ring labels per line on the bit-mask path (the class-code path's
+                                      // open-ring slots, 10 + 2 x 8, fit in the same column)
 constexpr int kFastMax = 2047;        // longest line on the fast path (token positions use 11 bits)
 constexpr uint32_t kLongLine = 1u << 30;
 constexpr uint8_t kLfNl = 1, kLfSlow = 2;
@@ -713,8 +714,12 @@ struct CW {
         for (uint32_t r = lane; r < nb; r += 32) S.perm[M.hist[S.olen[r]] + S.loff[r]] = (uint8_t)r;
         __syncwarp();
 
+        // Lines go to lanes longest first in snake order (round k: lane l takes sorted line 32k + l for even
+        // k, 32k + 31 - l for odd k), so a lane with a long line in one round gets a short one in the next.
         bool lane_slow = false;
-        for (uint32_t qd = lane; qd < nb; qd += 32) {
+        for (uint32_t q0 = 0; q0 < nb; q0 += 32) {
+            const uint32_t qd = q0 + ((q0 & 32u) ? 31u - lane : lane);
+            if (qd >= nb) continue;
             const uint32_t r = S.perm[qd];
             const uint32_t a = S.start[r];
             uint8_t fl = S.flag[r];
@@ -827,7 +832,9 @@ struct CW {
         const uint32_t lane = C.lane;
         const uint8_t *gbase = A.in + tile_base(t) - 16;
         const uint32_t so = (uint32_t)(((uint64_t)(uintptr_t)A.out + out_at) & 15u);
-        for (uint32_t qd = lane; qd < nb; qd += 32) {
+        for (uint32_t q0 = 0; q0 < nb; q0 += 32) {  // the same snake order as the encode loop
+            const uint32_t qd = q0 + ((q0 & 32u) ? 31u - lane : lane);
+            if (qd >= nb) continue;
             const uint32_t r = S.perm[qd];
             const uint32_t a = S.start[r];
             const uint8_t fl = S.flag[r];
@@ -1003,11 +1010,14 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_warp_kernel(cons
 }
 
 // The compiled geometries. Variant 0 (about 30 lines of 46 bytes per warp tile, so mostly one lane round;
-// 18 warps per SM) is the default; variant 1 keeps long lines (hundreds of bytes) several to a tile;
-// variant 2 sits between.
-using CwV0 = CwGeom<18, 1408, 512, 64, 960>;
-using CwV1 = CwGeom<8, 4096, 1024, 192, 1728>;
-using CwV2 = CwGeom<12, 2048, 1024, 96, 1472>;
+// 19 warps per SM) is the default, and variant 1 the same tile with 18 warps for a dictionary whose
+// transducer image leaves too little shared memory for 19; variant 2 keeps long lines (hundreds of bytes)
+// several to a tile; variant 3 (about 60 lines per tile: two lane rounds, which the snake order balances)
+// suits a mix with a long tail of lines.
+using CwV0 = CwGeom<19, 1408, 512, 64, 960>;
+using CwV1 = CwGeom<18, 1408, 512, 64, 960>;
+using CwV2 = CwGeom<8, 4096, 1024, 192, 1728>;
+using CwV3 = CwGeom<12, 2816, 512, 96, 1920>;
 
 template <class Geo>
 size_t cw_smem(const zs_dict *d)
@@ -1075,9 +1085,10 @@ constexpr CwEntry cw_entry(const char *name)
 }
 
 const CwEntry kCw[] = {
-    cw_entry<CwV0>("compress w18 t1408"),
-    cw_entry<CwV1>("compress w8 t4096"),
-    cw_entry<CwV2>("compress w12 t2048"),
+    cw_entry<CwV0>("compress w19 t1408"),
+    cw_entry<CwV1>("compress w18 t1408"),
+    cw_entry<CwV2>("compress w8 t4096"),
+    cw_entry<CwV3>("compress w12 t2816"),
 };
 constexpr int kNumCw = (int)(sizeof(kCw) / sizeof(kCw[0]));
 

@@ -548,6 +548,7 @@ inline ShardView single_shard(const uint8_t *in, uint64_t n, uint8_t *out, uint6
 int compress_warp_variants();
 const KernelVariant *compress_warp_variant(int v);
 bool compress_warp_fits(int v, const zs_dict *d);
+int compress_default_variant(const zs_dict *d);  // the geometry zs_compress uses, or -1: the generic kernel
 cudaError_t launch_compress_warp(int v, const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s);
 int decompress_variants();
 const KernelVariant *decompress_variant(int v);

@@ -81,10 +81,11 @@ def _decompress_shards(zs, d, comps):
     return [(i, o[:-16], None) for i, o in zip(ins, outs)], outs
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", range(8))
 def test_plan_every_variant(zs, dicts, expected, variant):
     d, od = dicts
-    assert variant < zs.zs_kernel_variants(zs.OP_COMPRESS)
+    if variant >= zs.zs_kernel_variants(zs.OP_COMPRESS):
+        pytest.skip("not a compiled variant")
     shards, outs, idxs = _compress_shards(zs, RAW)
     p = zs.Plan(d, zs.OP_COMPRESS, shards, flags=1, variant=variant, use_graph=True)
     assert p.variant == variant
@@ -156,10 +157,12 @@ def test_many_small_shards(zs, dicts):
     _check_compressed(p.run(), shards, outs, idxs, exp)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", range(8))
 def test_tile_boundaries_every_variant(zs, dicts, variant):
     """Lines ending just before, at and after each variant's tile and halo boundaries."""
     d, od = dicts
+    if variant >= zs.zs_kernel_variants(zs.OP_COMPRESS):
+        pytest.skip("not a compiled variant")
     name = zs.zs_kernel_variant_name(zs.OP_COMPRESS, variant)
     tile = int(name.split("t")[-1])
     raws = []
