@@ -774,8 +774,8 @@ cudaError_t launch_compress(const zs_dict *d, const uint8_t *in, uint64_t n, uns
 
 uint64_t compress_tiles(uint64_t n) { return (n + kTB - 1) / kTB; }
 
-// The transducer kernel's geometry for a dictionary: variant 0 (19 warps per SM) when its transducer
-// image leaves room for them, else variant 1 (the same tile, 18 warps); -1 when neither fits, and the
+// The transducer kernel's geometry for a dictionary: variant 0 (20 warps per SM) when its transducer
+// image leaves room for them, else variant 1 (the same tile, 19 warps); -1 when neither fits, and the
 // generic kernel (automaton + window scan per byte) runs.
 int compress_default_variant(const zs_dict *d)
 {

@@ -33,17 +33,16 @@ namespace {
 using namespace cx;
 
 // Tile geometry of one compiled variant of the kernel.
-template <int W, int TW, int HW, int MAXL, int OUTW>
+template <int W, int TW, int HW, int MAXL, int OUTW, int TOK>
 struct CwGeom {
     static constexpr int kWarps = W;        // warps per CTA
     static constexpr int kTile = TW;        // owned bytes per warp tile
     static constexpr int kHalo = HW;        // bytes staged past the tile for the tile's last line
     static constexpr int kMaxLines = MAXL;  // lines per batch
     static constexpr int kOut = OUTW;       // staged output bytes per tile
+    static constexpr int kTok = TOK;        // per-lane column: ring labels of a line on the bit-mask path, and
+                                            // the class-code path's open-ring slots (10 + 2 per open %nn label)
 };
-
-constexpr int kTokMax = 26;           // ring labels per line on the bit-mask path (the class-code path's
-                                      // open-ring slots, 10 + 2 x 8, fit in the same column)
 constexpr int kFastMax = 2047;        // longest line on the fast path (token positions use 11 bits)
 constexpr uint32_t kLongLine = 1u << 30;
 constexpr uint8_t kLfNl = 1, kLfSlow = 2;
@@ -79,17 +78,18 @@ struct CW {
     static constexpr int kStW = 16 + kTW + kHW;  // staged bytes: the byte before the tile (index 15), tile, halo
     static constexpr int kMaxLW = Geo::kMaxLines;
     static constexpr int kOutW = Geo::kOut;
+    static constexpr int kTokMax = Geo::kTok;
     static constexpr uint32_t kImaskChunks = (kStW + 31) / 16 + 2;
-    static_assert(kTW % 16 == 0 && kHW % 16 == 0 && kOutW % 16 == 0 && kMaxLW % 8 == 0 && kMaxLW <= 256,
+    static_assert(kTW % 16 == 0 && kHW % 16 == 0 && kOutW % 16 == 0 && kMaxLW % 8 == 0 && kMaxLW <= 256 &&
+                      kTokMax >= 12 && kTokMax <= 32,
                   "tile geometry");
 
     struct alignas(16) Slot {
         uint8_t st[kStW + 48];
         uint16_t start[kMaxLW + 8];
         uint16_t plen[kMaxLW];
-        uint32_t olen[kMaxLW];
-        uint32_t loff[kMaxLW];
-        uint32_t soff[kMaxLW];
+        uint32_t olen[kMaxLW];  // per line: length bucket (sort), output bytes, then (in place) output offset
+        uint32_t soff[kMaxLW];  // per line: rank in its bucket (sort), then slow-path work space / 16
         uint8_t flag[kMaxLW];
         uint8_t perm[kMaxLW];
         uint64_t bar;
@@ -187,13 +187,13 @@ struct CW {
     // opened still holds: lc[x] = position + 1 of the latest close that took label x. Both label bytes of
     // a ring are written when it closes (a %nn label's '%' becomes the digit and its two digits a deletion
     // mark, squeezed out at the end), so only the open rings are remembered, in the lane's column of `opn`
-    // (stride 32): slot x < 10 = position + 1 of the open label x (bit 15 set if it was written %0x), slots 10 + 2j / 11 + 2j = (label + 1,
-    // position) of up to 8 open %nn labels. A line found invalid at its end (unclosed ring or bracket, bad
+    // (stride 32): slot x < 10 = position + 1 of the open label x (bit 15 set if it was written %0x), slots
+    // 10 + 2j / 11 + 2j = (label + 1, position) of up to kOpen2 open %nn labels. A line found invalid at its end (unclosed ring or bracket, bad
     // %) is restored from its raw bytes and left as it is.
-    // Returns the new length, or -1 for the slow path (a label >= 10 needed, more than 8 open %nn labels,
+    // Returns the new length, or -1 for the slow path (a label >= 10 needed, more than kOpen2 open %nn labels,
     // or more than kFastMax bytes). *modified: some ring label was rewritten.
     static constexpr uint8_t kClsDel = 0xFE;  // a deleted byte (the digits of a rewritten %nn label)
-    static constexpr int kOpen2 = 8;
+    static constexpr int kOpen2 = (kTokMax - 10) / 2;  // open %nn labels the class-code path follows
 
     static __device__ __forceinline__ int preprocess_classes(uint8_t *st, const uint32_t *imask, uint32_t a, uint32_t n,
                                                              const uint8_t *raw, const Ctx &C, uint16_t *opn,
@@ -701,7 +701,7 @@ struct CW {
             S.flag[r] = fl;
             const uint32_t bucket = 63u - min(len >> 3, 63u);
             S.olen[r] = bucket;
-            S.loff[r] = atomicAdd(&M.hist[bucket], 1u);
+            S.soff[r] = atomicAdd(&M.hist[bucket], 1u);
         }
         __syncwarp();
         {
@@ -711,7 +711,7 @@ struct CW {
             M.hist[2 * lane + 1] = ex + h0;
         }
         __syncwarp();
-        for (uint32_t r = lane; r < nb; r += 32) S.perm[M.hist[S.olen[r]] + S.loff[r]] = (uint8_t)r;
+        for (uint32_t r = lane; r < nb; r += 32) S.perm[M.hist[S.olen[r]] + S.soff[r]] = (uint8_t)r;
         __syncwarp();
 
         // Lines go to lanes longest first in snake order (round k: lane l takes sorted line 32k + l for even
@@ -813,8 +813,9 @@ struct CW {
             for (uint32_t k = 0; k < per; ++k) {
                 const uint32_t r = lane * per + k;
                 if (r < nb) {
-                    S.loff[r] = (uint32_t)acc;
-                    acc += S.olen[r];
+                    const uint32_t o = S.olen[r];
+                    S.olen[r] = (uint32_t)acc;  // output bytes become the output offset
+                    acc += o;
                 }
             }
         }
@@ -838,7 +839,7 @@ struct CW {
             const uint32_t r = S.perm[qd];
             const uint32_t a = S.start[r];
             const uint8_t fl = S.flag[r];
-            const uint32_t loff = S.loff[r];
+            const uint32_t loff = S.olen[r];  // the output offset by now
             if (A.index && line0 + r < A.index_cap) A.index[line0 + r] = out_at + loff;
             if (fl & kLfSlow) {
                 if (S.soff[r] == 0xFFFFFFFFu) continue;
@@ -1010,14 +1011,14 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_warp_kernel(cons
 }
 
 // The compiled geometries. Variant 0 (about 30 lines of 46 bytes per warp tile, so mostly one lane round;
-// 19 warps per SM) is the default, and variant 1 the same tile with 18 warps for a dictionary whose
-// transducer image leaves too little shared memory for 19; variant 2 keeps long lines (hundreds of bytes)
-// several to a tile; variant 3 (about 60 lines per tile: two lane rounds, which the snake order balances)
-// suits a mix with a long tail of lines.
-using CwV0 = CwGeom<19, 1408, 512, 64, 960>;
-using CwV1 = CwGeom<18, 1408, 512, 64, 960>;
-using CwV2 = CwGeom<8, 4096, 1024, 192, 1728>;
-using CwV3 = CwGeom<12, 2816, 512, 96, 1920>;
+// 20 warps per SM, five per scheduler, the most that keep 96 registers a thread) is the default, and
+// variant 1 the same tile with 19 warps for a dictionary whose transducer image leaves too little shared
+// memory for 20; variant 2 keeps long lines (hundreds of bytes) several to a tile; variant 3 (about 60
+// lines per tile: two lane rounds, which the snake order balances) suits a mix with a long tail of lines.
+using CwV0 = CwGeom<20, 1408, 512, 64, 960, 26>;
+using CwV1 = CwGeom<19, 1408, 512, 64, 960, 26>;
+using CwV2 = CwGeom<8, 4096, 1024, 192, 1728, 26>;
+using CwV3 = CwGeom<12, 2816, 512, 96, 1920, 26>;
 
 template <class Geo>
 size_t cw_smem(const zs_dict *d)
@@ -1085,8 +1086,8 @@ constexpr CwEntry cw_entry(const char *name)
 }
 
 const CwEntry kCw[] = {
-    cw_entry<CwV0>("compress w19 t1408"),
-    cw_entry<CwV1>("compress w18 t1408"),
+    cw_entry<CwV0>("compress w20 t1408"),
+    cw_entry<CwV1>("compress w19 t1408"),
     cw_entry<CwV2>("compress w8 t4096"),
     cw_entry<CwV3>("compress w12 t2816"),
 };
