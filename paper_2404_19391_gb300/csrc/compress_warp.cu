@@ -1018,7 +1018,7 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_warp_kernel(cons
 using CwV0 = CwGeom<20, 1408, 512, 64, 960, 26>;
 using CwV1 = CwGeom<19, 1408, 512, 64, 960, 26>;
 using CwV2 = CwGeom<8, 4096, 1024, 192, 1728, 26>;
-using CwV3 = CwGeom<12, 2816, 512, 96, 1920, 26>;
+using CwV3 = CwGeom<12, 2816, 512, 128, 1920, 26>;
 
 template <class Geo>
 size_t cw_smem(const zs_dict *d)

@@ -23,7 +23,7 @@ def env():
 
 def _pinned(a: np.ndarray) -> torch.Tensor:
     t = torch.empty(a.size, dtype=torch.uint8, pin_memory=True)
-    t.copy_(torch.from_numpy(a))
+    t.copy_(torch.from_numpy(np.array(a, dtype=np.uint8, copy=True)))
     return t
 
 
