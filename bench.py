@@ -511,6 +511,16 @@ def run_gpu(args):
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     r0 = zs.zs_compress(d, x, zs.PREPROCESS, comp, idx)  # the resident store random access reads
     store, store_idx = comp[: r0.out_len], idx[: r0.n_lines + 1]
+    # ---- the line index rebuilt from the compressed stream alone (zs_build_line_index), checked against the
+    # index the compressor wrote; outside the timed step ----
+    idx2 = torch.empty(idx.numel(), dtype=torch.int64, device=dev)
+    li_ms = []
+    for k in range(6):
+        n_li = zs.zs_build_line_index(store, idx2)
+        if k:
+            li_ms.append(zs.zs_last_kernel_ms())
+    li_same = n_li == r0.n_lines and torch.equal(idx2[: n_li + 1], store_idx)
+    del idx2
     io = {}
 
     def e2e_step():
@@ -543,6 +553,8 @@ def run_gpu(args):
     kc = float(np.mean(kms["compress"]))
     kd = float(np.mean(kms["decompress"]))
     kl = float(np.mean(kms["lines"]))
+    li_k = float(np.median(li_ms))
+    li_alg = sizes["comp"] + 8 * (sizes["n_lines"] + 1)  # read the stream, write n_lines + 1 offsets
     comp_bytes = nbytes + sizes["comp"] + 8 * (sizes["n_lines"] + 1)   # read input, write output + index
     dec_bytes = sizes["comp"] + sizes["dec"]                            # read compressed, write decoded
     achieved_c = comp_bytes / (kc * 1e-3) / 1e9
@@ -579,6 +591,9 @@ def run_gpu(args):
             "decompress": {"kernel_ms": kd, "gbps_in": sizes["comp"] / (kd * 1e-3) / 1e9,
                            "gbps_out": sizes["dec"] / (kd * 1e-3) / 1e9, "hbm_gbps": achieved_d,
                            "hbm_frac": achieved_d / peak, "hbm_frac_nominal": achieved_d / HBM_NOMINAL_GBS},
+            "line_index": {"kernel_ms": li_k, "gbps_in": sizes["comp"] / (li_k * 1e-3) / 1e9,
+                           "hbm_gbps": li_alg / (li_k * 1e-3) / 1e9, "hbm_frac": li_alg / (li_k * 1e-3) / 1e9 / peak,
+                           "identical_to_compress_index": bool(li_same)},
             "random_access": {"ids": RA_IDS, "kernel_ms": kl, "lines_per_s": RA_IDS / (kl * 1e-3),
                               "p50_ms": float(np.percentile(kms["lines"], 50)),
                               "p99_ms": float(np.percentile(kms["lines"], 99))},
