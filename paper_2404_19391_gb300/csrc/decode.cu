@@ -8,10 +8,21 @@ namespace zs {
 namespace {
 
 // ------------------------------------------------------------------------------------------------
-// Line index: newline ranks via warp-segmented 16-byte loads, block scan, decoupled look-back.
+// Line index: newline ranks via warp-segmented 16-byte loads, a block scan and a warp-wide decoupled
+// look-back, software-pipelined like the codec kernels:
+//   - a CTA claims tile t+1 and issues its loads before it finishes tile t;
+//   - it publishes a tile's aggregate as soon as the tile is scanned, but looks back for that tile only
+//     after scanning the next one. By then the predecessors have had a whole tile's time to publish their
+//     inclusive prefixes, so the walk back is short. Looking back at once would make every in-flight tile
+//     walk back to the last finished one, 32 records per round trip.
+// A tile's entries are staged in shared memory (two buffers, by rank within the tile) and written out as one
+// contiguous run of coalesced 8-byte stores; a tile with more newlines than a buffer holds writes its entries
+// directly.
 // ------------------------------------------------------------------------------------------------
 constexpr int kINT = 256;
-constexpr int kIT = 16384;  // bytes per tile: each warp 2 KiB = 4 x 512
+constexpr int kIChunks = 8;                       // 16-byte chunks per lane: each warp 4 KiB = 8 x 512
+constexpr int kIT = kINT / 32 * kIChunks * 512;   // bytes per tile (32 KiB)
+constexpr uint32_t kIdxStage = 2048;              // staged index entries per tile and buffer (16 KiB)
 
 struct IdxArgs {
     const uint8_t *in;
@@ -32,77 +43,146 @@ __device__ __forceinline__ uint32_t zero_bits4(uint32_t t)
     return ((z >> 7) & 1u) | ((z >> 14) & 2u) | ((z >> 21) & 4u) | ((z >> 28) & 8u);
 }
 
-__device__ __forceinline__ uint32_t nl_bits(const uint8_t *in, uint64_t n, uint64_t p, bool aligned)
+// The 16 bytes at p (bytes at or past n read as 0, which is no newline).
+__device__ __forceinline__ uint4 load16(const uint8_t *in, uint64_t n, uint64_t p, bool aligned)
 {
-    if (p >= n) return 0;
-    if (aligned && p + 16 <= n) {
-        uint4 v = __ldg(reinterpret_cast<const uint4 *>(in + p));
-        const uint32_t k = 0x0A0A0A0Au;
-        return zero_bits4(v.x ^ k) | (zero_bits4(v.y ^ k) << 4) | (zero_bits4(v.z ^ k) << 8) |
-               (zero_bits4(v.w ^ k) << 12);
+    if (aligned && p + 16 <= n) return __ldg(reinterpret_cast<const uint4 *>(in + p));
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    for (uint32_t q = 0; q < 16; ++q)
+        if (p + q < n) w[q >> 2] |= (uint32_t)in[p + q] << (8 * (q & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ uint32_t nl_bits16v(uint4 v)
+{
+    const uint32_t k = 0x0A0A0A0Au;
+    return zero_bits4(v.x ^ k) | (zero_bits4(v.y ^ k) << 4) | (zero_bits4(v.z ^ k) << 8) |
+           (zero_bits4(v.w ^ k) << 12);
+}
+
+__device__ __forceinline__ uint64_t tile_warp_base(uint64_t t, int warp)
+{
+    return t * (uint64_t)kIT + (uint64_t)warp * (kIChunks * 512u);
+}
+
+// Visits the newlines of a warp's part of a tile in byte order: f(rank, position after the newline), ranks
+// counted from `rank` (the warp's first).
+template <class F>
+__device__ __forceinline__ void for_each_newline(const uint32_t *bits, uint64_t wbase, uint64_t rank, int lane, F f)
+{
+#pragma unroll
+    for (int it = 0; it < kIChunks; ++it) {
+        uint32_t b = bits[it];
+        const uint32_t c = __popc(b);
+        const uint32_t inc = warp_incl_u32(c);
+        uint64_t rk = rank + inc - c;
+        const uint64_t p0 = wbase + (uint64_t)it * 512u + (uint64_t)lane * 16u;
+        while (b) {
+            const int q = __ffs(b) - 1;
+            b &= b - 1;
+            f(rk, p0 + (uint64_t)q + 1u);
+            ++rk;
+        }
+        rank += __shfl_sync(0xffffffffu, inc, 31);
     }
-    uint32_t bits = 0;
-    for (uint32_t q = 0; q < 16 && p + q < n; ++q)
-        if (in[p + q] == kNl) bits |= 1u << q;
-    return bits;
 }
 
 __global__ void __launch_bounds__(kINT) line_index_kernel(IdxArgs A)
 {
     __shared__ uint64_t scan[2 * (kINT / 32 + 1)];
-    __shared__ uint64_t s_tile, s_E;
+    __shared__ uint64_t s_tile, s_next, s_E;
+    __shared__ uint64_t s_idx[2][kIdxStage];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool aligned = A.in_aligned != 0;
     uint32_t *status = &A.res->status;
-    for (;;) {
-        if (tid == 0) s_tile = atomicAdd(&A.res->tile_counter, 1ull);
+
+    // the pending tile: scanned and its aggregate published, its look-back and writes still to do
+    bool pending = false;
+    uint64_t t_pend = 0, ta_pend = 0, wrank_pend = 0;
+    uint32_t bits_pend[kIChunks];
+    uint32_t buf = 0;
+    auto finish = [&]() {  // looks back for the pending tile and writes its entries (whole block)
+        const uint64_t tp = t_pend;
+        if (warp == 0) {
+            uint64_t ea = 0, eb = 0;
+            if (tp > 0) lookback_warp(A.tiles, tp, &ea, &eb, A.limit_ns, status);
+            if (lane == 0) {
+                if (tp > 0 && (int64_t)tp != A.stall_tile) publish(&A.tiles[tp], 2u, ea + ta_pend, 0);
+                s_E = ea;
+                if (tp == 0 && A.index_cap > 0) A.index[0] = 0;
+                if (tp == A.ntiles - 1) {
+                    const uint64_t nl = ea + ta_pend;
+                    const bool open_last = A.in[A.n - 1] != kNl;
+                    const uint64_t lines = nl + (open_last ? 1u : 0u);
+                    A.res->n_lines = lines;
+                    if (open_last && lines < A.index_cap) A.index[lines] = A.n;
+                }
+            }
+        }
         __syncthreads();
-        const uint64_t t = s_tile;
-        if (t >= A.ntiles) break;
-        const uint64_t wbase = t * (uint64_t)kIT + (uint64_t)warp * 2048u;
-        uint32_t bits[4];
+        const uint64_t E = s_E;
+        if (ta_pend <= kIdxStage) {
+            const uint64_t *src = s_idx[buf ^ 1u];
+            for (uint32_t j = (uint32_t)tid; j < (uint32_t)ta_pend; j += kINT) {
+                const uint64_t g = E + 1u + j;
+                if (g < A.index_cap) A.index[g] = src[j];
+            }
+        } else {
+            for_each_newline(bits_pend, tile_warp_base(tp, warp), E + wrank_pend, lane, [&](uint64_t rk, uint64_t v) {
+                if (rk + 1 < A.index_cap) A.index[rk + 1] = v;
+            });
+        }
+    };
+
+    if (tid == 0) s_tile = atomicAdd(&A.res->tile_counter, 1ull);
+    __syncthreads();
+    uint64_t t = s_tile;
+    uint4 v[kIChunks];
+    if (t < A.ntiles) {
+#pragma unroll
+        for (int it = 0; it < kIChunks; ++it)
+            v[it] = load16(A.in, A.n, tile_warp_base(t, warp) + (uint64_t)it * 512u + (uint64_t)lane * 16u, aligned);
+    }
+    while (t < A.ntiles) {
+        uint32_t bits[kIChunks];
         uint32_t cnt = 0;
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-            bits[it] = nl_bits(A.in, A.n, wbase + (uint64_t)it * 512u + (uint64_t)lane * 16u, A.in_aligned != 0);
+        for (int it = 0; it < kIChunks; ++it) {
+            bits[it] = nl_bits16v(v[it]);
             cnt += __popc(bits[it]);
         }
+        if (tid == 0) s_next = atomicAdd(&A.res->tile_counter, 1ull);
         uint64_t xa, xb, ta, tb;
-        block_excl2_u64<kINT>(cnt, 0, scan, &xa, &xb, &ta, &tb);
-        if (tid == 0) {
-            const bool stall = (int64_t)t == A.stall_tile;
-            if (!stall) publish(&A.tiles[t], t == 0 ? 2u : 1u, ta, 0);
-            uint64_t ea = 0, eb = 0;
-            if (t > 0) lookback(A.tiles, t, &ea, &eb, A.limit_ns, status);
-            if (t > 0 && !stall) publish(&A.tiles[t], 2u, ea + ta, 0);
-            s_E = ea;
-            if (t == 0 && A.index_cap > 0) A.index[0] = 0;
-            if (t == A.ntiles - 1) {
-                const uint64_t nl = ea + ta;
-                const bool open_last = A.in[A.n - 1] != kNl;
-                const uint64_t lines = nl + (open_last ? 1u : 0u);
-                A.res->n_lines = lines;
-                if (open_last && lines < A.index_cap) A.index[lines] = A.n;
-            }
-        }
-        __syncthreads();
-        // each newline at p ends line k and starts line k+1 at p+1 (the last one marks the end); chunks of
-        // a warp interleave (iteration-major), so ranks come from the warp's base plus per-iteration scans
-        uint64_t rank = s_E + __shfl_sync(0xffffffffu, xa, 0);
+        block_excl2_u64<kINT>(cnt, 0, scan, &xa, &xb, &ta, &tb);  // its barriers also publish s_next
+        const uint64_t tn = s_next;
+        if (tn < A.ntiles) {  // the next tile's reads, in flight while the pending tile looks back
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-            uint32_t b = bits[it];
-            const uint32_t c = __popc(b);
-            const uint32_t inc = warp_incl_u32(c);
-            uint64_t rk = rank + inc - c;
-            const uint64_t p0 = wbase + (uint64_t)it * 512u + (uint64_t)lane * 16u;
-            while (b) {
-                const int q = __ffs(b) - 1;
-                b &= b - 1;
-                if (rk + 1 < A.index_cap) A.index[rk + 1] = p0 + (uint64_t)q + 1u;
-                ++rk;
-            }
-            rank += __shfl_sync(0xffffffffu, inc, 31);
+            for (int it = 0; it < kIChunks; ++it)
+                v[it] = load16(A.in, A.n, tile_warp_base(tn, warp) + (uint64_t)it * 512u + (uint64_t)lane * 16u,
+                               aligned);
         }
+        if (tid == 0 && (int64_t)t != A.stall_tile) publish(&A.tiles[t], t == 0 ? 2u : 1u, ta, 0);
+        // each newline at p ends line k and starts line k+1 at p+1 (the last one marks the end)
+        const uint64_t wrank = __shfl_sync(0xffffffffu, xa, 0);  // the warp's first rank within the tile
+        if (ta <= kIdxStage) {  // the same for the whole block
+            uint64_t *dst = s_idx[buf];
+            for_each_newline(bits, tile_warp_base(t, warp), wrank, lane, [&](uint64_t rk, uint64_t v) {
+                dst[rk] = v;
+            });
+        }
+        if (pending) finish();
+        __syncthreads();  // the written buffer and s_E are reused; s_next is rewritten
+        pending = true;
+        t_pend = t;
+        ta_pend = ta;
+        wrank_pend = wrank;
+#pragma unroll
+        for (int it = 0; it < kIChunks; ++it) bits_pend[it] = bits[it];
+        buf ^= 1u;
+        t = tn;
+    }
+    if (pending) {
+        finish();
         __syncthreads();
     }
 }
