@@ -5,10 +5,12 @@
 // last ends with '\n'). Up to n_streams chunks are in flight, each on its own stream with its own device
 // buffers:
 //   copy in (H2D) -> tiled kernel -> result record back to pinned host memory
-// The host thread retires chunks in order. Once a chunk's output size is known it places the chunk:
+// The host thread retires chunks in order. Once a chunk's output size is known it places the chunk, on the
+// slot's own copy-out stream:
 //   - rebases the chunk's line index by the bytes before it (a small kernel);
 //   - copies output and index to their offsets in the caller's host buffers (D2H);
-//   - then reuses the slot for a later chunk.
+//   - then reuses the slot for a later chunk: its copy in starts at once, and only its kernel, which
+//     rewrites the slot's output buffers, waits for the copy out.
 // Copies in both directions and the kernels of different chunks overlap.
 #include <algorithm>
 #include <cstring>
@@ -21,8 +23,11 @@
 namespace {
 
 struct PipeSlot {
-    cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaStream_t st = nullptr;      // copy in, kernel, result record
+    cudaEvent_t ev = nullptr;       // the chunk's result record has landed
+    cudaStream_t out_st = nullptr;  // rebase and copy out
+    cudaEvent_t out_ev = nullptr;   // the slot's output buffers have been copied out
+    bool out_pending = false;
     uint8_t *d_in = nullptr, *d_out = nullptr, *slow = nullptr;
     uint64_t *d_idx = nullptr;
     void *scratch = nullptr;  // DevResult + TileState[tiles]
@@ -49,8 +54,11 @@ void free_pipe(Pipe &p)
 {
     for (PipeSlot &s : p.slots) {
         if (s.st) cudaStreamSynchronize(s.st);
+        if (s.out_st) cudaStreamSynchronize(s.out_st);
         if (s.ev) cudaEventDestroy(s.ev);
+        if (s.out_ev) cudaEventDestroy(s.out_ev);
         if (s.st) cudaStreamDestroy(s.st);
+        if (s.out_st) cudaStreamDestroy(s.out_st);
         if (s.d_in) cudaFree(s.d_in);
         if (s.d_out) cudaFree(s.d_out);
         if (s.d_idx) cudaFree(s.d_idx);
@@ -102,6 +110,8 @@ zs_status get_pipe(zs_dict *d, zs_op op, size_t chunk, int nst, Pipe **out)
     for (PipeSlot &s : p.slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.out_st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.out_ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMalloc(&s.d_in, chunk + 16);
         if (e == cudaSuccess) e = cudaMalloc(&s.d_out, out_bound(d, op, chunk));
         if (e == cudaSuccess && op == ZS_OP_COMPRESS) e = cudaMalloc(&s.d_idx, (chunk + 2) * sizeof(uint64_t));
@@ -199,6 +209,8 @@ zs_status run_pipeline(const zs_dict *dc, zs_op op, const uint8_t *h_in, size_t 
         cudaError_t e2 = cudaMemcpyAsync(s.d_in, h_in + off, len, cudaMemcpyHostToDevice, s.st);
         if (e2 == cudaSuccess)
             e2 = cudaMemsetAsync(s.scratch, 0, sizeof(zs::DevResult) + ntiles * sizeof(zs::TileState), s.st);
+        if (e2 == cudaSuccess && s.out_pending) e2 = cudaStreamWaitEvent(s.st, s.out_ev, 0);
+        s.out_pending = false;
         if (e2 == cudaSuccess)
             e2 = op == ZS_OP_COMPRESS
                      ? zs::launch_compress_any(d, s.d_in, len, flags, s.d_out, out_bound(d, op, len),
@@ -242,21 +254,27 @@ zs_status run_pipeline(const zs_dict *dc, zs_op op, const uint8_t *h_in, size_t 
                 T.msg = std::string(what) + ": malformed input at byte " + std::to_string(T.err_offset);
             }
         }
-        // place the chunk (clipped to the caller's capacities; the totals still count everything)
-        if (r.out_len && T.out < out_cap) {
+        // place the chunk (clipped to the caller's capacities; the totals still count everything), on the
+        // copy-out stream; the slow-path recode above, if any, ran on the slot's stream, so order after it
+        e2 = cudaEventRecord(s.ev, s.st);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s.out_st, s.ev, 0);
+        if (e2 == cudaSuccess && r.out_len && T.out < out_cap) {
             const uint64_t n = std::min<uint64_t>(r.out_len, out_cap - T.out);
-            e2 = cudaMemcpyAsync(h_out + T.out, s.d_out, n, cudaMemcpyDeviceToHost, s.st);
+            e2 = cudaMemcpyAsync(h_out + T.out, s.d_out, n, cudaMemcpyDeviceToHost, s.out_st);
         }
         if (e2 == cudaSuccess && op == ZS_OP_COMPRESS && h_index && r.n_lines && T.lines < index_cap) {
             const uint64_t n = std::min<uint64_t>(r.n_lines, index_cap - T.lines);
             if (T.out) {
                 const unsigned blocks = (unsigned)std::min<uint64_t>((n + 255) / 256, 1024);
-                rebase_kernel<<<blocks, 256, 0, s.st>>>(s.d_idx, n, T.out);
+                rebase_kernel<<<blocks, 256, 0, s.out_st>>>(s.d_idx, n, T.out);
                 e2 = cudaGetLastError();
             }
             if (e2 == cudaSuccess)
-                e2 = cudaMemcpyAsync(h_index + T.lines, s.d_idx, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.st);
+                e2 = cudaMemcpyAsync(h_index + T.lines, s.d_idx, n * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                     s.out_st);
         }
+        if (e2 == cudaSuccess) e2 = cudaEventRecord(s.out_ev, s.out_st);
+        s.out_pending = e2 == cudaSuccess;
         T.out += r.out_len;
         T.lines += r.n_lines;
         return e2;
@@ -286,8 +304,11 @@ zs_status run_pipeline(const zs_dict *dc, zs_op op, const uint8_t *h_in, size_t 
         order.erase(order.begin());
         e = retire(p->slots[si]);
     }
-    for (PipeSlot &s : p->slots)
+    for (PipeSlot &s : p->slots) {
         if (s.st) cudaStreamSynchronize(s.st);
+        if (s.out_st) cudaStreamSynchronize(s.out_st);
+        s.out_pending = false;
+    }
     if (e != cudaSuccess && T.st == ZS_OK) return zs::cuda_fail(e, what);
     res->out_len = T.out;
     res->n_lines = T.lines;
