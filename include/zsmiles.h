@@ -230,7 +230,8 @@ enum { ZS_MAX_SHARDS = 1 << 20 };
 int zs_kernel_variants(zs_op op);                     /* number of compiled variants (0 for a bad op) */
 const char *zs_kernel_variant_name(zs_op op, int v);  /* static string, or NULL */
 
-/* One-shot batched calls: one launch of the default variant over all shards, then a wait. res: host
+/* One-shot batched calls: one launch of the default variant over all shards, then a wait. flags: as for
+ * zs_compress (here and in zs_plan_create; not used by decompression). res: host
  * array of n_shards results (out_len, n_lines and err_offset of each shard). Errors: as for
  * zs_compress / zs_decompress; the first failing shard is named in zs_last_error(), and every shard's
  * res entry is filled. A dictionary whose transducer does not fit in shared memory (see
@@ -269,7 +270,8 @@ void zs_plan_destroy(zs_plan *p);
  * .zsd file text to `out` (host, out_cap bytes; *out_len receives its size, also on ZS_ERR_CAPACITY).
  *
  * Steps:
- *   - with ZS_PREPROCESS, the lines are ring-ID pre-processed first (Sec. IV-A);
+ *   - with ZS_PREPROCESS, the lines are ring-ID pre-processed first (Sec. IV-A), in opening order if
+ *     ZS_PREPROCESS_OUTER is set too;
  *   - every substring of lmin..lmax bytes that holds no ' ' and no '\n' is counted on the GPU, overlapping
  *     occurrences included;
  *   - then T patterns are picked greedily by occ * (len - overlap) (Eq. 1), where overlap is the largest
