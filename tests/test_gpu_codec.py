@@ -295,6 +295,26 @@ def test_line_index_large(zs):
         assert np.array_equal(idx.cpu().numpy().astype(np.uint64), oracle.line_index(raw[off:]))
 
 
+@pytest.mark.parametrize("off", [0, 3])
+def test_line_index_dense_and_sparse_tiles(zs, off):
+    """Runs of newlines put more entries in a tile than the index kernel stages in shared memory (those tiles
+    write directly), between tiles with no newline and ordinary lines; the index must still equal a plain
+    newline scan, aligned or not, with no final newline."""
+    rng = np.random.default_rng(11)
+    parts = []
+    for k in range(12):
+        if k % 3 == 0:
+            parts.append(np.full(40000 + k, 10, dtype=np.uint8))
+        elif k % 3 == 1:
+            parts.append(rng.integers(11, 256, size=70000 + 17 * k).astype(np.uint8))
+        else:
+            parts.append(np.frombuffer(bytes(synth.generate(synth.CFG0, k, 3000)), dtype=np.uint8))
+    raw = np.concatenate(parts + [np.array([65, 66], dtype=np.uint8)])
+    x = dev(np.concatenate([np.zeros(off, dtype=np.uint8), raw]))[off:]
+    idx = zs.line_index(x)
+    assert np.array_equal(idx.cpu().numpy().astype(np.uint64), oracle.line_index(raw))
+
+
 def test_random_access_parity(zs, dicts):
     d, od = dicts
     raw = synth.generate(synth.CFG3, 0, 30000)
