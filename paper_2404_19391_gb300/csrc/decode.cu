@@ -196,6 +196,7 @@ constexpr int kRNT = 256;
 struct LinesArgs {
     const uint8_t *comp;
     uint64_t comp_len;
+    uint32_t comp_aligned;  // comp is 4-byte aligned
     const uint64_t *index;
     uint64_t n_lines;
     const uint64_t *ids;
@@ -210,6 +211,26 @@ struct LinesArgs {
     uint64_t limit_ns;
     int64_t stall_tile;
 };
+
+// Calls f(c) for the bytes comp[a, b) in order, reading whole aligned 4-byte words where they lie inside
+// [a, b) (so inside the buffer) and single bytes at the ends.
+template <class F>
+__device__ __forceinline__ void for_each_byte(const uint8_t *comp, uint64_t a, uint64_t b, bool aligned, F f)
+{
+    uint64_t p = a;
+    if (aligned) {
+        for (; p < b && (p & 3u); ++p) f((uint32_t)comp[p]);
+#pragma unroll 4
+        for (; p + 4 <= b; p += 4) {
+            const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(comp + p));
+            f(w & 255u);
+            f((w >> 8) & 255u);
+            f((w >> 16) & 255u);
+            f(w >> 24);
+        }
+    }
+    for (; p < b; ++p) f((uint32_t)comp[p]);
+}
 
 __global__ void __launch_bounds__(kRNT) lines_kernel(LinesArgs A)
 {
@@ -241,18 +262,19 @@ __global__ void __launch_bounds__(kRNT) lines_kernel(LinesArgs A)
             }
             if (ok && b > a && A.comp[b - 1] == kNl) --b;
             bool lit = false;
-            for (uint64_t p = a; ok && p < b; ++p) {
-                const uint8_t c = A.comp[p];
-                if (lit) {
-                    olen += 1;
-                    lit = false;
-                } else if (c == kEsc) {
-                    lit = true;
-                } else {
-                    const uint32_t l = plen[c];
-                    if (l == 0) ok = false;  // unknown symbol or a '\n' inside the line
-                    olen += l;
-                }
+            if (ok) {
+                for_each_byte(A.comp, a, b, A.comp_aligned != 0, [&](uint32_t c) {
+                    if (lit) {
+                        olen += 1;
+                        lit = false;
+                    } else if (c == kEsc) {
+                        lit = true;
+                    } else {
+                        const uint32_t l = plen[c];
+                        if (l == 0) ok = false;  // unknown symbol or a '\n' inside the line
+                        olen += l;
+                    }
+                });
             }
             if (lit) ok = false;
             if (!ok) {
@@ -265,16 +287,18 @@ __global__ void __launch_bounds__(kRNT) lines_kernel(LinesArgs A)
         }
         uint64_t xa, xb, ta, tb;
         block_excl2_u64<kRNT>(olen, 0, scan, &xa, &xb, &ta, &tb);
-        if (tid == 0) {
+        if (tid < 32) {  // warp 0: publish, then look back 32 predecessors per round trip
             const bool stall = (int64_t)t == A.stall_tile;
-            if (!stall) publish(&A.tiles[t], t == 0 ? 2u : 1u, ta, 0);
+            if (tid == 0 && !stall) publish(&A.tiles[t], t == 0 ? 2u : 1u, ta, 0);
             uint64_t ea = 0, eb = 0;
-            if (t > 0) lookback(A.tiles, t, &ea, &eb, A.limit_ns, status);
-            if (t > 0 && !stall) publish(&A.tiles[t], 2u, ea + ta, 0);
-            s_E = ea;
-            if (t == A.ntiles - 1) {
-                A.res->out_len = ea + ta;
-                A.out_off[A.k] = ea + ta;
+            if (t > 0) lookback_warp(A.tiles, t, &ea, &eb, A.limit_ns, status);
+            if (tid == 0) {
+                if (t > 0 && !stall) publish(&A.tiles[t], 2u, ea + ta, 0);
+                s_E = ea;
+                if (t == A.ntiles - 1) {
+                    A.res->out_len = ea + ta;
+                    A.out_off[A.k] = ea + ta;
+                }
             }
         }
         __syncthreads();
@@ -283,23 +307,22 @@ __global__ void __launch_bounds__(kRNT) lines_kernel(LinesArgs A)
             A.out_off[r] = pos;
             if (ok) {
                 bool lit = false;
-                for (uint64_t p = a; p < b; ++p) {
-                    const uint8_t c = A.comp[p];
+                for_each_byte(A.comp, a, b, A.comp_aligned != 0, [&](uint32_t c) {
                     if (!lit && c == kEsc) {
                         lit = true;
-                        continue;
+                        return;
                     }
                     if (lit) {
-                        if (pos < A.out_cap) A.out[pos] = c;
+                        if (pos < A.out_cap) A.out[pos] = (uint8_t)c;
                         ++pos;
                         lit = false;
-                        continue;
+                        return;
                     }
                     const uint32_t l = plen[c];
                     const uint8_t *src = pat + 16u * c;
                     for (uint32_t q = 0; q < l; ++q, ++pos)
                         if (pos < A.out_cap) A.out[pos] = src[q];
-                }
+                });
                 if (pos < A.out_cap) A.out[pos] = kNl;
             }
         }
@@ -356,6 +379,7 @@ cudaError_t launch_lines(const zs_dict *d, const uint8_t *comp, uint64_t comp_le
     LinesArgs a{};
     a.comp = comp;
     a.comp_len = comp_len;
+    a.comp_aligned = (((uintptr_t)comp) & 3u) == 0;
     a.index = index;
     a.n_lines = n_lines;
     a.ids = ids;
