@@ -6,8 +6,8 @@
 //     it has odd length (every unescaped ' ' escapes the byte after it, and a run always starts
 //     unescaped), so each lane decodes its own slice (default 68 bytes) after counting the spaces in front of it
 //     (an odd number of words per slice keeps the lanes' shared-memory reads on distinct banks).
-//   - Small tiles and 20-32 warps per SM: the per-lane loops are chains of dependent shared-memory loads,
-//     so the kernel is bound by latency, and the warp count is what hides it.
+//   - Small tiles and 20-32 warps per SM (22 by default): the per-lane loops are chains of dependent
+//     shared-memory loads, so the kernel is bound by latency, and the warp count is what hides it.
 //   - Sizes phase: per lane, the decoded size of its slice (pattern lengths from a shared table), then a
 //     warp scan; the tile's aggregate is published for the decoupled look-back.
 //   - Software pipeline: the warp computes the sizes of tile k+1 before it resolves tile k's output
@@ -25,10 +25,11 @@ namespace {
 
 // Geometry of one compiled variant: warps per CTA and compressed bytes per lane slice (an odd number of
 // 4-byte words, so lane l's word w sits in a bank of its own).
-template <int W, int LANE>
+template <int W, int LANE, int OUTQ>
 struct DwGeom {
     static constexpr int kWarps = W;
     static constexpr int kLane = LANE;
+    static constexpr int kOutQ = OUTQ;  // staged output bytes per tile, in quarters of the tile's input bytes
 };
 
 constexpr unsigned kFullD = 0xffffffffu;
@@ -54,7 +55,7 @@ struct DW {
     static constexpr int kDNTW = 32 * kDW;
     static constexpr int kDLane = Geo::kLane;
     static constexpr int kDTile = 32 * kDLane;                  // compressed bytes per warp tile
-    static constexpr int kDOut = (kDTile * 5 / 2 + 255) & ~255;  // staged output bytes per tile
+    static constexpr int kDOut = (kDTile * Geo::kOutQ / 4 + 255) & ~255;  // staged output bytes per tile
     static_assert(kDLane % 8 == 4, "lane slices must be an odd number of 4-byte words and 16-byte tiles");
 
     struct alignas(16) DSlot {
@@ -450,10 +451,13 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) decompress_warp_kernel(co
     DW<Geo, NARROW>::run(&P);
 }
 
-// Compiled geometries; variant 0 is the default.
-using DwV0 = DwGeom<20, 68>;
-using DwV1 = DwGeom<32, 36>;
-using DwV2 = DwGeom<28, 44>;
+// Compiled geometries; variant 0 is the default: 22 warps, the output of a tile staged in 2.25 x its input
+// bytes (a tile that expands more stores directly). Variant 1 is the same tile with 20 warps and 2.5 x for
+// dictionaries that expand more; variants 2 and 3 hold smaller tiles with more warps.
+using DwV0 = DwGeom<22, 68, 9>;
+using DwV1 = DwGeom<20, 68, 10>;
+using DwV2 = DwGeom<28, 52, 9>;
+using DwV3 = DwGeom<32, 36, 10>;
 
 template <class Geo, bool NARROW>
 cudaError_t dw_launch_as(const DwArgs &a, uint64_t total_tiles, cudaStream_t s)
@@ -505,9 +509,10 @@ constexpr DwEntry dw_entry(const char *name)
 }
 
 const DwEntry kDwv[] = {
-    dw_entry<DwV0>("decompress w20 t2176"),
-    dw_entry<DwV1>("decompress w32 t1152"),
-    dw_entry<DwV2>("decompress w28 t1408"),
+    dw_entry<DwV0>("decompress w22 t2176"),
+    dw_entry<DwV1>("decompress w20 t2176"),
+    dw_entry<DwV2>("decompress w28 t1664"),
+    dw_entry<DwV3>("decompress w32 t1152"),
 };
 constexpr int kNumDw = (int)(sizeof(kDwv) / sizeof(kDwv[0]));
 
