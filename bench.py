@@ -566,6 +566,7 @@ def run_gpu(args):
             "config": {"workload": workload_desc(lines, nbytes), "lines_per_rank": lines,
                        "bytes_per_rank": nbytes, "dictionary": "frozen default (Algorithm 1, seed-1 100k-line "
                                                                "training set, L_max 8, T 146)",
+                       "dictionary_sha256": hashlib.sha256(open(zs.DEFAULT_DICTIONARY, "rb").read()).hexdigest(),
                        "step": f"zs_compress + zs_decompress + zs_decompress_lines({RA_IDS:,} random ids)",
                        "l2": "inputs (and outputs) larger than the 129 MB L2; no flush",
                        "parallelism": f"{world} independent replica(s)"},
