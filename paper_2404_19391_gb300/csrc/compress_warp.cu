@@ -474,7 +474,9 @@ struct CW {
         }
         const uint32_t my_steps = result == 0x7FFFFFFF ? ntok : 0u;
         const uint32_t steps = __reduce_max_sync(am, my_steps);
-        uint32_t lc0 = 0u, lc1 = 0u, lc2 = 0xFFFF0000u;  // labels 0-3, 4-7, 8-9 (bytes 10, 11 never free)
+        // lc: latest close position + 1 of each new label, label x in byte x / 3 of register x % 3 (positions
+        // are at most 112); the bytes of labels 10 and 11 hold 127, never free
+        uint32_t lc0 = 0u, lc1 = 0x7F000000u, lc2 = 0x7F000000u;
         uint64_t dmap = 0;
         uint32_t dopen = 0;
         bool need_slow = false;
@@ -499,18 +501,21 @@ struct CW {
                 dopen ^= act ? (1u << label) : 0u;
                 continue;
             }
-            const uint32_t t = ((eo & 0x7Fu) + 1u) * 0x01010101u;  // lc <= open position + 1: free
-            const uint32_t fr = pack4(__vcmpleu4(lc0, t)) | (pack4(__vcmpleu4(lc1, t)) << 4) |
-                                (pack4(__vcmpleu4(lc2, t)) << 8);
+            // label x is free when lc[x] <= open position + 1 = p. Per byte, (0x80 + p) - lc[x] stays within the
+            // byte (both are below 128) and has its top bit set exactly then; one find-first-set over the three
+            // registers' top bits (bit 8 * byte + register) gives the smallest free label
+            const uint32_t t = (((eo & 0x7Fu) + 1u) * 0x01010101u) | 0x80808080u;
+            const uint32_t y = (((t - lc0) & 0x80808080u) >> 7) | (((t - lc1) & 0x80808080u) >> 6) |
+                               (((t - lc2) & 0x80808080u) >> 5);
             const bool closing = act && open;
-            const int nl = __ffs(fr) - 1;
-            need_slow = need_slow || (closing && fr == 0u);  // would need a two-digit label
-            const bool upd = closing && fr != 0u;
-            const uint32_t val = (rel + 1u) << (8 * (nl & 3));
-            const uint32_t clr = ~(0xFFu << (8 * (nl & 3)));
-            lc0 = (upd && (nl >> 2) == 0) ? ((lc0 & clr) | val) : lc0;
-            lc1 = (upd && (nl >> 2) == 1) ? ((lc1 & clr) | val) : lc1;
-            lc2 = (upd && (nl >> 2) == 2) ? ((lc2 & clr) | val) : lc2;
+            const uint32_t fb = (uint32_t)__ffs(y) - 1u;
+            const uint32_t by = fb >> 3, rg = fb & 7u;
+            const int nl = (int)(3u * by + rg);
+            need_slow = need_slow || (closing && y == 0u);  // would need a two-digit label
+            const bool upd = closing && y != 0u;
+            lc0 = (upd && rg == 0) ? put_byte(lc0, rel + 1u, by) : lc0;
+            lc1 = (upd && rg == 1) ? put_byte(lc1, rel + 1u, by) : lc1;
+            lc2 = (upd && rg == 2) ? put_byte(lc2, rel + 1u, by) : lc2;
             if (upd) tok[ko * 32] = (uint16_t)(eo | ((uint32_t)nl << 12));
             if (act) tok[it * 32] = (uint16_t)(upd ? (rel | ((uint32_t)nl << 12)) : rel);
             const bool opening = act && !open;
@@ -522,6 +527,14 @@ struct CW {
         if (dopen != 0) return (int)n;  // an unclosed ring: left as it is
         *modified = true;
         return write_labels(st, a, n, tok, ntok, false);
+    }
+
+    // Byte lane b of x (b = 0..3) replaced by the low 8 bits of v.
+    static __device__ __forceinline__ uint32_t put_byte(uint32_t x, uint32_t v, uint32_t b)
+    {
+        uint32_t r;
+        asm("bfi.b32 %0, %1, %2, %3, 8;" : "=r"(r) : "r"(v), "r"(x), "r"(8u * b));
+        return r;
     }
 
     // Packs the 0x00 / 0xFF byte lanes of x into 4 bits (byte i -> bit i).
