@@ -1,29 +1,31 @@
 // zs_compress, transducer path: ring-ID pre-processing (Sec. IV-A) and the minimum-length parse
-// (Sec. IV-D1) with one warp per 4 KiB tile.
+// (Sec. IV-D1) with one warp per tile (default: 20 warps per SM, 1408-byte tiles, about 30 lines each).
 //
 //   - Each warp of a persistent CTA claims tiles on its own (atomic counter in launch order) and stages
-//     each tile, the byte before it and a 1 KiB halo with one bulk (TMA) copy. No CTA-wide barrier is on
-//     the per-tile path.
+//     each tile, the byte before it and a halo (512 bytes by default) with one bulk (TMA) copy. No
+//     CTA-wide barrier is on the per-tile path.
 //   - Software pipeline: a warp encodes tile k+1 (publishing its aggregate) before it resolves tile k's
 //     output offset by look-back and emits it, so by the time it looks back, its predecessors have long
 //     published; two staging slots per warp hold the two tiles.
-//   - After staging, the warp replaces every staged byte by its class code (coalesced 16-byte chunks, a
-//     lane-replicated class table so lookups never conflict on a bank) and flags, per chunk, the bytes
-//     pre-processing must look at (digits, '%', brackets, space, tab). Newlines keep their own class.
-//   - Segmentation ranks line starts (newline class) with 16-byte shared loads and warp prefix sums.
-//     Lines are sorted by length (per-warp counting sort) and dealt to lanes, one line per lane.
-//   - Pre-processing visits only the flagged bytes of its line: it records where ring labels sit (at
-//     most 32 per line), assigns labels per token (pairing through a per-lane table of open labels) and
-//     writes them back (the class of digit d is d), %nn labels shrinking in place.
+//   - Segmentation counts and ranks line starts on the raw bytes (16-byte shared loads, warp prefix sums);
+//     then only the bytes the tile's lines cover are replaced by class codes (coalesced 16-byte chunks, a
+//     lane-replicated class table so lookups never conflict on a bank), with per-chunk flags for the bytes
+//     pre-processing must look at (digits; '%', brackets, space, tab). Lines are sorted by length (per-warp
+//     counting sort) and dealt to lanes longest first, in snake order when a batch needs several rounds.
+//   - Pre-processing: a line of at most 112 bytes without '%' and with at most kTok ring labels takes the
+//     bit-mask path (lanes in lockstep over the ring tokens, per-label state in register byte lanes); any
+//     other line walks its flagged bytes once and relabels in place. Either way the new labels are written
+//     into the class codes (the class of digit d is d), %nn labels shrinking in place.
 //   - Parse: the backward shortest-path scan is the minimal transducer built by zs_load_dictionary: per
 //     byte one transition lookup on the class code gives the next state, the increment of the path cost
 //     and the symbol chosen at that byte. Codes are read and symbols written a 4-byte word at a time;
 //     only the state lookups form a dependent chain.
 //   - Emission walks the chosen symbols front to back into a per-warp staging buffer aligned to the
 //     output's 16-byte grid, written out with coalesced 16-byte stores.
-//   - Lines longer than 2047 bytes or the halo, lines needing a 3-byte label or holding more than 32 ring
-//     labels, and lines that had labels rewritten and need an escape take the exact slow path in global
-//     scratch (one lane). Tiles with more than 192 lines are processed in batches, look-back first.
+//   - Lines longer than 2047 bytes or past the halo, lines needing a two-digit label or holding more open
+//     %nn labels than the lane's column has slots, and lines whose relabelled text needs an escape of a
+//     byte that is not a digit take the exact slow path in global scratch (one lane). A tile with more lines
+//     than a batch holds is processed batch by batch, look-back first.
 #include <algorithm>
 
 #include "compress_shared.cuh"
@@ -413,10 +415,12 @@ struct CW {
     //     the ring tokens.
     //   - The tokens are then visited in order by every lane at once, as many steps as the lane with the
     //     most tokens, each step predicated rather than branched. lc (latest close position + 1 of each
-    //     label, positions < 128) lives in the byte lanes of three registers, so finding the smallest
-    //     label free since the ring opened is three SIMD byte compares.
-    // Returns as preprocess_classes, or -2 when the line holds a '%' (the caller then runs
-    // preprocess_classes). Every lane of the calling group must call it.
+    //     label, positions <= 112) lives in the byte lanes of three registers, so finding the smallest
+    //     label free since the ring opened is three 32-bit subtractions and one find-first-set.
+    //   - A token's new label goes to the lane's column of `tok` (position | label << 12); the labels are
+    //     written into the class codes once the line is known to be valid.
+    // Returns as preprocess_classes, or -2 when the line holds a '%' or more than kTokMax ring labels (the
+    // caller then runs preprocess_classes). Every lane of the calling group must call it.
     static constexpr uint32_t kBitMax = 112;
 
     static __device__ __forceinline__ int preprocess_bits(uint8_t *st, const uint32_t *imask, uint32_t nchunks,
