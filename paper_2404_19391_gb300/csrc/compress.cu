@@ -774,12 +774,12 @@ cudaError_t launch_compress(const zs_dict *d, const uint8_t *in, uint64_t n, uns
 
 uint64_t compress_tiles(uint64_t n) { return (n + kTB - 1) / kTB; }
 
-// The transducer kernel's geometry for a dictionary: variant 0 (20 warps per SM) when its transducer
-// image leaves room for them, else variant 1 (the same tile, 19 warps); -1 when neither fits, and the
-// generic kernel (automaton + window scan per byte) runs.
+// The transducer kernel's geometry for a dictionary, the fastest first that leaves its transducer image
+// room in shared memory: variant 0 (20 warps per SM), 1 (the same tile, 19 warps), 3 (12 warps), 2 (8
+// warps); -1 when none fits, and the generic kernel (automaton + window scan per byte) runs.
 int compress_default_variant(const zs_dict *d)
 {
-    for (int v = 0; v <= 1; ++v)
+    for (int v : {0, 1, 3, 2})
         if (compress_warp_fits(v, d)) return v;
     return -1;
 }
