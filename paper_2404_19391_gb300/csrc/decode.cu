@@ -189,9 +189,12 @@ __global__ void __launch_bounds__(kINT) line_index_kernel(IdxArgs A)
 
 // ------------------------------------------------------------------------------------------------
 // Random access: one request per thread; decoded sizes, block scan + look-back over request tiles for
-// the output offsets, then each thread decodes its line.
+// the output offsets, then each thread decodes its line into a shared-memory stage at its offset within
+// the tile, and the block writes the stage out as one contiguous run (coalesced); a tile whose lines
+// decode to more than the stage holds writes them directly.
 // ------------------------------------------------------------------------------------------------
 constexpr int kRNT = 256;
+constexpr uint32_t kRStage = 16384;  // staged decoded bytes per tile of requests
 
 struct LinesArgs {
     const uint8_t *comp;
@@ -235,6 +238,7 @@ __device__ __forceinline__ void for_each_byte(const uint8_t *comp, uint64_t a, u
 __global__ void __launch_bounds__(kRNT) lines_kernel(LinesArgs A)
 {
     __shared__ __align__(16) uint8_t dec[kDecBytes];
+    __shared__ __align__(16) uint8_t s_out[kRStage];
     __shared__ uint64_t scan[2 * (kRNT / 32 + 1)];
     __shared__ uint64_t s_tile, s_E;
     const int tid = threadIdx.x;
@@ -302,10 +306,18 @@ __global__ void __launch_bounds__(kRNT) lines_kernel(LinesArgs A)
             }
         }
         __syncthreads();
+        const uint64_t E = s_E;
+        const bool staged = ta <= kRStage;  // the same for the whole block
         if (r < A.k) {
-            uint64_t pos = s_E + xa;
-            A.out_off[r] = pos;
+            A.out_off[r] = E + xa;
             if (ok) {
+                // staged: bytes go to s_out at the line's offset within the tile; else straight to the output
+                uint64_t pos = staged ? xa : E + xa;
+                auto put = [&](uint8_t v) {
+                    if (staged) s_out[pos] = v;
+                    else if (pos < A.out_cap) A.out[pos] = v;
+                    ++pos;
+                };
                 bool lit = false;
                 for_each_byte(A.comp, a, b, A.comp_aligned != 0, [&](uint32_t c) {
                     if (!lit && c == kEsc) {
@@ -313,17 +325,22 @@ __global__ void __launch_bounds__(kRNT) lines_kernel(LinesArgs A)
                         return;
                     }
                     if (lit) {
-                        if (pos < A.out_cap) A.out[pos] = (uint8_t)c;
-                        ++pos;
+                        put((uint8_t)c);
                         lit = false;
                         return;
                     }
                     const uint32_t l = plen[c];
                     const uint8_t *src = pat + 16u * c;
-                    for (uint32_t q = 0; q < l; ++q, ++pos)
-                        if (pos < A.out_cap) A.out[pos] = src[q];
+                    for (uint32_t q = 0; q < l; ++q) put(src[q]);
                 });
-                if (pos < A.out_cap) A.out[pos] = kNl;
+                put(kNl);
+            }
+        }
+        if (staged) {
+            __syncthreads();
+            for (uint32_t j = (uint32_t)tid; j < (uint32_t)ta; j += kRNT) {
+                const uint64_t g = E + j;
+                if (g < A.out_cap) A.out[g] = s_out[j];
             }
         }
         __syncthreads();
