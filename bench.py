@@ -38,6 +38,7 @@ import synth  # noqa: E402
 
 METRIC = "compress/decompress input GB/s (frac. of HBM peak); random-access p99 latency"
 RA_IDS = 100_000
+REF_BUDGET_S = 120.0  # CPU seconds the reference arm's warm-up and timed steps aim to take in all
 HBM_FALLBACK_GBS = 6800.0
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (context only; fractions are taken of the measured peak)
 
@@ -201,7 +202,13 @@ def run_reference(args):
         return
     threads = os.cpu_count() or 1
     shape = synth.CFG1
-    sample = args.ref_sample_lines
+    # each step is a bounded sample of the workload, sized from a timed probe so that the warm-up and timed
+    # steps together take about REF_BUDGET_S of CPU work whatever --steps and --warmup are
+    probe = synth.generate(shape, 0, 100_000)
+    t_probe = sum(oracle_round_trip(probe, threads))
+    lines_per_s = 100_000 / max(t_probe, 1e-6)
+    fit = int(lines_per_s * REF_BUDGET_S / max(1, args.steps + args.warmup))
+    sample = max(10_000, min(args.ref_sample_lines, fit))
     raw = synth.generate(shape, 0, sample)
     for _ in range(args.warmup):
         oracle_round_trip(raw, threads)
