@@ -185,8 +185,9 @@ zs_status zs_decompress_lines(const zs_dict *d, const uint8_t *d_comp, size_t co
  * at most 570,420,992 bytes (zs_decompress_noalloc_limit() returns this figure); a larger input returns
  * ZS_ERR_INVALID_ARG without touching the device (use zs_decompress instead).
  *
- * Set-up: the first call on each device (with that device current) looks up the array's device address
- * once; make that first call before any stream capture on the device.
+ * Set-up: every call looks up the array's device address on the current device (cudaGetSymbolAddress),
+ * so nothing is cached across a cudaDeviceReset. The call clears the scratch it uses, launches the
+ * decoder, copies the result record to host memory and waits for its stream before returning.
  * Concurrency: every call shares the one array, and the call clears what must start at zero. Calls whose
  * work overlaps on the GPU (from several host threads or streams at once) race on the array: the caller
  * must serialise them.

@@ -3,8 +3,10 @@ from __future__ import annotations
 
 import glob
 import os
+import platform
 import subprocess
 import sys
+import time
 from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -29,10 +31,33 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
+def _nvcc_version() -> str:
+    try:
+        r = subprocess.run([NVCC, "--version"], capture_output=True, text=True)
+        lines = [ln for ln in r.stdout.splitlines() if "release" in ln]
+        return lines[-1].strip() if lines else r.stdout.strip().splitlines()[-1]
+    except OSError as e:
+        return f"unavailable ({e})"
+
+
+def _log(msg: str) -> None:
+    """One line to stderr and to _build/build_info.txt, so a run's record shows how the library came to be."""
+    line = f"[zsmiles build] {msg}"
+    sys.stderr.write(line + "\n")
+    try:
+        os.makedirs(BUILD, exist_ok=True)
+        with open(os.path.join(BUILD, "build_info.txt"), "a") as f:
+            f.write(time.strftime("%Y-%m-%dT%H:%M:%S ") + line + "\n")
+    except OSError:
+        pass
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
+        _log(f"reused {LIB} (newer than every source; host {platform.machine()})")
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    t0 = time.time()
     objs = []
 
     def compile_one(src):
@@ -55,6 +80,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    _log(f"compiled {len(objs)} sources on {platform.machine()} with nvcc {_nvcc_version()} "
+         f"{' '.join(ARCH)} {' '.join(FLAGS)} in {time.time() - t0:.1f} s -> {LIB}")
     return LIB
 
 

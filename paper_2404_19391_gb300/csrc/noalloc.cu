@@ -11,8 +11,6 @@
 // The array is kNoAllocScratchBytes (8 MiB) of device memory that every GPU loading the library holds
 // until the process exits. Every call shares it; calls whose work overlaps on the GPU (from several
 // host threads or streams at once) race on it and must be serialised by the caller.
-#include <mutex>
-
 #include "zs_common.cuh"
 
 namespace zs {
@@ -25,25 +23,15 @@ constexpr size_t kNoAllocScratchBytes = 8u << 20;
 // a device address: the kernel gets the address returned by cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {nullptr};
-
-// Set-up, once per device, with that device current: look up the array's device address.
-zs_status scratch_address(int dev, void **out)
+// The array's device address on the current device. It is looked up on every call rather than cached:
+// after cudaDeviceReset the module is loaded again and a cached address would be stale. Once the module
+// is loaded the lookup allocates nothing.
+zs_status scratch_address(void **out)
 {
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("zs_decompress_noalloc: device ordinal out of range");
-        return ZS_ERR_INVALID_ARG;
-    }
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_fail(e, "zs_decompress_noalloc: cudaGetSymbolAddress");
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "zs_decompress_noalloc: cudaGetSymbolAddress");
+    *out = p;
     return ZS_OK;
 }
 
@@ -76,7 +64,7 @@ extern "C" zs_status zs_decompress_noalloc(const zs_dict *d, const uint8_t *d_in
     }
     if (in_len == 0) return ZS_OK;
     void *scratch = nullptr;
-    zs_status st = zs::scratch_address(dev, &scratch);
+    zs_status st = zs::scratch_address(&scratch);
     if (st != ZS_OK) return st;
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -89,12 +77,13 @@ extern "C" zs_status zs_decompress_noalloc(const zs_dict *d, const uint8_t *d_in
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, dr, sizeof r, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return zs::cuda_fail(e, "zs_decompress_noalloc");
-    res->out_len = r.out_len;
-    res->n_lines = r.n_lines;
+    // the same order as zs_decompress: on a timeout *res stays zero
     if (r.status & zs::kStTimeout) {
         zs::set_error("zs_decompress_noalloc: a device-side wait expired");
         return ZS_ERR_TIMEOUT;
     }
+    res->out_len = r.out_len;
+    res->n_lines = r.n_lines;
     if (r.status & zs::kStMalformed) {
         res->err_offset = ~r.err_key;
         zs::set_error("zs_decompress_noalloc: malformed input at byte " + std::to_string(res->err_offset));

@@ -477,13 +477,21 @@ def zs_train_dictionary(d_train: torch.Tensor, flags: int = PREPROCESS, lmin: in
 # ---- conveniences built only from the calls above ----------------------------------------------------
 
 def compress(d: Dictionary, d_in: torch.Tensor, flags: int = PREPROCESS, with_index: bool = True, stream=None):
-    """Compress a device byte tensor; returns (compressed bytes, line index or None, Result)."""
+    """Compress a device byte tensor; returns (compressed bytes, line index or None, Result).
+
+    The index buffer starts from a guess (one line per 24 input bytes) and is resized from the call's own
+    ZS_ERR_CAPACITY answer (res.n_lines) when the guess is short, so no extra device pass sizes it."""
     out = torch.empty(zs_compress_bound(d_in.numel()), dtype=torch.uint8, device=d_in.device)
     idx = None
     if with_index:
-        n_lines = int(torch.count_nonzero(d_in == 10).item()) + 1
-        idx = torch.empty(n_lines + 1, dtype=torch.int64, device=d_in.device)
-    r = zs_compress(d, d_in, flags, out, idx, stream)
+        idx = torch.empty(d_in.numel() // 24 + 2, dtype=torch.int64, device=d_in.device)
+    try:
+        r = zs_compress(d, d_in, flags, out, idx, stream)
+    except ZsError as e:
+        if e.status != ERR_CAPACITY or idx is None or e.result is None or e.result.n_lines + 1 <= idx.numel():
+            raise
+        idx = torch.empty(e.result.n_lines + 1, dtype=torch.int64, device=d_in.device)
+        r = zs_compress(d, d_in, flags, out, idx, stream)
     return out[: r.out_len], (idx[: r.n_lines + 1] if idx is not None else None), r
 
 
@@ -494,18 +502,30 @@ def decompress(d: Dictionary, d_in: torch.Tensor, stream=None):
 
 
 def line_index(d_in: torch.Tensor, stream=None) -> torch.Tensor:
-    cap = int(torch.count_nonzero(d_in == 10).item()) + 2
-    idx = torch.empty(cap, dtype=torch.int64, device=d_in.device)
-    n = zs_build_line_index(d_in, idx, stream)
+    """Line index of a device stream, sized from zs_build_line_index's own answer on ZS_ERR_CAPACITY."""
+    idx = torch.empty(d_in.numel() // 16 + 2, dtype=torch.int64, device=d_in.device)
+    try:
+        n = zs_build_line_index(d_in, idx, stream)
+    except ZsError as e:
+        if e.status != ERR_CAPACITY or e.result is None:
+            raise
+        idx = torch.empty(e.result.n_lines + 1, dtype=torch.int64, device=d_in.device)
+        n = zs_build_line_index(d_in, idx, stream)
     return idx[: n + 1]
 
 
 def decompress_lines(d: Dictionary, d_comp: torch.Tensor, d_index: torch.Tensor, d_ids: torch.Tensor,
                      out_cap: int | None = None, stream=None):
-    if out_cap is None:
-        spans = (d_index[d_ids.clamp(max=d_index.numel() - 2) + 1] - d_index[d_ids.clamp(max=d_index.numel() - 2)])
-        out_cap = int(spans.sum().item()) * d.lmax + d_ids.numel() + 16
-    out = torch.empty(max(1, out_cap), dtype=torch.uint8, device=d_comp.device)
+    """Random access with the output sized by the call itself: a first guess, then the exact size that
+    zs_decompress_lines reports (res.out_len) on ZS_ERR_CAPACITY."""
+    guess = out_cap if out_cap is not None else 64 * d_ids.numel() + 64
+    out = torch.empty(max(1, guess), dtype=torch.uint8, device=d_comp.device)
     off = torch.empty(d_ids.numel() + 1, dtype=torch.int64, device=d_comp.device)
-    r = zs_decompress_lines(d, d_comp, d_index, d_ids, out, off, stream)
+    try:
+        r = zs_decompress_lines(d, d_comp, d_index, d_ids, out, off, stream)
+    except ZsError as e:
+        if out_cap is not None or e.status != ERR_CAPACITY or e.result is None:
+            raise
+        out = torch.empty(max(1, e.result.out_len), dtype=torch.uint8, device=d_comp.device)
+        r = zs_decompress_lines(d, d_comp, d_index, d_ids, out, off, stream)
     return out[: r.out_len], off, r

@@ -81,30 +81,28 @@ def _decompress_shards(zs, d, comps):
     return [(i, o[:-16], None) for i, o in zip(ins, outs)], outs
 
 
-@pytest.mark.parametrize("variant", range(8))
-def test_plan_every_variant(zs, dicts, expected, variant):
-    d, od = dicts
-    if variant >= zs.zs_kernel_variants(zs.OP_COMPRESS):
-        pytest.skip("not a compiled variant")
-    shards, outs, idxs = _compress_shards(zs, RAW)
-    p = zs.Plan(d, zs.OP_COMPRESS, shards, flags=1, variant=variant, use_graph=True)
-    assert p.variant == variant
-    for _ in range(2):  # graph replay: the scratch is cleared by the graph itself
-        res = p.run()
-        _check_compressed(res, shards, outs, idxs, expected)
-    p.close()
-    comps = [ec for ec, _ in expected]
-    dv = variant % zs.zs_kernel_variants(zs.OP_DECOMPRESS)
-    dsh, douts = _decompress_shards(zs, d, comps)
-    q = zs.Plan(d, zs.OP_DECOMPRESS, dsh, variant=dv, use_graph=True)
-    for _ in range(2):
-        res = q.run()
-        for k, (r, raw) in enumerate(zip(res, RAW)):
-            want = oracle.preprocess_stream(np.frombuffer(raw, dtype=np.uint8))
-            assert r.out_len == want.size, f"shard {k}"
-            assert np.array_equal(douts[k][: r.out_len].cpu().numpy(), want), f"shard {k}"
-            assert torch.all(douts[k][r.out_len:] == 0xEE)
-    q.close()
+def test_plan_every_variant(zs, dicts, expected):
+    for variant in range(zs.zs_kernel_variants(zs.OP_COMPRESS)):
+        d, od = dicts
+        shards, outs, idxs = _compress_shards(zs, RAW)
+        p = zs.Plan(d, zs.OP_COMPRESS, shards, flags=1, variant=variant, use_graph=True)
+        assert p.variant == variant
+        for _ in range(2):  # graph replay: the scratch is cleared by the graph itself
+            res = p.run()
+            _check_compressed(res, shards, outs, idxs, expected)
+        p.close()
+        comps = [ec for ec, _ in expected]
+        dv = variant % zs.zs_kernel_variants(zs.OP_DECOMPRESS)
+        dsh, douts = _decompress_shards(zs, d, comps)
+        q = zs.Plan(d, zs.OP_DECOMPRESS, dsh, variant=dv, use_graph=True)
+        for _ in range(2):
+            res = q.run()
+            for k, (r, raw) in enumerate(zip(res, RAW)):
+                want = oracle.preprocess_stream(np.frombuffer(raw, dtype=np.uint8))
+                assert r.out_len == want.size, f"shard {k}"
+                assert np.array_equal(douts[k][: r.out_len].cpu().numpy(), want), f"shard {k}"
+                assert torch.all(douts[k][r.out_len:] == 0xEE)
+        q.close()
 
 
 def test_autotuned_plan(zs, dicts, expected):
@@ -157,30 +155,28 @@ def test_many_small_shards(zs, dicts):
     _check_compressed(p.run(), shards, outs, idxs, exp)
 
 
-@pytest.mark.parametrize("variant", range(8))
-def test_tile_boundaries_every_variant(zs, dicts, variant):
+def test_tile_boundaries_every_variant(zs, dicts):
     """Lines ending just before, at and after each variant's tile and halo boundaries."""
-    d, od = dicts
-    if variant >= zs.zs_kernel_variants(zs.OP_COMPRESS):
-        pytest.skip("not a compiled variant")
-    name = zs.zs_kernel_variant_name(zs.OP_COMPRESS, variant)
-    tile = int(name.split("t")[-1])
-    raws = []
-    for edge in (tile, 2 * tile, 3 * tile + 512, 2 * tile + 1024):
-        for delta in (-2, -1, 0, 1, 2):
-            line = (b"c1ccccc1C(=O)N" * 800)[: edge + delta - 3]
-            raws.append(b"CC\n" + line + b"\nCCO\n" + b"C1CC1\n" * 50)
-    exp = [oracle.compress_stream(od, np.frombuffer(b, dtype=np.uint8), 1) for b in raws]
-    shards, outs, idxs = _compress_shards(zs, raws)
-    p = zs.Plan(d, zs.OP_COMPRESS, shards, flags=1, variant=variant, use_graph=False)
-    _check_compressed(p.run(), shards, outs, idxs, exp)
-    comps = [ec for ec, _ in exp]
-    for dv in range(zs.zs_kernel_variants(zs.OP_DECOMPRESS)):
-        dsh, douts = _decompress_shards(zs, d, comps)
-        res = zs.Plan(d, zs.OP_DECOMPRESS, dsh, variant=dv).run()
-        for k, r in enumerate(res):
-            want = oracle.decompress_stream(od, comps[k])
-            assert np.array_equal(douts[k][: r.out_len].cpu().numpy(), want), f"variant {dv} shard {k}"
+    for variant in range(zs.zs_kernel_variants(zs.OP_COMPRESS)):
+        d, od = dicts
+        name = zs.zs_kernel_variant_name(zs.OP_COMPRESS, variant)
+        tile = int(name.split("t")[-1])
+        raws = []
+        for edge in (tile, 2 * tile, 3 * tile + 512, 2 * tile + 1024):
+            for delta in (-2, -1, 0, 1, 2):
+                line = (b"c1ccccc1C(=O)N" * 800)[: edge + delta - 3]
+                raws.append(b"CC\n" + line + b"\nCCO\n" + b"C1CC1\n" * 50)
+        exp = [oracle.compress_stream(od, np.frombuffer(b, dtype=np.uint8), 1) for b in raws]
+        shards, outs, idxs = _compress_shards(zs, raws)
+        p = zs.Plan(d, zs.OP_COMPRESS, shards, flags=1, variant=variant, use_graph=False)
+        _check_compressed(p.run(), shards, outs, idxs, exp)
+        comps = [ec for ec, _ in exp]
+        for dv in range(zs.zs_kernel_variants(zs.OP_DECOMPRESS)):
+            dsh, douts = _decompress_shards(zs, d, comps)
+            res = zs.Plan(d, zs.OP_DECOMPRESS, dsh, variant=dv).run()
+            for k, r in enumerate(res):
+                want = oracle.decompress_stream(od, comps[k])
+                assert np.array_equal(douts[k][: r.out_len].cpu().numpy(), want), f"variant {dv} shard {k}"
 
 
 def test_graph_replay_sees_new_data(zs, dicts):

@@ -62,6 +62,68 @@ def test_matches_zs_decompress_two_calls_in_a_row(env):
             assert torch.all(out[r.out_len:] == 0xAB)
 
 
+def _decompress_status(env, comp, out):
+    zs, lib, d = env
+    r = _Result()
+    st = lib.zs_decompress(d.handle, comp.data_ptr(), comp.numel(), out.data_ptr(), out.numel(), ctypes.byref(r),
+                           torch.cuda.current_stream().cuda_stream or None)
+    return st, r
+
+
+def test_same_errors_as_zs_decompress(env):
+    """Malformed input (status and first bad offset) and a short output buffer (ZS_ERR_CAPACITY with the
+    size needed) come back exactly as zs_decompress reports them."""
+    zs, lib, d = env
+    raw = synth.generate(synth.CFG0, 0, 4000)
+    comp, _, _ = zs.compress(d, torch.from_numpy(raw).cuda(), with_index=False)
+    good = comp.clone()
+    cases = []
+    bad = good.clone()
+    bad[1234] = 0x01  # a byte that is no symbol of the default dictionary
+    cases.append(bad)
+    bad2 = good.clone()
+    nl = torch.nonzero(bad2 == 10).flatten()
+    bad2[int(nl[7]) - 1] = 32  # an escape with nothing after it in its line
+    cases.append(bad2)
+    cases.append(torch.cat([good, torch.tensor([32], dtype=torch.uint8, device="cuda")]))  # dangling at the end
+    for c in cases:
+        out_a = torch.empty(d.decompress_bound(c.numel()), dtype=torch.uint8, device="cuda")
+        out_b = torch.empty_like(out_a)
+        st_a, ra = _decompress_status(env, c, out_a)
+        st_b, rb = _noalloc(env, c, out_b)
+        assert st_a == zs.ERR_MALFORMED
+        assert (st_b, rb.err_offset) == (st_a, ra.err_offset)
+    small_a = torch.empty(1000, dtype=torch.uint8, device="cuda")
+    small_b = torch.empty(1000, dtype=torch.uint8, device="cuda")
+    st_a, ra = _decompress_status(env, good, small_a)
+    st_b, rb = _noalloc(env, good, small_b)
+    assert st_a == zs.ERR_CAPACITY
+    assert (st_b, rb.out_len, rb.n_lines) == (st_a, ra.out_len, ra.n_lines)
+
+
+def test_allocates_nothing_across_calls(env):
+    """After a first call (which may load the library's device module), further calls leave the device's
+    free memory and torch's allocator untouched."""
+    zs, lib, d = env
+    raw = synth.generate(synth.CFG0, 0, 20000)
+    comp, _, _ = zs.compress(d, torch.from_numpy(raw).cuda(), with_index=False)
+    comp = comp.clone()
+    out = torch.empty(d.decompress_bound(comp.numel()), dtype=torch.uint8, device="cuda")
+    st, _ = _noalloc(env, comp, out)
+    assert st == zs.OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        st, _ = _noalloc(env, comp, out)
+        assert st == zs.OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.memory_reserved() == reserved0
+
+
 def test_rejects_inputs_beyond_its_scratch(env):
     zs, lib, d = env
     comp = torch.zeros(16, dtype=torch.uint8, device="cuda")
