@@ -181,8 +181,8 @@ zs_status zs_decompress_lines(const zs_dict *d, const uint8_t *d_comp, size_t co
  * device memory compiled into the library, which every GPU that loads the library holds until the
  * process exits, and its result is copied straight into *res.
  *
- * Limit: the scratch holds 262,142 tile records of 2,176 bytes of compressed input each, so in_len may be
- * at most 570,420,992 bytes (zs_decompress_noalloc_limit() returns this figure); a larger input returns
+ * Limit: the scratch holds 262,142 tile records of 2,048 bytes of compressed input each, so in_len may be
+ * at most 536,866,816 bytes (zs_decompress_noalloc_limit() returns this figure); a larger input returns
  * ZS_ERR_INVALID_ARG without touching the device (use zs_decompress instead).
  *
  * Set-up: every call looks up the array's device address on the current device (cudaGetSymbolAddress),

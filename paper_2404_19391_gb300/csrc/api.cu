@@ -77,7 +77,7 @@ zs_status ScratchPool::get(void *stream, size_t tiles, size_t slow, Scratch **ou
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    Scratch &s = map_[stream];
+    Scratch &s = map_[std::make_pair(stream, std::this_thread::get_id())];
     if (s.device >= 0 && s.device != dev) {
         set_error("stream scratch belongs to another device");
         return ZS_ERR_INVALID_ARG;

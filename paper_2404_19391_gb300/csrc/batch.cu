@@ -61,7 +61,7 @@ int variant_count(zs_op op) { return op == ZS_OP_COMPRESS ? zs::compress_warp_va
 bool variant_usable(const zs_plan *p, int v)
 {
     if (!variant_info(p->op, v)) return false;
-    return p->op == ZS_OP_DECOMPRESS || zs::compress_warp_fits(v, p->d);
+    return p->op == ZS_OP_DECOMPRESS ? zs::decompress_fits(v, p->d) : zs::compress_warp_fits(v, p->d);
 }
 
 void drop_graph(zs_plan *p)
@@ -160,10 +160,12 @@ zs_status grow_slow(zs_plan *p, size_t need)
     return ZS_OK;
 }
 
-// One run on `s`, retried with a larger long-line scratch when it overflowed. Fills p->host.
-zs_status run_once(zs_plan *p, cudaStream_t s)
+// One run on `s`, retried with a larger long-line scratch when it overflowed, and (when `fall_back`) with
+// the general compression kernel when the span kernel met a line outside its fast path: the plan keeps that
+// geometry from then on. Fills p->host.
+zs_status run_once(zs_plan *p, cudaStream_t s, bool fall_back = true)
 {
-    for (int attempt = 0; attempt < 3; ++attempt) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
         cudaError_t e;
         if (p->use_graph) {
             if (!p->exec) {
@@ -182,6 +184,17 @@ zs_status run_once(zs_plan *p, cudaStream_t s)
             p->last_ms = 0.f;
         }
         const DevResult &g = p->host[0];
+        if ((g.status & zs::kStFallback) && !(g.status & zs::kStTimeout) && fall_back &&
+            p->op == ZS_OP_COMPRESS && zs::compress_variant_is_span(p->variant)) {
+            const int gv = zs::compress_general_variant(p->d);
+            if (gv < 0) {
+                zs::set_error("zs_plan_run: no general kernel variant fits this dictionary");
+                return ZS_ERR_BAD_DICT;
+            }
+            zs_status st = layout(p, gv);
+            if (st != ZS_OK) return st;
+            continue;
+        }
         if (g.status & zs::kStSlowOverflow) {
             const size_t need = (size_t)g.slow_used + ((size_t)g.slow_used >> 2) + (1u << 20);
             zs_status st = grow_slow(p, need);
@@ -236,10 +249,11 @@ zs_status tune(zs_plan *p, int reps)
     for (int v = 0; v < nv; ++v) {
         if (!variant_usable(p, v)) continue;
         zs_status st = layout(p, v);
-        if (st == ZS_OK) st = run_once(p, p->cap);  // warm-up (and long-line scratch sizing)
+        if (st == ZS_OK) st = run_once(p, p->cap, false);  // warm-up (and long-line scratch sizing)
+        if (st == ZS_OK && (p->host[0].status & zs::kStFallback)) continue;  // this batch needs the general kernel
         std::vector<float> t;
         for (int k = 0; k < reps && st == ZS_OK; ++k) {
-            st = run_once(p, p->cap);
+            st = run_once(p, p->cap, false);
             t.push_back(p->last_ms);
         }
         if (st != ZS_OK) {
@@ -433,7 +447,7 @@ extern "C" zs_status zs_compress_batch(const zs_dict *d, const zs_shard *shards,
 extern "C" zs_status zs_decompress_batch(const zs_dict *d, const zs_shard *shards, size_t n_shards, zs_result *res,
                                          void *stream)
 {
-    zs_plan_options o{zs::kDefaultVariant, 0, 0};
+    zs_plan_options o{d ? zs::decompress_default_variant(d) : zs::kDefaultVariant, 0, 0};
     zs_plan *p = nullptr;
     zs_status st = zs_plan_create(d, ZS_OP_DECOMPRESS, 0, shards, n_shards, &o, &p);
     if (st != ZS_OK) return st;

@@ -774,14 +774,22 @@ cudaError_t launch_compress(const zs_dict *d, const uint8_t *in, uint64_t n, uns
 
 uint64_t compress_tiles(uint64_t n) { return (n + kTB - 1) / kTB; }
 
-// The transducer kernel's geometry for a dictionary, the fastest first that leaves its transducer image
-// room in shared memory: variant 0 (20 warps per SM), 1 (the same tile, 19 warps), 3 (12 warps), 2 (8
-// warps); -1 when none fits, and the generic kernel (automaton + window scan per byte) runs.
+// The tiled geometry zs_compress uses for a dictionary: the span kernel's default geometry when the
+// dictionary has a byte-indexed transducer, else the general transducer kernel's fastest geometry that
+// leaves its image room in shared memory (20 warps, the same tile with 19, 12 warps, 8 warps); -1 when none
+// fits, and the generic kernel (automaton + window scan per byte) runs.
+int compress_general_variant(const zs_dict *d)
+{
+    const int ns = span_variants();
+    for (int v : {0, 1, 3, 2})
+        if (compress_warp_fits(ns + v, d)) return ns + v;
+    return -1;
+}
+
 int compress_default_variant(const zs_dict *d)
 {
-    for (int v : {0, 1, 3, 2})
-        if (compress_warp_fits(v, d)) return v;
-    return -1;
+    if (compress_warp_fits(0, d)) return 0;
+    return compress_general_variant(d);
 }
 
 bool use_transducer(const zs_dict *d) { return compress_default_variant(d) >= 0; }
@@ -792,17 +800,20 @@ extern "C" int zs_dictionary_uses_transducer(const zs_dict *d) { return d && zs:
 
 namespace zs {
 
+// Look-back records for a call: enough for the default geometry and for the general one it may fall back to.
 uint64_t compress_scratch_tiles(const zs_dict *d, uint64_t n)
 {
-    const int v = compress_default_variant(d);
-    return v >= 0 ? tiles_for(n, compress_warp_variant(v)->tile_bytes) : compress_tiles(n);
+    uint64_t m = compress_tiles(n);
+    for (int v : {compress_default_variant(d), compress_general_variant(d)})
+        if (v >= 0) m = std::max<uint64_t>(m, tiles_for(n, compress_warp_variant(v)->tile_bytes));
+    return m;
 }
 
 cudaError_t launch_compress_any(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,
                                 uint64_t out_cap, uint64_t *index, uint64_t index_cap, DevResult *res,
-                                TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s)
+                                TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s, bool general)
 {
-    const int v = compress_default_variant(d);
+    const int v = general ? compress_general_variant(d) : compress_default_variant(d);
     if (v < 0) return launch_compress(d, in, n, flags, out, out_cap, index, index_cap, res, tiles, slow, slow_cap, s);
     TiledLaunch L{};
     L.one = single_shard(in, n, out, out_cap, index, index_cap, tiles, res,
@@ -879,7 +890,8 @@ extern "C" zs_status zs_compress(const zs_dict *d, const uint8_t *d_in, size_t i
     }
     const uint64_t ntiles = zs::compress_scratch_tiles(d, in_len);
     size_t slow_need = 16u << 20;
-    for (int attempt = 0; attempt < 3; ++attempt) {
+    bool general = false;  // the span kernel met a line outside its fast path: run the general kernel
+    for (int attempt = 0; attempt < 4; ++attempt) {
         zs::Scratch *sc = nullptr;
         zs_status st = const_cast<zs_dict *>(d)->pool.get(stream, ntiles, slow_need, &sc);
         if (st != ZS_OK) return st;
@@ -889,7 +901,7 @@ extern "C" zs_status zs_compress(const zs_dict *d, const uint8_t *d_in, size_t i
         if (e != cudaSuccess) return zs::cuda_fail(e, "zs_compress: memset");
         zs::mark_kernel_start(sc, s);
         e = zs::launch_compress_any(d, d_in, in_len, flags, d_out, out_cap, d_line_index,
-                                    d_line_index ? index_cap : 0, dr, tiles, sc->slow, sc->slow_cap, s);
+                                    d_line_index ? index_cap : 0, dr, tiles, sc->slow, sc->slow_cap, s, general);
         if (e != cudaSuccess) return zs::cuda_fail(e, "zs_compress: launch");
         zs::mark_kernel_end(sc, s);
         e = cudaMemcpyAsync(sc->host, dr, sizeof(zs::DevResult), cudaMemcpyDeviceToHost, s);
@@ -897,6 +909,10 @@ extern "C" zs_status zs_compress(const zs_dict *d, const uint8_t *d_in, size_t i
         if (e != cudaSuccess) return zs::cuda_fail(e, "zs_compress");
         const zs::DevResult r = *sc->host;
         zs::note_kernel_time(sc);
+        if ((r.status & zs::kStFallback) && !(r.status & zs::kStTimeout) && !general) {
+            general = true;
+            continue;
+        }
         if (r.status & zs::kStSlowOverflow) {
             slow_need = (size_t)r.slow_used + ((size_t)r.slow_used >> 2) + (1u << 20);
             continue;

@@ -1,0 +1,1068 @@
+// zs_compress, span path: ring-ID pre-processing (Sec. IV-A) and the minimum-length parse (Sec. IV-D1) with
+// one warp per tile and, within the tile, one contiguous span of whole lines per lane.
+//
+//   - Tiles and look-back as in the other tiled kernels: each warp of a persistent CTA claims tiles in
+//     launch order, stages a tile (plus the byte before it and a halo for the last line) with one bulk
+//     (TMA) copy, and resolves its output offset by a warp-wide decoupled look-back, one tile behind the
+//     one it encodes (software pipeline).
+//   - Token mask: the warp classifies the staged bytes 16 at a time with SIMD byte arithmetic (no table):
+//     one bit per byte marks the bytes pre-processing looks at (digits, '%', '[', ']', ' ', tab, '\n'),
+//     plus bytes >= 0x80 so that a tile holding any is known.
+//   - Spans: lane l owns the lines that start between two boundaries, each the line start closest to
+//     l / 32 of the tile, so every lane gets about 1/32 of the bytes whatever the line lengths.
+//   - Pre-processing: each lane walks only the token bits of its span; ring labels are rewritten in place
+//     when a ring closes (or opens, for the other reading), %nn labels shrink and the span is compacted.
+//   - Parse: the backward shortest-path scan is the minimal transducer of the dictionary, re-indexed by
+//     the raw byte: per byte one byte-permute builds (state << 8 | 2 * byte) and one 16-bit shared load
+//     gives the next state and the symbol chosen there. '\n' resets the state, so a whole span is one
+//     scan, and the chosen symbols overwrite the text in place.
+//   - Emission: a count walk over the chosen pieces gives each lane's output bytes, a warp scan places
+//     them, and a write walk stores them into a per-warp staging buffer (and the line starts into an
+//     index stage), which the finishing step copies out with aligned 16-byte stores.
+//   - Anything outside this fast path (a line that needs a label above 9, more open %nn labels than a lane
+//     follows, a line longer than tile + halo, an escape of an input byte in a compacted span) sets
+//     kStFallback, and the call is run again by the general kernel.
+#include <algorithm>
+
+#include "compress_shared.cuh"
+
+namespace zs {
+namespace {
+using namespace cx;
+
+template <int W, int TB, int HB, int OUTB, int MAXL>
+struct SpGeom {
+    static constexpr int kWarps = W;    // warps per CTA (one CTA per SM)
+    static constexpr int kTile = TB;    // owned input bytes per warp tile
+    static constexpr int kHalo = HB;    // bytes staged past the tile for its last line
+    static constexpr int kOut = OUTB;   // staged output bytes per tile (more: the tile writes directly)
+    static constexpr int kMaxL = MAXL;  // staged index entries per tile (more: the tile writes directly)
+};
+
+constexpr unsigned kAll = 0xffffffffu;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint8_t kDel = 0xFF;           // a deleted byte (digits of a rewritten %nn label); never staged text
+constexpr uint32_t kOpen2 = 4;           // open %nn labels (>= 10) a lane follows
+constexpr uint32_t kChEscDigit = 0x10;   // choice 0x10 + d: escape of the (new) digit d
+constexpr uint32_t kChEsc = 0x20;        // choice ' ': escape of the input byte at that position
+constexpr uint32_t kPosBits = 13, kPosMask = (1u << kPosBits) - 1u;  // emission walks: position | out bytes << 13
+// Aggregate published by a tile that met a line outside the fast path (and by every tile claimed after the
+// call was marked for the general kernel): every later tile's output and index offsets then lie past any
+// buffer's capacity, so nothing is written past what the general kernel's run will write.
+constexpr uint64_t kPoison = 1ull << 40;
+
+// Launch-wide arguments; the per-shard ones are in the ShardView of each claimed tile.
+struct SpArgs {
+    ShardView one;
+    const ShardView *shards;
+    uint32_t n_shards;
+    uint32_t flags;
+    uint64_t total_tiles;
+    const uint8_t *bimg;  // byte transducer image (ByteLayout)
+    uint32_t img_bytes;
+    uint32_t meta_off;    // offset of meta[256] in the image
+    uint32_t q0;          // start state
+    uint32_t rep_col;     // 2 * a byte below 0x80 that acts like every byte >= 0x80
+    DevResult *g;
+    uint64_t limit_ns;
+    int64_t stall_tile;
+};
+
+// Per-byte SIMD classification (bytes of a 32-bit word; the high bit of each result byte is the answer).
+// Bytes >= 0x80 are in no class. Range tests add to the low seven bits, which never carries out of a byte.
+struct Classes {
+    uint32_t nl, dig, ob, cb, sp;  // '\n'; '0'-'9'; '['; ']'; '%', ' ' or tab
+};
+
+__device__ __forceinline__ Classes classify(uint32_t x)
+{
+    const uint32_t y = x & 0x7F7F7F7Fu, h = 0x80808080u & ~x;
+    Classes c;
+    c.nl = ~((y ^ 0x0A0A0A0Au) + 0x7F7F7F7Fu) & h;
+    c.dig = (y + 0x50505050u) & ~(y + 0x46464646u) & h;  // >= 0x30 and < 0x3A
+    c.ob = ~((y ^ 0x5B5B5B5Bu) + 0x7F7F7F7Fu) & h;
+    c.cb = ~((y ^ 0x5D5D5D5Du) + 0x7F7F7F7Fu) & h;
+    c.sp = ~(((y ^ 0x25252525u) + 0x7F7F7F7Fu) & ((y ^ 0x20202020u) + 0x7F7F7F7Fu) &
+             ((y ^ 0x09090909u) + 0x7F7F7F7Fu)) & h;
+    return c;
+}
+
+// The top bits of the four bytes of a high-bit mask, moved to bits 28..31 (byte i -> bit 28 + i).
+__device__ __forceinline__ uint32_t top4(uint32_t hb) { return hb * 0x00204081u; }
+
+// Bit masks of the 16 bytes of a chunk (byte i -> bit i) for each class.
+__device__ __forceinline__ void class_bits16(uint4 v, uint32_t *nl, uint32_t *dig, uint32_t *ob, uint32_t *cb,
+                                             uint32_t *sp)
+{
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t n = 0, d = 0, o = 0, c2 = 0, e = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const Classes c = classify(w[k]);
+        n = (n >> 4) | (top4(c.nl) & 0xF0000000u);
+        d = (d >> 4) | (top4(c.dig) & 0xF0000000u);
+        o = (o >> 4) | (top4(c.ob) & 0xF0000000u);
+        c2 = (c2 >> 4) | (top4(c.cb) & 0xF0000000u);
+        e = (e >> 4) | (top4(c.sp) & 0xF0000000u);
+    }
+    *nl = n >> 16;
+    *dig = d >> 16;
+    *ob = o >> 16;
+    *cb = c2 >> 16;
+    *sp = e >> 16;
+}
+
+// Prefix XOR of the bits of x (bit i = XOR of bits 0..i).
+__device__ __forceinline__ uint32_t prefix_xor(uint32_t x)
+{
+    x ^= x << 1;
+    x ^= x << 2;
+    x ^= x << 4;
+    x ^= x << 8;
+    x ^= x << 16;
+    return x;
+}
+
+template <class Geo, bool OUTER>
+struct SP {
+    static constexpr int kW = Geo::kWarps;
+    static constexpr int kNT = 32 * kW;
+    static constexpr int kTB = Geo::kTile;
+    static constexpr int kHB = Geo::kHalo;
+    static constexpr int kSt = 16 + kTB + kHB;  // staged bytes: [0, 16) holds the byte before the tile at 15
+    static constexpr int kOutB = Geo::kOut;
+    static constexpr int kMaxL = Geo::kMaxL;
+    static constexpr int kMaskWords = kSt / 32 + 2;
+    static_assert(kTB % 512 == 0 && kHB % 16 == 0 && kOutB % 16 == 0 && kSt + 16 <= (int)kPosMask, "span geometry");
+
+    struct alignas(16) OutSlot {
+        uint8_t out[kOutB + 16];
+        uint32_t idx[kMaxL];  // tile-relative output offset of each line start (entry 0 = 0)
+        uint32_t total;       // output bytes of the tile
+        uint32_t lines;       // lines starting in the tile
+        uint32_t direct;      // 1: the tile's output did not fit the stage (written at finish time); 2: none
+        uint32_t _pad;
+        uint64_t t;
+        ShardView sv;
+    };
+
+    struct alignas(16) WarpMem {
+        uint8_t text[kSt + 16];
+        uint32_t nmask[kMaskWords];  // one bit per staged byte: '\n'
+        uint32_t dmask[kMaskWords];  // digits
+        uint32_t omask[kMaskWords];  // '[', and '%' ' ' tab
+        uint32_t cmask[kMaskWords];  // ']', and '%' ' ' tab (a byte in both masks always makes an exception)
+        uint16_t ring[(20 + 2 * kOpen2) * 32];  // per lane (entry k of lane l at [k * 32 + l]): open positions
+                                                 // of labels 0-9, latest closes of new labels 0-9, open %nn
+        OutSlot os[2];
+        uint64_t bar;
+        uint32_t high;  // the staged tile holds a byte >= 0x80
+        uint32_t _pad;
+    };
+
+    struct Ctx {
+        const SpArgs *P;
+        const ShardView *A;
+        WarpMem *M;
+        const uint8_t *tab;    // transducer table in shared memory
+        const uint32_t *meta;  // per choice: input bytes consumed | output bytes << 13
+        uint32_t lane;
+        uint32_t *status;
+    };
+
+    // ---- staging and token mask ---------------------------------------------------------------------
+    static __device__ __forceinline__ uint64_t tile_base(uint64_t t) { return t * (uint64_t)kTB; }
+
+    static __device__ __forceinline__ void stage_issue(const Ctx &C, uint64_t t)
+    {
+        const ShardView &A = *C.A;
+        WarpMem &M = *C.M;
+        const uint64_t base = tile_base(t);
+        const uint64_t stage_hi = min(A.n, base + (uint64_t)kTB + kHB);
+        const uint64_t lo = base >= 16 ? base - 16 : 0;
+        const uint32_t j0 = (uint32_t)(lo + 16 - base);
+        const uint32_t nbytes = (uint32_t)(stage_hi - lo);
+        const uint32_t nbulk = A.in_aligned ? (nbytes & ~15u) : 0u;
+        __syncwarp();
+        if (C.lane == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_tx(&M.bar, nbulk);
+            if (nbulk) bulk_g2s(M.text + j0, A.in + lo, nbulk, &M.bar);
+        }
+        for (uint32_t j = nbulk + C.lane; j < nbytes; j += 32) M.text[j0 + j] = A.in[lo + j];
+        if (t == 0 && C.lane == 0) M.text[15] = kNl;  // position 0 starts a line
+    }
+
+    // Class bits of the staged bytes [16 * c0, 16 * c1) (whole chunks); returns whether any byte >= 0x80.
+    static __device__ __forceinline__ bool mask_chunks(const Ctx &C, uint32_t c0, uint32_t c1)
+    {
+        WarpMem &M = *C.M;
+        uint32_t hi = 0;
+        uint16_t *n16 = reinterpret_cast<uint16_t *>(M.nmask);
+        uint16_t *d16 = reinterpret_cast<uint16_t *>(M.dmask);
+        uint16_t *o16 = reinterpret_cast<uint16_t *>(M.omask);
+        uint16_t *c16 = reinterpret_cast<uint16_t *>(M.cmask);
+        for (uint32_t c = c0 + C.lane; c < c1; c += 32) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(M.text + 16 * c);
+            hi |= (v.x | v.y | v.z | v.w);
+            uint32_t n, d, o, cl, e;
+            class_bits16(v, &n, &d, &o, &cl, &e);
+            n16[c] = (uint16_t)n;
+            d16[c] = (uint16_t)d;
+            o16[c] = (uint16_t)(o | e);
+            c16[c] = (uint16_t)(cl | e);
+        }
+        return __any_sync(kAll, (hi & 0x80808080u) != 0);
+    }
+
+    // ---- newline searches (every lane on its own) ---------------------------------------------------------
+    // First '\n' at a staged position in [p, lim), or kNone.
+    static __device__ __forceinline__ uint32_t next_nl(const WarpMem &M, uint32_t p, uint32_t lim)
+    {
+        while (p < lim) {
+            const uint32_t w = p >> 5;
+            const uint32_t bits = M.nmask[w] & (kAll << (p & 31));
+            if (bits) {
+                const uint32_t q = (w << 5) + (uint32_t)(__ffs(bits) - 1);
+                return q < lim ? q : kNone;
+            }
+            p = (w + 1) << 5;
+        }
+        return kNone;
+    }
+
+    // Last '\n' at a staged position in [lo, p), or kNone.
+    static __device__ __forceinline__ uint32_t prev_nl(const WarpMem &M, uint32_t p, uint32_t lo)
+    {
+        while (p > lo) {
+            const uint32_t w = (p - 1) >> 5;
+            const uint32_t bits = M.nmask[w] & (kAll >> (31u - ((p - 1) & 31u)));
+            if (bits) {
+                const uint32_t q = (w << 5) + 31u - (uint32_t)__clz(bits);
+                return q >= lo ? q : kNone;
+            }
+            p = w << 5;
+        }
+        return kNone;
+    }
+
+    // Bits of mask m at staged positions [lo, hi) (all of them, one word at a time): their count.
+    static __device__ __forceinline__ uint32_t count_bits(const uint32_t *m, uint32_t lo, uint32_t hi)
+    {
+        uint32_t n = 0;
+        for (uint32_t w = lo >> 5; (w << 5) < hi; ++w) {
+            uint32_t bits = m[w];
+            if ((w << 5) < lo) bits &= kAll << (lo & 31);
+            if (((w + 1) << 5) > hi) bits &= (1u << (hi & 31)) - 1u;
+            n += __popc(bits);
+        }
+        return n;
+    }
+
+    // ---- spans ------------------------------------------------------------------------------------------
+    struct Span {
+        uint32_t a, b;      // this lane's lines: staged positions [a, b)
+        uint32_t B0, B32;   // the tile's lines: [B0, B32)
+        bool long_last;     // the tile's last line runs past the staged bytes
+    };
+
+    // Tile segmentation and span boundaries. Line starts owned by the tile are staged positions
+    // [16, 16 + nown) preceded by '\n'. Lane l's first line is the line start closest to 16 + l * nown / 32.
+    static __device__ __forceinline__ Span spans(const Ctx &C, uint64_t t, uint32_t nown, uint32_t stage_end,
+                                                 bool stream_end_staged)
+    {
+        const WarpMem &M = *C.M;
+        const uint32_t lane = C.lane;
+        const uint32_t own_nl = 15u + nown;  // newlines at [15, own_nl) open owned lines
+        Span s;
+        uint32_t B0 = kNone, B32 = kNone;
+        bool long_last = false;
+        if (lane == 0) {
+            const uint32_t q = next_nl(M, 15, own_nl);
+            B0 = q == kNone ? kNone : q + 1;
+        }
+        B0 = __shfl_sync(kAll, B0, 0);
+        if (B0 == kNone) {  // no line starts in this tile
+            s.a = s.b = s.B0 = s.B32 = 16;
+            s.long_last = false;
+            return s;
+        }
+        if (lane == 31) {
+            const uint32_t q = next_nl(M, own_nl, stage_end);
+            if (q != kNone) {
+                B32 = q + 1;
+            } else {
+                B32 = stage_end;
+                long_last = !stream_end_staged;
+            }
+        }
+        B32 = __shfl_sync(kAll, B32, 31);
+        long_last = __shfl_sync(kAll, long_last, 31);
+        uint32_t Bl = B0;
+        if (lane > 0) {
+            const uint32_t target = 16u + (uint32_t)(((uint64_t)lane * nown) >> 5);
+            const uint32_t qm = prev_nl(M, target, B0 - 1u);
+            const uint32_t qp = next_nl(M, target - 1u, own_nl);
+            const uint32_t sm = qm == kNone ? kNone : qm + 1;
+            const uint32_t sp = qp == kNone ? B32 : qp + 1;
+            Bl = (sm != kNone && target - sm <= sp - target) ? sm : sp;
+            Bl = min(max(Bl, B0), B32);
+        }
+        uint32_t Bn = __shfl_down_sync(kAll, Bl, 1);
+        if (lane == 31) Bn = B32;
+        s.a = Bl;
+        s.b = Bn;
+        s.B0 = B0;
+        s.B32 = B32;
+        s.long_last = long_last;
+        return s;
+    }
+
+    // ---- pre-processing ---------------------------------------------------------------------------------
+    // Walks the token bits of the lane's span [a, b) line by line and relabels ring IDs in place (closing
+    // order by default: a ring takes, when it closes, the smallest label whose latest ring closed before this
+    // one opened; opening order with OUTER: a ring takes, when it opens, the smallest label no open ring
+    // holds). A line found invalid at its end (unclosed ring or bracket, bad %) is restored from the input.
+    // %nn labels become one digit; their two digits are marked and squeezed out at the line's end, moving
+    // the rest of the span down. Returns the span's end after compaction; *lines = lines in the span;
+    // *shifted = some line was compacted; *fallback = a line needs the general kernel.
+    static __device__ uint32_t relabel_general(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
+                                               uint32_t *lines_out, bool *shifted, bool *fallback)
+    {
+        WarpMem &M = *C.M;
+        uint8_t *text = M.text;
+        uint16_t *ring = M.ring + C.lane;  // entry k at ring[32 * k]
+        const bool pre = (C.P->flags & ZS_PREPROCESS) != 0;
+        uint32_t shift = 0, lines = 0;
+        bool fb = false;
+        // per-line state
+        uint32_t ls = a;  // line start (original positions)
+        uint32_t dopen = 0, lcv = 0, held = 0, nopen2 = 0, skip_to = 0;
+        bool in_br = false, field_done = false, bad = false, any_pct = false, wrote = false;
+        auto finish_line = [&](uint32_t le) {  // le: the line's end (its '\n' or the span end), original
+            const uint32_t cls = ls - shift, cle = le - shift;
+            if (wrote && (bad || in_br || dopen != 0 || nopen2 != 0)) {  // left as it is
+                for (uint32_t k = cls; k < cle; ++k) text[k] = raw[k + shift];
+            } else if (wrote && any_pct) {  // squeeze out the deleted digits, then move the rest down
+                uint32_t w = cls;
+                for (uint32_t r = cls; r < cle; ++r) {
+                    const uint8_t v = text[r];
+                    if (v != kDel) text[w++] = v;
+                }
+                const uint32_t d = cle - w;
+                const uint32_t bend = b - shift;
+                for (uint32_t r = cle; r < bend; ++r) text[r - d] = text[r];
+                shift += d;
+            }
+            ++lines;
+            ls = le + 1;
+            if (nopen2 != 0)
+                for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
+            dopen = lcv = held = nopen2 = 0;
+            skip_to = 0;
+            in_br = field_done = bad = any_pct = wrote = false;
+        };
+        for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
+        if (a < b) {
+            uint32_t w = a >> 5;
+            uint32_t bits = (M.nmask[w] | M.dmask[w] | M.omask[w] | M.cmask[w]) & (kAll << (a & 31));
+            for (;;) {
+                while (bits == 0) {
+                    ++w;
+                    if ((w << 5) >= b) break;
+                    bits = M.nmask[w] | M.dmask[w] | M.omask[w] | M.cmask[w];
+                }
+                if (bits == 0) break;
+                const uint32_t p = (w << 5) + (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1;
+                if (p >= b) break;
+                const uint32_t q = p - shift;  // current position
+                const uint32_t c = text[q];
+                if (c == kNl) {
+                    finish_line(p);
+                    continue;
+                }
+                if (!pre || field_done || bad || p < skip_to || fb) continue;
+                if (c == ' ' || c == '\t') {  // the SMILES field ends at the first space or tab
+                    field_done = true;
+                    continue;
+                }
+                if (in_br) {
+                    if (c == ']') in_br = false;
+                    continue;
+                }
+                if (c == '[') {
+                    in_br = true;
+                    continue;
+                }
+                uint32_t label;
+                bool pct = false;
+                if (c == '%') {  // %nn: two digits must follow within the line
+                    const uint32_t d1 = (uint32_t)text[q + 1] - '0', d2 = (uint32_t)text[q + 2] - '0';
+                    if (p + 2 >= b || d1 > 9 || d2 > 9) {
+                        bad = true;
+                        continue;
+                    }
+                    label = d1 * 10 + d2;
+                    pct = true;
+                    skip_to = p + 3;
+                } else if (c >= '0' && c <= '9') {
+                    label = c - '0';
+                } else {
+                    continue;  // a byte the token test passes but pre-processing ignores
+                }
+                // open_e: the ring's open token (position + 1, bit 15: written %nn) if this token closes it;
+                // oslot: the entry that keeps an opening token's position
+                uint32_t open_e = 0, oslot = label;
+                if (label < 10) {
+                    if ((dopen >> label) & 1u) open_e = ring[32 * label];
+                    dopen ^= 1u << label;
+                } else {
+                    int hit = -1, empty = -1;
+#pragma unroll
+                    for (int j = 0; j < (int)kOpen2; ++j) {
+                        const uint32_t v = ring[32 * (20 + 2 * j)];
+                        if (v == label + 1) hit = j;
+                        if (v == 0 && empty < 0) empty = j;
+                    }
+                    if (hit >= 0) {
+                        open_e = ring[32 * (21 + 2 * hit)];
+                        ring[32 * (20 + 2 * hit)] = 0;
+                        --nopen2;
+                    } else if (empty >= 0) {
+                        ring[32 * (20 + 2 * empty)] = (uint16_t)(label + 1);
+                        oslot = 21u + 2u * (uint32_t)empty;
+                        ++nopen2;
+                    } else {
+                        fb = true;  // more open %nn labels than the lane follows
+                        continue;
+                    }
+                }
+                const bool opening = open_e == 0;
+                uint32_t nl;
+                if (OUTER) {
+                    if (opening) {
+                        const uint32_t fr = ~held & 0x3FFu;
+                        if (fr == 0) {  // would need a two-digit label
+                            fb = true;
+                            continue;
+                        }
+                        nl = (uint32_t)__ffs(fr) - 1u;
+                        held |= 1u << nl;
+                        ring[32 * oslot] = (uint16_t)((q + 1) | (pct ? 0x8000u : 0u));
+                    } else {
+                        nl = (uint32_t)text[(open_e & 0x7FFFu) - 1u] - '0';
+                        held &= ~(1u << nl);
+                    }
+                } else {
+                    if (opening) {
+                        ring[32 * oslot] = (uint16_t)((q + 1) | (pct ? 0x8000u : 0u));
+                        continue;
+                    }
+                    const uint32_t o = (open_e & 0x7FFFu) - 1u;  // position of the open token
+                    nl = 10;
+                    for (uint32_t x = 0; x < 10; ++x) {
+                        if (!((lcv >> x) & 1u) || ring[32 * (10 + x)] <= o) {
+                            nl = x;
+                            break;
+                        }
+                    }
+                    if (nl == 10) {  // would need a two-digit label
+                        fb = true;
+                        continue;
+                    }
+                    text[o] = (uint8_t)('0' + nl);
+                    if (open_e & 0x8000u) {
+                        text[o + 1] = kDel;
+                        text[o + 2] = kDel;
+                        any_pct = true;
+                    }
+                    ring[32 * (10 + nl)] = (uint16_t)(q + 1);
+                    lcv |= 1u << nl;
+                }
+                text[q] = (uint8_t)('0' + nl);
+                if (pct) {
+                    text[q + 1] = kDel;
+                    text[q + 2] = kDel;
+                    any_pct = true;
+                }
+                wrote = true;
+            }
+        }
+        if (ls < b) finish_line(b);  // the stream's last line, without '\n'
+        *lines_out = lines;
+        *shifted = shift != 0;
+        *fallback = fb;
+        return b - shift;
+    }
+
+    // Whether the span [a, b) can take the fast relabelling: no '%', space or tab, and every bracket atom
+    // opens and closes within its line, without nesting and without a digit inside. Bit arithmetic over the
+    // class masks, one 32-bit word at a time: the prefix XOR of the bracket bits is 1 from a '[' up to its ']'.
+    // '%', space and tab are in both bracket masks, so each one is a '[' inside an atom or a ']' outside one.
+    static __device__ __forceinline__ bool exception_free(const WarpMem &M, uint32_t a, uint32_t b)
+    {
+        uint32_t in = 0;  // inside a bracket atom at the start of the word
+        uint32_t bad = 0;
+        for (uint32_t w = a >> 5; (w << 5) < b; ++w) {
+            uint32_t keep = kAll;
+            if ((w << 5) < a) keep &= kAll << (a & 31);
+            if (((w + 1) << 5) > b) keep &= (1u << (b & 31)) - 1u;
+            const uint32_t o = M.omask[w] & keep, c = M.cmask[w] & keep;
+            const uint32_t t = o | c;
+            const uint32_t px = prefix_xor(t) ^ (0u - in);   // 1 from each '[' up to, not including, its ']'
+            const uint32_t before = px ^ t;                  // the state just before each bit
+            bad |= (o & before)                              // '[' inside a bracket atom
+                   | (c & ~before)                           // ']' outside one ('%', space, tab: always one
+                                                             //  of the two, being in both masks)
+                   | (M.dmask[w] & keep & px & ~t)           // a digit inside one
+                   | (M.nmask[w] & keep & px);               // a line ending inside one
+            in = (px >> 31) & 1u;
+        }
+        return bad == 0 && in == 0;
+    }
+
+    // Digits of the line [ls, le) back to their input bytes (a line found invalid at its end).
+    static __device__ __forceinline__ void restore_digits(const WarpMem &M, uint8_t *text, const uint8_t *raw,
+                                                          uint32_t ls, uint32_t le)
+    {
+        for (uint32_t w = ls >> 5; (w << 5) < le; ++w) {
+            uint32_t bits = M.dmask[w];
+            while (bits) {
+                const uint32_t q = (w << 5) + (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1;
+                if (q >= ls && q < le) text[q] = raw[q];
+            }
+        }
+    }
+
+    // Relabelling of an exception-free span: only the digit bits are visited, all of them ring labels. Labels
+    // of a line are decided as in relabel_general; the latest close of each new label is kept in 16-bit
+    // halves of five registers (label x in register x % 5, high half for x >= 5), so finding the smallest
+    // label free since the ring opened is five subtractions and one find-first-set, without branches.
+    static __device__ __forceinline__ void relabel_fast(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
+                                                        bool *fallback)
+    {
+        WarpMem &M = *C.M;
+        uint8_t *text = M.text;
+        uint16_t *openp = M.ring + C.lane;  // open position + 1 of digit label d at openp[32 * d]
+        uint32_t ls = a, dopen = 0, held = 0;
+        uint32_t L0 = 0, L1 = 0, L2 = 0, L3 = 0, L4 = 0;
+        bool fb = false;
+        uint32_t w = a >> 5;
+        uint32_t bits = (M.dmask[w] | M.nmask[w]) & (kAll << (a & 31));
+        for (;;) {
+            while (bits == 0) {
+                ++w;
+                if ((w << 5) >= b) break;
+                bits = M.dmask[w] | M.nmask[w];
+            }
+            if (bits == 0) break;
+            const uint32_t p = (w << 5) + (uint32_t)(__ffs(bits) - 1);
+            bits &= bits - 1;
+            if (p >= b) break;
+            const uint32_t c = text[p];
+            if (c == kNl) {  // end of a line: one with an unclosed ring stays as it is
+                if (dopen) restore_digits(M, text, raw, ls, p);
+                dopen = held = 0;
+                L0 = L1 = L2 = L3 = L4 = 0;
+                ls = p + 1u;
+                continue;
+            }
+            const uint32_t d = c - '0';
+            const uint32_t bit = 1u << d;
+            if (dopen & bit) {  // closes the ring opened at o
+                const uint32_t o = (uint32_t)openp[32 * d] - 1u;
+                uint32_t nl;
+                if (OUTER) {
+                    nl = (uint32_t)text[o] - '0';
+                    held &= ~(1u << nl);
+                } else {
+                    const uint32_t orep = (o * 0x00010001u) | 0x80008000u;
+                    const uint32_t g = (((orep - L0) & 0x80008000u) >> 15) | (((orep - L1) & 0x80008000u) >> 14) |
+                                       (((orep - L2) & 0x80008000u) >> 13) | (((orep - L3) & 0x80008000u) >> 12) |
+                                       (((orep - L4) & 0x80008000u) >> 11);
+                    const uint32_t f = (g & 0x1Fu) | ((g >> 11) & 0x3E0u);  // labels free since o, in order
+                    if (f == 0) {  // would need a two-digit label
+                        fb = true;
+                        break;
+                    }
+                    nl = (uint32_t)__ffs(f) - 1u;
+                    text[o] = (uint8_t)('0' + nl);
+                    const uint32_t r = nl < 5 ? nl : nl - 5u;
+                    const uint32_t hm = nl < 5 ? 0x0000FFFFu : 0xFFFF0000u;
+                    const uint32_t v = ((p + 1u) * 0x00010001u) & hm;
+                    L0 = r == 0 ? (L0 & ~hm) | v : L0;
+                    L1 = r == 1 ? (L1 & ~hm) | v : L1;
+                    L2 = r == 2 ? (L2 & ~hm) | v : L2;
+                    L3 = r == 3 ? (L3 & ~hm) | v : L3;
+                    L4 = r == 4 ? (L4 & ~hm) | v : L4;
+                }
+                text[p] = (uint8_t)('0' + nl);
+            } else {  // opens a ring
+                openp[32 * d] = (uint16_t)(p + 1u);
+                if (OUTER) {
+                    const uint32_t fr = ~held & 0x3FFu;
+                    if (fr == 0) {
+                        fb = true;
+                        break;
+                    }
+                    const uint32_t nl = (uint32_t)__ffs(fr) - 1u;
+                    held |= 1u << nl;
+                    text[p] = (uint8_t)('0' + nl);
+                }
+            }
+            dopen ^= bit;
+        }
+        if (!fb && dopen) restore_digits(M, text, raw, ls, b);
+        *fallback = fb;
+    }
+
+    // Pre-processing of the lane's span (Sec. IV-A): the fast relabelling when the span allows it, else the
+    // general walk. Returns the span's end after compaction; *lines = lines in the span.
+    static __device__ __forceinline__ uint32_t preprocess(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
+                                                          uint32_t *lines, bool *shifted, bool *fallback)
+    {
+        const WarpMem &M = *C.M;
+        *lines = a < b ? count_bits(M.nmask, a, b) + (M.text[b - 1] != kNl ? 1u : 0u) : 0u;
+        *shifted = false;
+        *fallback = false;
+        if (!(C.P->flags & ZS_PREPROCESS) || a >= b) return b;
+        if (exception_free(M, a, b)) {
+            relabel_fast(C, a, b, raw, fallback);
+            return b;
+        }
+        uint32_t l2 = 0;
+        return relabel_general(C, a, b, raw, &l2, shifted, fallback);
+    }
+
+    // ---- parse ------------------------------------------------------------------------------------------
+    // Table lookup of the byte transducer: entry (next state | choice << 8) at byte offset
+    // (state << 8) | (2 * byte), built by one byte-permute from the previous entry and the doubled bytes.
+    static __device__ __forceinline__ uint32_t look(const uint8_t *tab, uint32_t prev, uint32_t x2, uint32_t sel)
+    {
+        return *reinterpret_cast<const uint16_t *>(tab + __byte_perm(prev, x2, sel));
+    }
+
+    // Backward scan of the lane's span [a, e): each byte is replaced by the choice made there. HIGH: the tile
+    // holds bytes >= 0x80, which read the column of rep_col (they match no pattern).
+    template <bool HIGH>
+    static __device__ __forceinline__ void parse(const Ctx &C, uint32_t a, uint32_t e)
+    {
+        uint8_t *text = C.M->text;
+        const uint8_t *tab = C.tab;
+        const uint32_t rep = C.P->rep_col;
+        uint32_t st = C.P->q0;
+        int32_t p = (int32_t)e - 1;
+        const int32_t lo = (int32_t)a;
+        auto col = [&](uint32_t b) -> uint32_t { return (HIGH && b >= 0x80u) ? rep : (b << 1); };
+        while (p >= lo && ((p + 1) & 3) != 0) {
+            st = look(tab, st, col(text[p]), 0x3204);
+            text[p] = (uint8_t)(st >> 8);
+            --p;
+        }
+        while (p - 3 >= lo) {
+            const int32_t wp = p - 3;
+            const uint32_t x = *reinterpret_cast<const uint32_t *>(text + wp);
+            uint32_t x2;
+            if (HIGH) {
+                x2 = (x & 0x7F7F7F7Fu) << 1;
+                const uint32_t hb = x & 0x80808080u;
+                if (hb) {
+                    const uint32_t hm = (hb >> 7) * 0xFFu;
+                    x2 = (x2 & ~hm) | ((rep * 0x01010101u) & hm);
+                }
+            } else {
+                x2 = (x + x) & 0xFEFEFEFEu;  // every byte is below 0x80; the mask keeps each address even
+            }
+            const uint32_t e3 = look(tab, st, x2, 0x3207);
+            const uint32_t e2 = look(tab, e3, x2, 0x3206);
+            const uint32_t e1 = look(tab, e2, x2, 0x3205);
+            const uint32_t e0 = look(tab, e1, x2, 0x3204);
+            *reinterpret_cast<uint32_t *>(text + wp) =
+                __byte_perm(__byte_perm(e0, e1, 0x0051), __byte_perm(e2, e3, 0x0051), 0x5410);
+            st = e0;
+            p -= 4;
+        }
+        while (p >= lo) {
+            st = look(tab, st, col(text[p]), 0x3204);
+            text[p] = (uint8_t)(st >> 8);
+            --p;
+        }
+    }
+
+    // ---- emission ---------------------------------------------------------------------------------------
+    // Output bytes of the pieces chosen along the span [a, e) (position in bits 0-12 of the walk, output
+    // bytes above). *gen_esc: an escape of an input byte was chosen.
+    static __device__ __forceinline__ uint32_t count_out(const Ctx &C, uint32_t a, uint32_t e, bool check, bool *gen_esc)
+    {
+        const uint8_t *text = C.M->text;
+        const uint32_t *meta = C.meta;
+        uint32_t acc = a;
+        bool ge = false;
+        if (!check) {
+            while ((acc & kPosMask) < e) acc += meta[text[acc & kPosMask]];
+        } else {
+            while ((acc & kPosMask) < e) {
+                const uint32_t c = text[acc & kPosMask];
+                ge |= c == kChEsc;
+                acc += meta[c];
+            }
+        }
+        *gen_esc = ge;
+        return acc >> kPosBits;
+    }
+
+    struct SmemOut {
+        uint8_t *o;
+        uint32_t *idx;
+        uint32_t nidx;
+        __device__ __forceinline__ void put(uint32_t w, uint8_t v) { o[w] = v; }
+        __device__ __forceinline__ void line(uint32_t r, uint32_t w) { if (r < nidx) idx[r] = w; }
+    };
+    struct GlobalOut {  // direct writes: output offset ea, lines from eb
+        uint8_t *out;
+        uint64_t cap, ea;
+        uint64_t *index;
+        uint64_t index_cap, eb;
+        uint32_t nlines;
+        __device__ __forceinline__ void put(uint32_t w, uint8_t v)
+        {
+            if (ea + w < cap) out[ea + w] = v;
+        }
+        __device__ __forceinline__ void line(uint32_t r, uint32_t w)
+        {
+            if (index && r < nlines && eb + r < index_cap) index[eb + r] = ea + w;
+        }
+    };
+
+    // Write walk of the span [a, e) from output offset w, the lane's first line being line `rank` of the
+    // tile: symbols as they are, escapes as ' ' + byte, and each new line's start offset.
+    template <class Sink>
+    static __device__ __forceinline__ void write_out(const Ctx &C, uint32_t a, uint32_t e, uint32_t w, uint32_t rank,
+                                                     const uint8_t *raw, Sink &S)
+    {
+        const uint8_t *text = C.M->text;
+        const uint32_t *meta = C.meta;
+        uint32_t acc = a;
+        while ((acc & kPosMask) < e) {
+            const uint32_t i = acc & kPosMask;
+            const uint32_t c = text[i];
+            acc += meta[c];
+            if (c > kChEsc) {
+                S.put(w++, (uint8_t)c);
+            } else if (c == kNl) {
+                S.put(w++, kNl);
+                S.line(++rank, w);
+            } else {
+                S.put(w++, kEsc);
+                S.put(w++, c == kChEsc ? raw[i] : (uint8_t)('0' + c - kChEscDigit));
+            }
+        }
+    }
+
+    // ---- one tile -----------------------------------------------------------------------------------------
+    struct Enc {
+        uint32_t a, e;      // the lane's span after pre-processing
+        uint32_t off;       // its output offset within the tile
+        uint32_t rank;      // its first line within the tile
+        uint32_t total, lines;
+    };
+
+    // Everything up to the tile's aggregate: masks, spans, pre-processing, parse, sizes (and, when the tile
+    // fits its stage, the staged output). Publishes the aggregate.
+    static __device__ Enc encode(const Ctx &C, OutSlot &O, uint64_t t)
+    {
+        const ShardView &A = *C.A;
+        WarpMem &M = *C.M;
+        const uint32_t lane = C.lane;
+        const uint64_t base = tile_base(t);
+        const uint32_t nown = (uint32_t)(min(A.n, base + kTB) - base);
+        const uint64_t stage_hi = min(A.n, base + (uint64_t)kTB + kHB);
+        const uint32_t stage_end = (uint32_t)(stage_hi - base) + 16u;
+        const uint8_t *raw = A.in + base - 16;  // global address of staged position 0
+        bool high = mask_chunks(C, 0, (16u + nown + 15u) >> 4);
+        // end of the tile's last line: the first '\n' at or after the last owned byte
+        uint32_t lastnl = kNone;
+        for (uint32_t off = (15u + nown) & ~15u; off < stage_end; off += 512) {
+            const uint32_t p0 = off + 16u * lane;
+            uint32_t bits = 0;
+            if (p0 < stage_end) {
+                bits = nl_bits16(*reinterpret_cast<const uint4 *>(M.text + p0));
+                if (p0 < 15u + nown) bits &= kAll << (15u + nown - p0);
+                if (p0 + 16u > stage_end) bits &= (1u << (stage_end - p0)) - 1u;
+            }
+            lastnl = __reduce_min_sync(kAll, bits ? p0 + (uint32_t)(__ffs(bits) - 1) : kNone);
+            if (lastnl != kNone) break;
+        }
+        const uint32_t tail_end = lastnl != kNone ? lastnl + 1u : stage_end;
+        high |= mask_chunks(C, (16u + nown) >> 4, (tail_end + 15u) >> 4);
+        bool fb = lastnl == kNone && stage_hi != A.n;  // the last line runs past the halo
+        const Span sp = spans(C, t, nown, tail_end, stage_hi == A.n);
+        uint32_t lines = 0;
+        bool shifted = false, pfb = false;
+        const uint32_t e = preprocess(C, sp.a, sp.b, raw, &lines, &shifted, &pfb);
+        fb |= pfb;
+        __syncwarp();
+        if (high) parse<true>(C, sp.a, e);
+        else parse<false>(C, sp.a, e);
+        bool gen_esc = false;
+        const uint32_t ob = count_out(C, sp.a, e, shifted, &gen_esc);
+        fb |= shifted && gen_esc;  // an escaped input byte no longer sits at its input position
+        fb = __any_sync(kAll, fb);
+        if (fb && lane == 0) atomicOr(C.status, kStFallback);
+        const uint32_t oinc = warp_incl_u32(ob), linc = warp_incl_u32(lines);
+        Enc E;
+        E.a = sp.a;
+        E.e = e;
+        E.off = oinc - ob;
+        E.rank = linc - lines;
+        E.total = __shfl_sync(kAll, oinc, 31);
+        E.lines = __shfl_sync(kAll, linc, 31);
+        const bool staged = !fb && E.total + 16u <= (uint32_t)kOutB && E.lines <= (uint32_t)kMaxL;
+        if (staged) {
+            SmemOut so{O.out, O.idx, E.lines};
+            if (lane == 0) O.idx[0] = 0;
+            write_out(C, E.a, E.e, E.off, E.rank, raw, so);
+        }
+        if (fb) {  // the call is run again by the general kernel: this tile and every later one write nothing
+            E.total = E.lines = 0;
+            E.e = E.a;
+        }
+        if (lane == 0) {
+            O.total = E.total;
+            O.lines = E.lines;
+            O.direct = fb ? 2u : (staged ? 0u : 1u);  // 2: nothing left to do (poison published)
+            O.t = t;
+            if ((int64_t)t != C.P->stall_tile) {
+                if (fb) publish(&A.tiles[t], 2u, kPoison, kPoison);
+                else publish(&A.tiles[t], t == 0 ? 2u : 1u, E.total, E.lines);
+            }
+        }
+        __syncwarp();
+        return E;
+    }
+
+    static __device__ __forceinline__ void finish_result(const Ctx &C, uint64_t t, uint64_t tot_a, uint64_t tot_b)
+    {
+        const ShardView &A = *C.A;
+        if (C.lane == 0 && t == A.ntiles - 1) {
+            A.res->out_len = tot_a;
+            A.res->n_lines = tot_b;
+            if (A.index && tot_b < A.index_cap) A.index[tot_b] = tot_a;
+        }
+    }
+
+    // Output offset by look-back, then the staged output and index.
+    static __device__ void finish_staged(const Ctx &C, OutSlot &O)
+    {
+        const ShardView &A = *C.A;
+        const uint64_t t = O.t;
+        uint64_t ea = 0, eb = 0;
+        if (t > 0) lookback_warp(A.tiles, t, &ea, &eb, C.P->limit_ns, C.status);
+        const uint32_t total = O.total, lines = O.lines;
+        if (C.lane == 0 && t > 0 && (int64_t)t != C.P->stall_tile) publish(&A.tiles[t], 2u, ea + total, eb + lines);
+        if (total) warp_copy_realign(O.out, total, A.out + ea, A.out_cap > ea ? A.out_cap - ea : 0);
+        if (A.index)
+            for (uint32_t r = C.lane; r < lines; r += 32)
+                if (eb + r < A.index_cap) A.index[eb + r] = ea + O.idx[r];
+        finish_result(C, t, ea + total, eb + lines);
+        __syncwarp();
+    }
+
+    // A tile whose output or lines do not fit the stage: look back first, then write straight to memory.
+    static __device__ void finish_direct(const Ctx &C, OutSlot &O, const Enc &E)
+    {
+        const ShardView &A = *C.A;
+        const uint64_t t = O.t;
+        uint64_t ea = 0, eb = 0;
+        if (t > 0) lookback_warp(A.tiles, t, &ea, &eb, C.P->limit_ns, C.status);
+        if (C.lane == 0 && t > 0 && (int64_t)t != C.P->stall_tile)
+            publish(&A.tiles[t], 2u, ea + E.total, eb + E.lines);
+        if (C.lane == 0 && A.index && E.lines > 0 && eb < A.index_cap) A.index[eb] = ea;
+        GlobalOut go{A.out, A.out_cap, ea, A.index, A.index_cap, eb, E.lines};
+        write_out(C, E.a, E.e, E.off, E.rank, A.in + tile_base(t) - 16, go);
+        finish_result(C, t, ea + E.total, eb + E.lines);
+        __syncwarp();
+    }
+
+    static __device__ void run(const SpArgs *P)
+    {
+        extern __shared__ __align__(128) uint8_t smem[];
+        __shared__ uint64_t img_bar;
+        const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        WarpMem &M = reinterpret_cast<WarpMem *>(smem)[wid];
+        uint8_t *img = smem + kW * sizeof(WarpMem);
+        Ctx C;
+        C.P = P;
+        C.A = nullptr;
+        C.M = &M;
+        C.tab = img;
+        C.meta = reinterpret_cast<const uint32_t *>(img + P->meta_off);
+        C.lane = lane;
+        C.status = &P->g->status;
+        if (threadIdx.x == 0) mbar_init(&img_bar, 1);
+        if (lane == 0) mbar_init(&M.bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_tx(&img_bar, P->img_bytes);
+            bulk_g2s(img, P->bimg, P->img_bytes, &img_bar);
+        }
+        const bool ok = mbar_wait_bounded(&img_bar, 0, P->limit_ns, C.status);
+        if (!__syncthreads_and(ok)) {
+            mbar_wait_bounded(&img_bar, 0, P->limit_ns, C.status);
+            return;
+        }
+        uint32_t ph = 0, s = 0;
+        bool pending = false;
+        for (;;) {
+            unsigned long long tt = 0;
+            if (lane == 0) tt = atomicAdd(&P->g->tile_counter, 1ull);
+            const uint64_t g = __shfl_sync(kAll, tt, 0);
+            if (g >= P->total_tiles) break;
+            OutSlot &O = M.os[s];
+            const uint32_t sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g);
+            load_shard(&O.sv, P->one, P->shards, P->n_shards, sh);
+            const uint64_t t = g - O.sv.tile0;
+            Ctx Cs = C;
+            Cs.A = &O.sv;
+            if (*((volatile uint32_t *)C.status) & kStFallback) {  // the call is redone: just unblock successors
+                if (lane == 0 && (int64_t)t != P->stall_tile) publish(&O.sv.tiles[t], 2u, kPoison, kPoison);
+                __syncwarp();
+                continue;
+            }
+            stage_issue(Cs, t);
+            if (!mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status)) {
+                mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status);
+                return;
+            }
+            ph ^= 1u;
+            __syncwarp();
+            const Enc E = encode(Cs, O, t);
+            if (pending) {
+                Ctx Cp = C;
+                Cp.A = &M.os[s ^ 1u].sv;
+                finish_staged(Cp, M.os[s ^ 1u]);
+                pending = false;
+            }
+            if (O.direct == 1u) {
+                finish_direct(Cs, O, E);
+            } else if (O.direct == 0u) {
+                pending = true;
+                s ^= 1u;
+            }
+        }
+        if (pending) {
+            Ctx Cp = C;
+            Cp.A = &M.os[s ^ 1u].sv;
+            finish_staged(Cp, M.os[s ^ 1u]);
+        }
+    }
+};
+
+template <class Geo, bool OUTER>
+__global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_span_kernel(const SpArgs P)
+{
+    SP<Geo, OUTER>::run(&P);
+}
+
+// Compiled geometries: 2048-byte tiles (about 44 lines of 46 bytes, so a lane span holds one or two lines)
+// with 20 warps per SM, the most whose stages fit beside a 170-state table; a variant with 4096-byte tiles
+// (longer spans, better balance across lanes, 11 warps) for long-line mixes.
+using SpV0 = SpGeom<20, 2048, 512, 1152, 128>;
+using SpV1 = SpGeom<11, 4096, 512, 2560, 320>;
+// beside the table of a 170-state transducer (the frozen default dictionary; larger tables are checked at
+// run time by span_fits)
+static_assert(20 * sizeof(SP<SpV0, false>::WarpMem) + 170 * 256 + 1024 <= 227 * 1024, "shared memory");
+static_assert(11 * sizeof(SP<SpV1, false>::WarpMem) + 170 * 256 + 1024 <= 227 * 1024, "shared memory");
+
+template <class Geo>
+size_t sp_smem(const zs_dict *d)
+{
+    return SP<Geo, false>::kW * sizeof(typename SP<Geo, false>::WarpMem) + d->blayout.img_bytes;
+}
+
+template <class Geo, bool OUTER>
+cudaError_t sp_launch_as(const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s)
+{
+    SpArgs a{};
+    a.one = L.one;
+    a.shards = L.shards;
+    a.n_shards = L.n_shards;
+    a.flags = flags;
+    a.total_tiles = L.total_tiles;
+    a.bimg = d->d_bimg;
+    a.img_bytes = d->blayout.img_bytes;
+    a.meta_off = d->blayout.meta_off;
+    a.q0 = d->blayout.q0;
+    a.rep_col = d->blayout.rep_col;
+    a.g = L.g;
+    a.limit_ns = wait_limit_ns();
+    a.stall_tile = injected_stall_tile();
+    const int smem = (int)sp_smem<Geo>(d);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static int set_smem = -1;
+    if (set_smem != smem) {
+        cudaError_t e = cudaFuncSetAttribute(compress_span_kernel<Geo, OUTER>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        set_smem = smem;
+    }
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compress_span_kernel<Geo, OUTER>, SP<Geo, OUTER>::kNT, smem);
+    if (per < 1) per = 1;
+    uint64_t grid = std::min<uint64_t>((L.total_tiles + Geo::kWarps - 1) / Geo::kWarps, (uint64_t)per * (uint64_t)sms);
+    if (grid == 0) grid = 1;
+    compress_span_kernel<Geo, OUTER><<<(unsigned)grid, SP<Geo, OUTER>::kNT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class Geo>
+cudaError_t sp_launch(const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s)
+{
+    return (flags & ZS_PREPROCESS_OUTER) ? sp_launch_as<Geo, true>(d, L, flags, s)
+                                         : sp_launch_as<Geo, false>(d, L, flags, s);
+}
+
+struct SpEntry {
+    KernelVariant info;
+    size_t (*smem)(const zs_dict *);
+    cudaError_t (*launch)(const zs_dict *, const TiledLaunch &, unsigned, cudaStream_t);
+};
+
+template <class Geo>
+constexpr SpEntry sp_entry(const char *name)
+{
+    return SpEntry{KernelVariant{name, Geo::kWarps, Geo::kTile}, &sp_smem<Geo>, &sp_launch<Geo>};
+}
+
+const SpEntry kSp[] = {
+    sp_entry<SpV0>("compress span w20 t2048"),
+    sp_entry<SpV1>("compress span w11 t4096"),
+};
+constexpr int kNumSp = (int)(sizeof(kSp) / sizeof(kSp[0]));
+
+}  // namespace
+
+int span_variants() { return kNumSp; }
+
+const KernelVariant *span_variant(int v) { return (v >= 0 && v < kNumSp) ? &kSp[v].info : nullptr; }
+
+bool span_fits(int v, const zs_dict *d)
+{
+    if (v < 0 || v >= kNumSp || !d->has_bytes) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return kSp[v].smem(d) <= (size_t)optin;
+}
+
+cudaError_t launch_span(int v, const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s)
+{
+    if (v < 0 || v >= kNumSp) return cudaErrorInvalidValue;
+    return kSp[v].launch(d, L, flags, s);
+}
+
+}  // namespace zs

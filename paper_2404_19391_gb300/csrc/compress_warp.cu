@@ -1112,12 +1112,23 @@ constexpr int kNumCw = (int)(sizeof(kCw) / sizeof(kCw[0]));
 
 }  // namespace
 
-int compress_warp_variants() { return kNumCw; }
+// Variant numbering of the tiled compression kernels: the span kernel's geometries first
+// (compress_span.cu), then this kernel's.
+int compress_warp_variants() { return span_variants() + kNumCw; }
 
-const KernelVariant *compress_warp_variant(int v) { return (v >= 0 && v < kNumCw) ? &kCw[v].info : nullptr; }
+const KernelVariant *compress_warp_variant(int v)
+{
+    const int ns = span_variants();
+    if (v >= 0 && v < ns) return span_variant(v);
+    v -= ns;
+    return (v >= 0 && v < kNumCw) ? &kCw[v].info : nullptr;
+}
 
 bool compress_warp_fits(int v, const zs_dict *d)
 {
+    const int ns = span_variants();
+    if (v >= 0 && v < ns) return span_fits(v, d);
+    v -= ns;
     if (v < 0 || v >= kNumCw || !d->has_machine) return false;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -1125,8 +1136,13 @@ bool compress_warp_fits(int v, const zs_dict *d)
     return kCw[v].smem(d) <= (size_t)optin;
 }
 
+bool compress_variant_is_span(int v) { return v >= 0 && v < span_variants(); }
+
 cudaError_t launch_compress_warp(int v, const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s)
 {
+    const int ns = span_variants();
+    if (v >= 0 && v < ns) return launch_span(v, d, L, flags, s);
+    v -= ns;
     if (v < 0 || v >= kNumCw) return cudaErrorInvalidValue;
     return kCw[v].launch(d, L, flags, s);
 }

@@ -1,0 +1,547 @@
+// zs_decompress (Sec. IV-D2), expansion kernel: one warp per tile of compressed input, 512 bytes per round.
+//
+//   - Tiles and look-back as in the other tiled kernels: each warp of a persistent CTA claims tiles in
+//     launch order, stages one (and the 16 bytes before it) with one bulk (TMA) copy, and resolves its
+//     output offset by a warp-wide decoupled look-back one tile behind the one it expands (software
+//     pipeline: two output stages per warp).
+//   - Rounds: lane l takes the 16 bytes at 16 l of each 512-byte round (conflict-free 16-byte loads) and
+//     looks up the 16 patterns at once. Each 64-bit entry holds the pattern (up to 7 bytes) and, in its top
+//     byte, its length plus 128 for '\n', so one sum gives the lane's output bytes and newlines; ' ' and
+//     bytes that are no symbol carry a flag instead, and such chunks (rare in SMILES text) take a byte loop.
+//     The table is replicated 16 times so that the 16 lanes of each half-warp read 16 different bank pairs.
+//   - A warp scan places the lanes; each lane funnels its patterns from registers into aligned 32-bit
+//     stores of the tile's output stage. A lane's first word may hold bytes of the lane before it, which
+//     that lane writes byte by byte after the warp's word stores.
+//   - Escapes need no sequential scan: a byte is verbatim exactly when the run of ' ' before it has odd
+//     length (every unescaped ' ' escapes the next byte, and a run starts unescaped).
+//   - The stage leaves with aligned 16-byte stores once the look-back has given the tile's offset; a tile
+//     that expands past its stage writes straight to memory after its look-back instead.
+#include <algorithm>
+
+#include "zs_common.cuh"
+
+namespace zs {
+namespace {
+
+template <int W, int TB, int OUTB>
+struct DxGeom {
+    static constexpr int kWarps = W;  // warps per CTA (one CTA per SM)
+    static constexpr int kTile = TB;  // compressed bytes per warp tile
+    static constexpr int kOut = OUTB; // staged output bytes per tile
+};
+
+constexpr unsigned kAllX = 0xffffffffu;
+constexpr uint32_t kCopies = 16;       // replicas of the pattern table
+constexpr uint32_t kFlag = 0x40000000u; // entry flag (top word): ' ' or a byte that is no symbol
+
+struct DxArgs {
+    ShardView one;
+    const ShardView *shards;
+    uint32_t n_shards;
+    uint32_t _pad;
+    uint64_t total_tiles;
+    const uint8_t *dec;  // plen[256], pat[256][16]
+    DevResult *g;
+    uint64_t limit_ns;
+    int64_t stall_tile;
+};
+
+template <class Geo>
+struct DX {
+    static constexpr int kW = Geo::kWarps;
+    static constexpr int kNT = 32 * kW;
+    static constexpr int kTB = Geo::kTile;
+    static constexpr int kOutB = Geo::kOut;
+    static constexpr int kRounds = kTB / 512;
+    static_assert(kTB % 512 == 0 && kOutB % 16 == 0, "expansion geometry");
+
+    struct alignas(16) OutSlot {
+        uint8_t out[kOutB + 32];
+        uint64_t t;
+        uint32_t total, nls;
+        uint32_t direct, _pad;
+        ShardView sv;
+    };
+
+    struct alignas(16) WarpMem {
+        uint8_t in[16 + kTB + 16];  // the 16 bytes before the tile, the tile
+        OutSlot os[2];
+        uint64_t bar;
+    };
+
+    struct Ctx {
+        const DxArgs *P;
+        const ShardView *A;
+        WarpMem *M;
+        const uint8_t *tab;  // pat8[256][kCopies]
+        const uint8_t *plen;
+        const uint8_t *pat;
+        uint32_t lane, lane8;
+        uint32_t *status;
+    };
+
+    static __device__ __forceinline__ void stage(const Ctx &C, uint64_t t, uint32_t nown)
+    {
+        const ShardView &A = *C.A;
+        WarpMem &M = *C.M;
+        const uint64_t base = t * (uint64_t)kTB;
+        const uint64_t lo = base >= 16 ? base - 16 : 0;
+        const uint32_t j0 = (uint32_t)(lo + 16 - base);
+        const uint32_t nbytes = (uint32_t)(base + nown - lo);
+        const uint32_t nbulk = A.in_aligned ? (nbytes & ~15u) : 0u;
+        __syncwarp();
+        if (C.lane == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_tx(&M.bar, nbulk);
+            if (nbulk) bulk_g2s(M.in + j0, A.in + lo, nbulk, &M.bar);
+        }
+        for (uint32_t j = nbulk + C.lane; j < nbytes; j += 32) M.in[j0 + j] = A.in[lo + j];
+        if (t == 0 && C.lane == 0) M.in[15] = 0;  // nothing precedes the stream
+    }
+
+    // Whether the byte at tile offset c0 is verbatim: the run of ' ' before it has odd length (staged bytes
+    // first, then global memory for a run that reaches past the stage).
+    static __device__ __forceinline__ bool literal_at(const Ctx &C, uint64_t base, uint32_t c0)
+    {
+        const WarpMem &M = *C.M;
+        int32_t q = 15 + (int32_t)c0;  // staged position of the byte before
+        uint32_t run = 0;
+        while (q >= 0 && M.in[q] == kEsc && base + (uint64_t)q >= 16) {
+            ++run;
+            --q;
+        }
+        if (q < 0) {  // the run continues before the stage
+            int64_t g = (int64_t)base - 17;
+            while (g >= 0 && C.A->in[g] == kEsc) {
+                ++run;
+                --g;
+            }
+        }
+        return (run & 1u) != 0;
+    }
+
+    // Byte loop over the staged bytes [p0, p1) (tile offsets): output bytes and newlines, noting malformed
+    // bytes. *lit: in, the first byte is verbatim; out, the last byte was an unpaired ' '.
+    static __device__ __forceinline__ void slow_size(const Ctx &C, uint64_t base, uint32_t p0, uint32_t p1, bool *lit,
+                                                     uint32_t *outb, uint32_t *nls)
+    {
+        const ShardView &A = *C.A;
+        const uint8_t *in = C.M->in + 16;
+        uint32_t ob = 0, nl = 0;
+        bool l = *lit;
+        for (uint32_t p = p0; p < p1; ++p) {
+            const uint8_t b = in[p];
+            if (l) {
+                if (b == kNl) {  // a line ending in an unpaired escape
+                    note_error_offset(A.res, base + p - 1);
+                    atomicOr(C.status, kStMalformed);
+                }
+                ob += 1;
+                nl += (b == kNl);
+                l = false;
+            } else if (b == kEsc) {
+                l = true;
+            } else if (b == kNl) {
+                ob += 1;
+                nl += 1;
+            } else {
+                const uint32_t len = C.plen[b];
+                if (len == 0) {
+                    note_error_offset(A.res, base + p);
+                    atomicOr(C.status, kStMalformed);
+                }
+                ob += len;
+            }
+        }
+        *lit = l;
+        *outb = ob;
+        *nls = nl;
+    }
+
+    // The same walk writing the bytes: into the stage at pos (STAGED) or to out[ea + pos] below cap.
+    template <bool STAGED>
+    static __device__ __forceinline__ void slow_write(const Ctx &C, uint32_t p0, uint32_t p1, bool lit, uint32_t pos,
+                                                      uint8_t *stg, uint64_t ea)
+    {
+        const ShardView &A = *C.A;
+        const uint8_t *in = C.M->in + 16;
+        auto put = [&](uint32_t w, uint8_t v) {
+            if (STAGED) stg[w] = v;
+            else if (ea + w < A.out_cap) A.out[ea + w] = v;
+        };
+        for (uint32_t p = p0; p < p1; ++p) {
+            const uint8_t b = in[p];
+            if (!lit && b == kEsc) {
+                lit = true;
+                continue;
+            }
+            if (lit || b == kNl) {
+                lit = false;
+                put(pos++, b);
+                continue;
+            }
+            const uint32_t l = C.plen[b];
+            for (uint32_t k = 0; k < l; ++k) put(pos + k, C.pat[16u * b + k]);
+            pos += l;
+        }
+    }
+
+    // One round's lanes: the chunk of lane `lane`, its 16 entries (fast path) or the byte-loop sizes.
+    struct Chunk {
+        uint32_t lo[16], hi[16];
+        uint32_t p0, p1;   // tile offsets of the chunk's valid bytes
+        uint32_t outb, nls;
+        bool fast, lit;
+    };
+
+    static __device__ __forceinline__ void load_chunk(const Ctx &C, uint64_t base, uint32_t nown, uint32_t r, Chunk &K)
+    {
+        const uint32_t c0 = (uint32_t)r * 512u + C.lane * 16u;
+        K.p0 = min(c0, nown);
+        K.p1 = min(c0 + 16u, nown);
+        K.outb = K.nls = 0;
+        K.lit = false;
+        K.fast = false;
+        if (K.p1 <= K.p0) return;
+        const uint8_t *in = C.M->in + 16;
+        K.fast = K.p1 - K.p0 == 16 && in[(int32_t)c0 - 1] != kEsc;
+        if (K.fast) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(in + c0);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            uint32_t acc = 0, fl = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const uint32_t b = (w[k >> 2] >> (8 * (k & 3))) & 255u;
+                const uint2 e = *reinterpret_cast<const uint2 *>(C.tab + ((b << 7) | C.lane8));
+                K.lo[k] = e.x;
+                K.hi[k] = e.y;
+                acc += e.y >> 24;
+                fl |= e.y;
+            }
+            if (fl & kFlag) {
+                K.fast = false;
+            } else {
+                K.outb = acc & 127u;
+                K.nls = acc >> 7;
+                return;
+            }
+        }
+        K.lit = literal_at(C, base, K.p0);
+        bool lit = K.lit;
+        slow_size(C, base, K.p0, K.p1, &lit, &K.outb, &K.nls);
+        if (lit && base + K.p1 == C.A->n) {  // the stream ends in an unpaired escape
+            note_error_offset(C.A->res, C.A->n - 1);
+            atomicOr(C.status, kStMalformed);
+        }
+    }
+
+    // Funnel of a fast chunk's patterns into aligned words of the stage from byte offset pos; returns the
+    // pending partial word (bytes [*wpos, *wpos + *n)) for the second phase. first: pos is where this
+    // round begins, so the stage's word there already holds the previous round's bytes below pos.
+    static __device__ __forceinline__ uint32_t funnel(const Chunk &K, uint8_t *stg, uint32_t pos, bool first,
+                                                      uint32_t *wpos_out, uint32_t *n_out)
+    {
+        uint32_t wpos = pos & ~3u, n = pos & 3u;
+        uint32_t a = 0;
+        if (first && n) a = *reinterpret_cast<const uint32_t *>(stg + wpos) & ((1u << (8 * n)) - 1u);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t l = K.hi[k] >> 24;  // no flag on a fast chunk: the length (no newline bit: below)
+            const uint32_t len = l & 7u;
+            const uint32_t h = K.hi[k] & 0x00FFFFFFu;
+            const uint32_t sh = 8u * n;
+            const uint32_t w0 = a | (K.lo[k] << sh);
+            const uint32_t w1 = __funnelshift_l(K.lo[k], h, sh);
+            const uint32_t w2 = __funnelshift_l(h, 0u, sh);
+            const uint32_t tot = n + len;
+            if (tot >= 4) *reinterpret_cast<uint32_t *>(stg + wpos) = w0;
+            if (tot >= 8) *reinterpret_cast<uint32_t *>(stg + wpos + 4) = w1;
+            a = tot >= 8 ? w2 : (tot >= 4 ? w1 : w0);
+            n = tot & 3u;
+            wpos += tot & ~3u;
+        }
+        *wpos_out = wpos;
+        *n_out = n;
+        return a;
+    }
+
+    // Sizes of one round, warp scan; returns the round's total; *pos = the lane's output offset in the round.
+    static __device__ __forceinline__ uint32_t place(const Ctx &C, const Chunk &K, uint32_t *pos)
+    {
+        const uint32_t inc = warp_incl_u32(K.outb);
+        *pos = inc - K.outb;
+        return __shfl_sync(kAllX, inc, 31);
+    }
+
+    // Expansion of a tile into slot O's stage. Returns false (nothing more written) once the tile outgrows
+    // the stage; *total and *nls are the tile's totals either way.
+    static __device__ bool expand(const Ctx &C, OutSlot &O, uint64_t t, uint32_t nown, uint32_t *total_out,
+                                  uint32_t *nls_out)
+    {
+        const uint64_t base = t * (uint64_t)kTB;
+        uint8_t *stg = O.out;
+        uint32_t run = 0, nls = 0;
+        bool fits = true;
+        for (int r = 0; r < kRounds; ++r) {
+            if ((uint32_t)r * 512u >= nown) break;
+            Chunk K;
+            load_chunk(C, base, nown, (uint32_t)r, K);
+            uint32_t pos;
+            const uint32_t rt = place(C, K, &pos);
+            nls += K.nls;
+            if (fits && run + rt + 32u > (uint32_t)kOutB) fits = false;
+            if (fits) {
+                uint32_t wpos = 0, n = 0, a = 0;
+                if (K.fast) a = funnel(K, stg, run + pos, pos == 0, &wpos, &n);
+                __syncwarp();
+                if (K.fast) {  // the pending partial word, byte by byte, never below the lane's first byte
+                    const uint32_t p0 = run + pos;
+                    const uint32_t j0 = wpos == (p0 & ~3u) ? (p0 & 3u) : 0u;
+                    for (uint32_t j = j0; j < n; ++j) stg[wpos + j] = (uint8_t)(a >> (8 * j));
+                } else if (K.p1 > K.p0) {
+                    slow_write<true>(C, K.p0, K.p1, K.lit, run + pos, stg, 0);
+                }
+                __syncwarp();
+            }
+            run += rt;
+        }
+        *total_out = run;
+        *nls_out = __reduce_add_sync(kAllX, nls);
+        return fits;
+    }
+
+    // A tile that outgrew its stage: sizes again round by round, bytes straight to out[ea + ...].
+    static __device__ void expand_direct(const Ctx &C, uint64_t t, uint32_t nown, uint64_t ea)
+    {
+        const uint64_t base = t * (uint64_t)kTB;
+        uint32_t run = 0;
+        for (int r = 0; r < kRounds; ++r) {
+            if ((uint32_t)r * 512u >= nown) break;
+            Chunk K;
+            load_chunk(C, base, nown, (uint32_t)r, K);
+            uint32_t pos;
+            const uint32_t rt = place(C, K, &pos);
+            if (K.p1 > K.p0) {
+                bool lit = K.fast ? false : K.lit;
+                if (K.fast) lit = false;
+                slow_write<false>(C, K.p0, K.p1, lit, run + pos, nullptr, ea);
+            }
+            run += rt;
+        }
+        __syncwarp();
+    }
+
+    static __device__ __forceinline__ void finish_result(const Ctx &C, uint64_t t, uint64_t tot_a, uint64_t tot_b)
+    {
+        const ShardView &A = *C.A;
+        if (C.lane == 0 && t == A.ntiles - 1) {
+            A.res->out_len = tot_a;
+            A.res->n_lines = tot_b + ((A.in[A.n - 1] != kNl) ? 1u : 0u);
+        }
+    }
+
+    static __device__ void finish_staged(const Ctx &C, OutSlot &O)
+    {
+        const ShardView &A = *C.A;
+        const uint64_t t = O.t;
+        uint64_t ea = 0, eb = 0;
+        if (t > 0) lookback_warp(A.tiles, t, &ea, &eb, C.P->limit_ns, C.status);
+        if (C.lane == 0 && t > 0 && (int64_t)t != C.P->stall_tile) publish(&A.tiles[t], 2u, ea + O.total, eb + O.nls);
+        if (O.total) warp_copy_realign(O.out, O.total, A.out + ea, A.out_cap > ea ? A.out_cap - ea : 0);
+        finish_result(C, t, ea + O.total, eb + O.nls);
+        __syncwarp();
+    }
+
+    static __device__ void run(const DxArgs *P)
+    {
+        extern __shared__ __align__(128) uint8_t smem[];
+        __shared__ uint64_t tab_bar;
+        const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        WarpMem &M = reinterpret_cast<WarpMem *>(smem)[wid];
+        uint8_t *tab = smem + kW * sizeof(WarpMem);  // pat8[256][kCopies], then plen[256] and pat[256][16]
+        uint8_t *dec = tab + 256 * kCopies * 8;
+        Ctx C;
+        C.P = P;
+        C.A = nullptr;
+        C.M = &M;
+        C.tab = tab;
+        C.plen = dec;
+        C.pat = dec + 256;
+        C.lane = lane;
+        C.lane8 = (lane & 15u) * 8u;
+        C.status = &P->g->status;
+        if (threadIdx.x == 0) mbar_init(&tab_bar, 1);
+        if (lane == 0) mbar_init(&M.bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_tx(&tab_bar, kDecBytes);
+            bulk_g2s(dec, P->dec, kDecBytes, &tab_bar);
+        }
+        const bool ok = mbar_wait_bounded(&tab_bar, 0, P->limit_ns, C.status);
+        if (!__syncthreads_and(ok)) {
+            mbar_wait_bounded(&tab_bar, 0, P->limit_ns, C.status);
+            return;
+        }
+        // pat8: pattern bytes 0-6, top byte = length | 128 for '\n'; ' ' and non-symbols carry kFlag
+        for (uint32_t i = threadIdx.x; i < 256 * kCopies; i += blockDim.x) {
+            const uint32_t b = i / kCopies;
+            const uint32_t l = dec[b];
+            uint64_t e;
+            if (b == kNl) {
+                e = (uint64_t)kNl | (0x81ull << 56);
+            } else if (b == kEsc || l == 0) {
+                e = (uint64_t)kFlag << 32;
+            } else {
+                e = (uint64_t)l << 56;
+                for (uint32_t k = 0; k < l; ++k) e |= (uint64_t)dec[256 + 16 * b + k] << (8 * k);
+            }
+            reinterpret_cast<uint64_t *>(tab)[i] = e;
+        }
+        __syncthreads();
+        uint32_t ph = 0, s = 0;
+        bool pending = false;
+        for (;;) {
+            unsigned long long tt = 0;
+            if (lane == 0) tt = atomicAdd(&P->g->tile_counter, 1ull);
+            const uint64_t g = __shfl_sync(kAllX, tt, 0);
+            if (g >= P->total_tiles) break;
+            OutSlot &O = M.os[s];
+            const uint32_t sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g);
+            load_shard(&O.sv, P->one, P->shards, P->n_shards, sh);
+            const uint64_t t = g - O.sv.tile0;
+            Ctx Cs = C;
+            Cs.A = &O.sv;
+            const uint64_t base = t * (uint64_t)kTB;
+            const uint32_t nown = (uint32_t)(min(O.sv.n, base + kTB) - base);
+            stage(Cs, t, nown);
+            if (!mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status)) {
+                mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status);
+                return;
+            }
+            ph ^= 1u;
+            __syncwarp();
+            uint32_t total = 0, nls = 0;
+            const bool fits = expand(Cs, O, t, nown, &total, &nls);
+            if (lane == 0) {
+                O.t = t;
+                O.total = total;
+                O.nls = nls;
+                O.direct = fits ? 0u : 1u;
+                if ((int64_t)t != P->stall_tile) publish(&O.sv.tiles[t], t == 0 ? 2u : 1u, total, nls);
+            }
+            __syncwarp();
+            if (pending) {
+                Ctx Cp = C;
+                Cp.A = &M.os[s ^ 1u].sv;
+                finish_staged(Cp, M.os[s ^ 1u]);
+                pending = false;
+            }
+            if (!fits) {  // look back first, then write straight to memory
+                uint64_t ea = 0, eb = 0;
+                if (t > 0) lookback_warp(O.sv.tiles, t, &ea, &eb, P->limit_ns, C.status);
+                if (lane == 0 && t > 0 && (int64_t)t != P->stall_tile) publish(&O.sv.tiles[t], 2u, ea + total, eb + nls);
+                expand_direct(Cs, t, nown, ea);
+                finish_result(Cs, t, ea + total, eb + nls);
+                __syncwarp();
+            } else {
+                pending = true;
+                s ^= 1u;
+            }
+        }
+        if (pending) {
+            Ctx Cp = C;
+            Cp.A = &M.os[s ^ 1u].sv;
+            finish_staged(Cp, M.os[s ^ 1u]);
+        }
+    }
+};
+
+template <class Geo>
+__global__ void __launch_bounds__(Geo::kWarps * 32, 1) decompress_expand_kernel(const DxArgs P)
+{
+    DX<Geo>::run(&P);
+}
+
+// Compiled geometries: 2048-byte tiles (four rounds) with a stage of 2.25 x the tile, 16 warps per SM beside
+// the 36 KB of tables; and 1024-byte tiles (2.5 x) with 24 warps.
+using DxV0 = DxGeom<16, 2048, 4608>;
+using DxV1 = DxGeom<24, 1024, 2560>;
+static_assert(16 * sizeof(DX<DxV0>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "shared memory");
+static_assert(24 * sizeof(DX<DxV1>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "shared memory");
+
+template <class Geo>
+size_t dx_smem()
+{
+    return DX<Geo>::kW * sizeof(typename DX<Geo>::WarpMem) + 256 * kCopies * 8 + kDecBytes;
+}
+
+template <class Geo>
+cudaError_t dx_launch(const zs_dict *d, const TiledLaunch &L, cudaStream_t s)
+{
+    DxArgs a{};
+    a.one = L.one;
+    a.shards = L.shards;
+    a.n_shards = L.n_shards;
+    a.total_tiles = L.total_tiles;
+    a.dec = d->d_dec;
+    a.g = L.g;
+    a.limit_ns = wait_limit_ns();
+    a.stall_tile = injected_stall_tile();
+    const int smem = (int)dx_smem<Geo>();
+    static int per = -1;
+    if (per < 0) {
+        cudaError_t e = cudaFuncSetAttribute(decompress_expand_kernel<Geo>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, decompress_expand_kernel<Geo>, DX<Geo>::kNT, smem);
+        if (per < 1) per = 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t grid = std::max<uint64_t>(
+        1, std::min<uint64_t>((L.total_tiles + Geo::kWarps - 1) / Geo::kWarps, (uint64_t)per * (uint64_t)sms));
+    decompress_expand_kernel<Geo><<<(unsigned)grid, DX<Geo>::kNT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+struct DxEntry {
+    KernelVariant info;
+    size_t (*smem)();
+    cudaError_t (*launch)(const zs_dict *, const TiledLaunch &, cudaStream_t);
+};
+
+template <class Geo>
+constexpr DxEntry dx_entry(const char *name)
+{
+    return DxEntry{KernelVariant{name, Geo::kWarps, Geo::kTile}, &dx_smem<Geo>, &dx_launch<Geo>};
+}
+
+const DxEntry kDx[] = {
+    dx_entry<DxV0>("decompress expand w16 t2048"),
+    dx_entry<DxV1>("decompress expand w24 t1024"),
+};
+constexpr int kNumDx = (int)(sizeof(kDx) / sizeof(kDx[0]));
+
+}  // namespace
+
+int expand_variants() { return kNumDx; }
+
+const KernelVariant *expand_variant(int v) { return (v >= 0 && v < kNumDx) ? &kDx[v].info : nullptr; }
+
+bool expand_fits(int v, const zs_dict *d)
+{
+    if (v < 0 || v >= kNumDx || d->max_plen > 7) return false;  // patterns and length share a 64-bit entry
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return kDx[v].smem() <= (size_t)optin;
+}
+
+cudaError_t launch_expand(int v, const zs_dict *d, const TiledLaunch &L, cudaStream_t s)
+{
+    if (v < 0 || v >= kNumDx) return cudaErrorInvalidValue;
+    return kDx[v].launch(d, L, s);
+}
+
+}  // namespace zs

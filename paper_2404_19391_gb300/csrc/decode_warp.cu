@@ -518,29 +518,54 @@ constexpr int kNumDw = (int)(sizeof(kDwv) / sizeof(kDwv[0]));
 
 }  // namespace
 
-int decompress_variants() { return kNumDw; }
+// Variant numbering of the decompression kernels: the expansion kernel's geometries first
+// (decode_expand.cu), then this kernel's.
+int decompress_variants() { return expand_variants() + kNumDw; }
 
-const KernelVariant *decompress_variant(int v) { return (v >= 0 && v < kNumDw) ? &kDwv[v].info : nullptr; }
+const KernelVariant *decompress_variant(int v)
+{
+    const int nx = expand_variants();
+    if (v >= 0 && v < nx) return expand_variant(v);
+    v -= nx;
+    return (v >= 0 && v < kNumDw) ? &kDwv[v].info : nullptr;
+}
+
+bool decompress_fits(int v, const zs_dict *d)
+{
+    const int nx = expand_variants();
+    if (v >= 0 && v < nx) return expand_fits(v, d);
+    return v >= nx && v < nx + kNumDw;
+}
+
+int decompress_default_variant(const zs_dict *d) { return expand_fits(0, d) ? 0 : expand_variants(); }
 
 cudaError_t launch_decompress(int v, const zs_dict *d, const TiledLaunch &L, cudaStream_t s)
 {
+    const int nx = expand_variants();
+    if (v >= 0 && v < nx) return launch_expand(v, d, L, s);
+    v -= nx;
     if (v < 0 || v >= kNumDw) return cudaErrorInvalidValue;
     return kDwv[v].launch(d, L, s);
 }
 
-uint64_t decompress_tiles(uint64_t n) { return tiles_for(n, kDwv[kDefaultVariant].info.tile_bytes); }
+// Look-back records for a single-stream call: enough for the smaller of the two default tiles.
+uint64_t decompress_tile_bytes()
+{
+    return std::min<uint64_t>(expand_variant(0)->tile_bytes, kDwv[0].info.tile_bytes);
+}
 
-uint64_t decompress_tile_bytes() { return kDwv[kDefaultVariant].info.tile_bytes; }
+uint64_t decompress_tiles(uint64_t n) { return tiles_for(n, (uint32_t)decompress_tile_bytes()); }
 
 cudaError_t launch_decompress_single(const zs_dict *d, const uint8_t *in, uint64_t n, uint8_t *out, uint64_t out_cap,
                                      DevResult *res, TileState *tiles, cudaStream_t s)
 {
+    const int v = decompress_default_variant(d);
     TiledLaunch L{};
-    L.one = single_shard(in, n, out, out_cap, nullptr, 0, tiles, res, decompress_tiles(n));
+    L.one = single_shard(in, n, out, out_cap, nullptr, 0, tiles, res, tiles_for(n, decompress_variant(v)->tile_bytes));
     L.n_shards = 1;
     L.total_tiles = L.one.ntiles;
     L.g = res;
-    return launch_decompress(kDefaultVariant, d, L, s);
+    return launch_decompress(v, d, L, s);
 }
 
 }  // namespace zs

@@ -445,6 +445,54 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
         memcpy(mimg.data() + zs::kMOffTable, rows.data(), rows.size() * 4);
     }
 
+    // byte-indexed transducer for the span kernel: at most 256 states (8-bit next state), every symbol
+    // above ' ' (so choices up to ' ' are free for escapes and '\n'), every pattern byte below 0x80 and
+    // some byte below 0x80 in no pattern that stands for the bytes >= 0x80
+    std::vector<uint8_t> bimg;
+    zs::ByteLayout BL{};
+    if (use_machine && mach.states <= 256) {
+        bool ok = true;
+        for (auto &en : entries) {
+            if (en.sym <= zs::kEsc) ok = false;
+            for (unsigned char c : en.pat)
+                if (c >= 0x80) ok = false;
+        }
+        int rep = -1;
+        for (int b = 1; b < 128 && rep < 0; ++b)
+            if (cls[b] == zs::kClsOther) rep = b;
+        if (ok && rep > 0) {
+            const uint32_t S = (uint32_t)mach.states;
+            BL.n_states = S;
+            BL.q0 = (uint32_t)mach.start;
+            BL.meta_off = S * 256u;
+            BL.img_bytes = BL.meta_off + 1024u;
+            BL.rep_col = 2u * (uint32_t)rep;
+            bimg.assign(BL.img_bytes, 0);
+            uint16_t *t16 = reinterpret_cast<uint16_t *>(bimg.data());
+            for (uint32_t q = 0; q < S; ++q)
+                for (uint32_t b = 0; b < 128; ++b) {
+                    uint32_t ns, ch;
+                    if (b == zs::kNl) {
+                        ns = BL.q0;
+                        ch = zs::kNl;
+                    } else {
+                        const uint32_t e2 = mach.table[(size_t)q * n_classes + cls[b]];
+                        ns = e2 & 0xFFFFu;
+                        ch = e2 >> 24;
+                        if (ch == zs::kEsc && b >= '0' && b <= '9') ch = 0x10u + (b - '0');
+                    }
+                    t16[q * 128 + b] = (uint16_t)(ns | (ch << 8));
+                }
+            uint32_t *meta = reinterpret_cast<uint32_t *>(bimg.data() + BL.meta_off);
+            for (uint32_t c = 0; c < 256; ++c) {
+                uint32_t step = 1, outb = 1;
+                if (c == zs::kEsc || (c >= 0x10 && c < 0x1A)) outb = 2;
+                else if (c > zs::kEsc && plen[c]) step = plen[c];
+                meta[c] = step | (outb << 13);
+            }
+        }
+    }
+
     std::vector<uint8_t> dec(zs::kDecBytes, 0);
     memcpy(dec.data(), plen, 256);
     memcpy(dec.data() + 256, pat, sizeof pat);
@@ -461,6 +509,8 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
     d->layout = L;
     d->mlayout = ML;
     d->has_machine = use_machine;
+    d->blayout = BL;
+    d->has_bytes = !bimg.empty();
     memcpy(d->plen, plen, 256);
     memcpy(d->pat, pat, sizeof pat);
     e = cudaMalloc((void **)&d->d_enc, L.img_bytes);
@@ -471,8 +521,13 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
         e = cudaMalloc((void **)&d->d_mimg, ML.img_bytes);
         if (e == cudaSuccess) e = cudaMemcpy(d->d_mimg, mimg.data(), ML.img_bytes, cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && d->has_bytes) {
+        e = cudaMalloc((void **)&d->d_bimg, BL.img_bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(d->d_bimg, bimg.data(), BL.img_bytes, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (d->d_bimg) cudaFree(d->d_bimg);
         if (d->d_enc) cudaFree(d->d_enc);
         if (d->d_dec) cudaFree(d->d_dec);
         if (d->d_mimg) cudaFree(d->d_mimg);
@@ -494,6 +549,7 @@ extern "C" void zs_free_dictionary(zs_dict *d)
     if (d->d_enc) cudaFree(d->d_enc);
     if (d->d_dec) cudaFree(d->d_dec);
     if (d->d_mimg) cudaFree(d->d_mimg);
+    if (d->d_bimg) cudaFree(d->d_bimg);
     if (cur >= 0) cudaSetDevice(cur);
     delete d;
 }

@@ -227,9 +227,10 @@ zs_status run_pipeline(const zs_dict *dc, zs_op op, const uint8_t *h_in, size_t 
         cudaError_t e2 = cudaEventSynchronize(s.ev);
         if (e2 != cudaSuccess) return e2;
         zs::DevResult r = *s.h_res;
-        if (op == ZS_OP_COMPRESS && (r.status & zs::kStSlowOverflow)) {
-            // the long-line scratch of the slot was too small: code this chunk again with the library's own
-            // scratch, which grows as needed
+        if (op == ZS_OP_COMPRESS && (r.status & (zs::kStSlowOverflow | zs::kStFallback))) {
+            // the long-line scratch of the slot was too small, or the chunk holds a line outside the span
+            // kernel's fast path: code this chunk again through zs_compress, whose scratch grows as needed
+            // and which runs the general kernel when the span kernel cannot
             zs_result rr{};
             const zs_status s2 = zs_compress(d, s.d_in, s.len, flags, s.d_out, out_bound(d, op, s.len),
                                              h_index ? s.d_idx : nullptr, h_index ? s.len + 2 : 0, &rr, s.st);

@@ -7,6 +7,8 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <utility>
 
 #include "../../include/zsmiles.h"
 
@@ -72,6 +74,22 @@ struct MachineLayout {
     uint32_t _pad[2];
 };
 constexpr uint32_t kMOffClsRep = 0, kMOffPlen = 8192, kMOffTable = 8448;
+
+// Byte-indexed parse transducer (the span kernel): the minimal transducer above with its columns indexed by
+// the raw byte (bytes 0-127; bytes >= 0x80 read the column of a byte below 0x80 in no pattern), so a lookup
+// needs no class table.
+//   [0, 256 * n_states)    table[state][128] (u16): next state | choice << 8, at byte offset state * 256 +
+//                          2 * byte. Choices: a symbol (every symbol is above ' '); ' ' = escape of the input
+//                          byte; 0x10 + d = escape of the digit d; '\n' = end of line (next state: the start)
+//   [meta_off, +1024)      meta[256] (u32) per choice: input bytes consumed | output bytes << 13
+struct ByteLayout {
+    uint32_t n_states;
+    uint32_t q0;         // start state
+    uint32_t meta_off;
+    uint32_t img_bytes;
+    uint32_t rep_col;    // 2 * the stand-in byte for bytes >= 0x80
+    uint32_t _pad[3];
+};
 constexpr uint32_t kMaxMachineBytes = 64u * 1024u;  // transition table budget in shared memory
 
 // Decoder tables (global, staged per CTA): plen[256] then pat[256][16].
@@ -94,6 +112,8 @@ enum : uint32_t {
     kStMalformed = 2u,     // bad compressed byte / request
     kStSlowOverflow = 4u,  // the long/irregular-line scratch was too small (host retries larger)
     kStTooBig = 8u,        // a single line needs more than 4 GiB of work space
+    kStFallback = 16u,     // the span kernel met a line outside its fast path: the call is run again by the
+                           // general kernel
 };
 
 struct alignas(16) DevResult {
@@ -121,13 +141,15 @@ struct Scratch {
 class ScratchPool {
    public:
     ~ScratchPool();
-    // Returns the scratch of `stream`, grown to hold `tiles` tile states and `slow` long-line bytes.
+    // Returns the scratch of `stream` for the calling host thread, grown to hold `tiles` tile states and
+    // `slow` long-line bytes. Keyed by thread as well as stream: calls from several threads on one stream
+    // are ordered on the device by the stream, but each needs its own host-side result record.
     zs_status get(void *stream, size_t tiles, size_t slow, Scratch **out);
     void release_all();
 
    private:
     std::mutex mu_;
-    std::map<void *, Scratch> map_;
+    std::map<std::pair<void *, std::thread::id>, Scratch> map_;
 };
 
 ScratchPool &global_pool();
@@ -160,6 +182,9 @@ struct zs_dict {
     zs::EncLayout layout{};
     zs::MachineLayout mlayout{};
     bool has_machine = false;
+    zs::ByteLayout blayout{};
+    bool has_bytes = false;     // the byte-indexed transducer exists (span kernel)
+    uint8_t *d_bimg = nullptr;  // its image (blayout.img_bytes)
     uint8_t *d_enc = nullptr;  // encoder image (layout.img_bytes)
     uint8_t *d_mimg = nullptr; // parse-transducer image (mlayout.img_bytes), if it fits
     uint8_t *d_dec = nullptr;  // decoder tables (kDecBytes)
@@ -180,7 +205,8 @@ void free_pipes(zs_dict *d);
 uint64_t compress_scratch_tiles(const zs_dict *d, uint64_t n);
 cudaError_t launch_compress_any(const zs_dict *d, const uint8_t *in, uint64_t n, unsigned flags, uint8_t *out,
                                 uint64_t out_cap, uint64_t *index, uint64_t index_cap, DevResult *res,
-                                TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s);
+                                TileState *tiles, uint8_t *slow, uint64_t slow_cap, cudaStream_t s,
+                                bool general = false);
 }  // namespace zs
 
 // ------------------------------------------------------------------------------------------------
@@ -481,6 +507,49 @@ __device__ __forceinline__ void warp_copy_out(const uint8_t *stage, uint32_t so,
     for (uint32_t k = max(c1 * 16u, h1) + lane; k < end; k += 32) g[k] = stage[k];
 }
 
+// Copies a warp's stage [0, len) to dst[0, len) for any alignment of dst (bytes at or past cap are not
+// written): each whole 16-byte chunk of the destination is one store, its bytes taken from two 16-byte
+// chunks of the stage by funnel shifts; the partial chunks at either end go byte by byte. The stage is
+// 16-byte aligned and readable up to 16 bytes past len. Called by all 32 lanes.
+template <int Q>
+__device__ __forceinline__ uint4 shift_chunk(const uint4 A, const uint4 B, uint32_t sh)
+{
+    const uint32_t v[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
+    return make_uint4(__funnelshift_r(v[Q], v[Q + 1], sh), __funnelshift_r(v[Q + 1], v[Q + 2], sh),
+                      __funnelshift_r(v[Q + 2], v[Q + 3], sh), __funnelshift_r(v[Q + 3], v[Q + 4], sh));
+}
+
+__device__ __forceinline__ void warp_copy_realign(const uint8_t *stg, uint64_t len64, uint8_t *dst, uint64_t cap)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t len = (uint32_t)min(len64, cap);
+    const uint32_t so = (uint32_t)((uintptr_t)dst & 15u);
+    uint4 *g = reinterpret_cast<uint4 *>(dst - so);
+    const uint4 *s16 = reinterpret_cast<const uint4 *>(stg);
+    const uint32_t j0 = so ? 1u : 0u, j1 = (len + so) >> 4;  // whole destination chunks [j0, j1)
+    if (so == 0) {
+        for (uint32_t j = lane; j < j1; j += 32) g[j] = s16[j];
+    } else {
+        // destination chunk j = stage bytes [16 j - so, 16 j - so + 16): chunk j - 1 from byte r = 16 - so on
+        const uint32_t r = 16u - so, q = r >> 2, sh = 8u * (r & 3u);
+        for (uint32_t j = j0 + lane; j < j1; j += 32) {
+            const uint4 A = s16[j - 1], B = s16[j];
+            uint4 o;
+            switch (q) {
+                case 0: o = shift_chunk<0>(A, B, sh); break;
+                case 1: o = shift_chunk<1>(A, B, sh); break;
+                case 2: o = shift_chunk<2>(A, B, sh); break;
+                default: o = shift_chunk<3>(A, B, sh); break;
+            }
+            g[j] = o;
+        }
+    }
+    const uint32_t h1 = min(len, j0 * 16u - so);  // head bytes [0, h1)
+    for (uint32_t k = lane; k < h1; k += 32) dst[k] = stg[k];
+    const uint32_t t0 = j1 > j0 ? max(h1, j1 * 16u - so) : h1;  // tail bytes [t0, len)
+    for (uint32_t k = t0 + lane; k < len; k += 32) dst[k] = stg[k];
+}
+
 __device__ __forceinline__ void note_error_offset(DevResult *r, uint64_t off)
 {
     atomicMax(&r->err_key, ~(unsigned long long)off);
@@ -544,14 +613,29 @@ inline ShardView single_shard(const uint8_t *in, uint64_t n, uint8_t *out, uint6
     return v;
 }
 
+// Span kernel (compress_span.cu): compiled geometries, fit, launch.
+int span_variants();
+const KernelVariant *span_variant(int v);
+bool span_fits(int v, const zs_dict *d);
+cudaError_t launch_span(int v, const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s);
+
 // Compiled variants of the tiled compression (transducer) and decompression kernels.
 int compress_warp_variants();
 const KernelVariant *compress_warp_variant(int v);
 bool compress_warp_fits(int v, const zs_dict *d);
 int compress_default_variant(const zs_dict *d);  // the geometry zs_compress uses, or -1: the generic kernel
+int compress_general_variant(const zs_dict *d);  // the same without the span kernel (its fallback)
+bool compress_variant_is_span(int v);
 cudaError_t launch_compress_warp(int v, const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s);
 int decompress_variants();
 const KernelVariant *decompress_variant(int v);
+bool decompress_fits(int v, const zs_dict *d);
+int decompress_default_variant(const zs_dict *d);  // the expansion kernel unless a pattern exceeds 7 bytes
+// Expansion kernel (decode_expand.cu): compiled geometries, fit, launch.
+int expand_variants();
+const KernelVariant *expand_variant(int v);
+bool expand_fits(int v, const zs_dict *d);
+cudaError_t launch_expand(int v, const zs_dict *d, const TiledLaunch &L, cudaStream_t s);
 cudaError_t launch_decompress(int v, const zs_dict *d, const TiledLaunch &L, cudaStream_t s);
 // Random access (decode.cu): tile records a launch over k requested ids needs, and the launch itself
 // (out_off[k + 1] receives each line's output offset and the total).
