@@ -1,20 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the ZSMILES codec hot path on GB300.
 
-Workload (N=1): the large single-stream configuration - 10,000,000 seeded synthetic SMILES lines
-(drug-like, mean ~49 bytes, ~490 MB), one shard per launch, the frozen default dictionary.
+Workload (N=1): the batched configuration - 64 shards of seeded synthetic SMILES lines (line counts log-uniform
+in 1k-5M, per-shard mean length 25-70; about 49M lines, 2.47 GB), the frozen default dictionary.
 
-One step = the whole hot path over that stream, through the C ABI on device-resident data:
-    zs_compress (pre-processing + shortest-output parse + line index)
-    -> zs_decompress of the result
-    -> zs_decompress_lines of 100,000 random line ids (random access).
-value = uncompressed bytes per second of step (GB/s, 1e9). Inputs (490 MB) are larger than the 129 MB L2,
-so no flush is needed between steps.
+One step = the whole hot path over those shards, through the C ABI on device-resident data:
+    zs_plan_run of the compression plan (pre-processing + shortest-output parse + line index, all 64 shards in
+    one persistent launch replayed from a CUDA graph, geometry autotuned)
+    -> zs_plan_run of the decompression plan over the 64 compressed streams
+    -> zs_decompress_lines of 100,000 random line ids of the largest shard (random access).
+value = uncompressed bytes per second of step (GB/s, 1e9); the line also gives each direction on its own
+(input GB/s and the fraction of HBM bandwidth its kernel reaches) and the random-access p99. Inputs are larger
+than the 129 MB L2, so no flush is needed between steps. Extra keys: the batched form against one launch per
+shard, config 1 (one 10M-line stream), config 3 (100M long-tail lines), the serving sweep (config 4), the
+CPU oracle.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--lines L]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank runs its own replica on its own 10M-line range (weak scaling, no
-collective on the data path); timing is the max over ranks.
+Under torchrun (N > 1) every rank runs its own replica of the 64 shards on its own line ranges (weak scaling,
+no collective on the data path); timing is the max over ranks.
 """
 from __future__ import annotations
 
@@ -158,6 +162,11 @@ def reduce_over_ranks(maxes, sums, device):
     return a.tolist(), b.tolist()
 
 
+def workload_desc_cfg2(n_shards: int, lines: int, nbytes: int) -> str:
+    return (f"batched: {n_shards} shards, {lines:,} synthetic SMILES lines ({nbytes / 1e9:.2f} GB), line counts "
+            "log-uniform 1k-5M, per-shard mean length 25-70; one persistent launch per direction (CUDA graph)")
+
+
 def workload_desc(lines: int, nbytes: int) -> str:
     return (f"plain codec, large single stream: {lines:,} synthetic drug-like SMILES lines "
             f"({nbytes / 1e6:.1f} MB, mean {nbytes / max(1, lines):.1f} B/line incl. newline), one shard per launch")
@@ -196,20 +205,42 @@ def cpu_baseline(sample_lines: int, shape, threads: int | None = None, stream: s
             "random_access_s": round(tr, 3)}
 
 
+def cfg2_sample(sample_bytes: int):
+    """A bounded sample of the batched workload: the first lines of every shard, the same fraction of each,
+    about sample_bytes in all (one stream; lines are independent)."""
+    specs = synth.batched_shards()
+    total = sum(synth.lines_size(sh, 0, c) for sh, c in specs)
+    f = min(1.0, sample_bytes / max(1, total))
+    parts = [synth.generate(sh, 0, max(1, int(c * f))) for sh, c in specs]
+    return np.concatenate(parts), f
+
+
+def cpu_baseline_cfg2(sample_bytes: int, threads: int | None = None):
+    threads = threads or (os.cpu_count() or 1)
+    raw, f = cfg2_sample(sample_bytes)
+    tc, td, tr = oracle_round_trip(raw, threads)
+    total = tc + td + tr
+    return {"value": raw.size / total / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"the first {f * 100:.1f}% of the lines of each of the 64 shards ({raw.size / 1e6:.1f} MB); "
+                      f"compress + decompress line-partitioned over {threads} thread(s), then {RA_IDS:,}-id "
+                      "random access (single thread)",
+            "seconds": round(total, 3), "compress_s": round(tc, 3), "decompress_s": round(td, 3),
+            "random_access_s": round(tr, 3)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     threads = os.cpu_count() or 1
-    shape = synth.CFG1
-    # each step is a bounded sample of the workload, sized from a timed probe so that the warm-up and timed
-    # steps together take about REF_BUDGET_S of CPU work whatever --steps and --warmup are
-    probe = synth.generate(shape, 0, 100_000)
+    # each step is a bounded sample of the workload (the first lines of every shard), sized from a timed probe
+    # so that the warm-up and timed steps together take about REF_BUDGET_S of CPU work whatever --steps and
+    # --warmup are
+    probe, _ = cfg2_sample(5_000_000)
     t_probe = sum(oracle_round_trip(probe, threads))
-    lines_per_s = 100_000 / max(t_probe, 1e-6)
-    fit = int(lines_per_s * REF_BUDGET_S / max(1, args.steps + args.warmup))
-    sample = max(10_000, min(args.ref_sample_lines, fit))
-    raw = synth.generate(shape, 0, sample)
+    bytes_per_s = probe.size / max(t_probe, 1e-6)
+    fit = int(bytes_per_s * REF_BUDGET_S / max(1, args.steps + args.warmup))
+    raw, f = cfg2_sample(max(2_000_000, min(args.ref_sample_bytes, fit)))
     for _ in range(args.warmup):
         oracle_round_trip(raw, threads)
     times = []
@@ -218,14 +249,17 @@ def run_reference(args):
         times.append(tc + td + tr)
     t = float(np.mean(times))
     value = raw.size / t / 1e9
+    specs = synth.batched_shards()
+    total = sum(synth.lines_size(sh, 0, c) for sh, c in specs)
     line = {"impl": "reference", "metric": metric_name(), "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": workload_desc(args.lines, synth.lines_size(shape, 0, args.lines)),
+            "config": {"workload": workload_desc_cfg2(len(specs), sum(c for _, c in specs), total),
                        "step": "CPU oracle round trip (compress + decompress + random access) over a bounded "
                                "sample of the workload"},
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
-                             "sample": f"first {sample:,} lines ({raw.size / 1e6:.1f} MB) per step"},
+                             "sample": f"the first {f * 100:.2f}% of the lines of each of the 64 shards "
+                                       f"({raw.size / 1e6:.1f} MB) per step"},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -234,16 +268,16 @@ def run_reference(args):
 # GPU path
 # ---------------------------------------------------------------------------------------------------------
 
-def _aligned_shards(zs, specs, dev):
-    """Generates [(shape, count)] into one pinned buffer (each shard 16-byte aligned), copies it to the
-    device; returns (device slices, sizes, line counts)."""
+def _aligned_shards(zs, specs, dev, first_of=lambda c: 0):
+    """Generates [(shape, count)] (lines [first_of(count), + count) of each shard's stream) into one pinned
+    buffer, each shard 16-byte aligned, copies it to the device; returns (device slices, sizes, line counts)."""
     import torch
-    sizes = [synth.lines_size(sh, 0, c) for sh, c in specs]
+    sizes = [synth.lines_size(sh, first_of(c), c) for sh, c in specs]
     spans = [(n + 15) & ~15 for n in sizes]
     host = torch.empty(max(16, sum(spans)), dtype=torch.uint8, pin_memory=True)
     at = 0
     for (sh, c), n, sp in zip(specs, sizes, spans):
-        synth.generate_into(sh, 0, c, host.data_ptr() + at, n)
+        synth.generate_into(sh, first_of(c), c, host.data_ptr() + at, n)
         at += sp
     big = host.to(dev)
     ins, at = [], 0
@@ -264,109 +298,41 @@ def _time_ms(stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def bench_batched(zs, d, dev, reps: int, peak: float):
-    """64 shards (log-uniform 1k-5M lines, per-shard mean length 25-70) through one autotuned,
-    graph-captured plan, against one zs_compress / zs_decompress launch per shard, same buffers."""
-    import torch
-    specs = synth.batched_shards()
-    ins, sizes, counts = _aligned_shards(zs, specs, dev)
-    outs = [torch.empty(zs.zs_compress_bound(n), dtype=torch.uint8, device=dev) for n in sizes]
-    idxs = [torch.empty(c + 2, dtype=torch.int64, device=dev) for c in counts]
-    shards = list(zip(ins, outs, idxs))
-    stream = torch.cuda.current_stream(dev)
-    t0 = time.time()
-    plan = zs.Plan(d, zs.OP_COMPRESS, shards, flags=zs.PREPROCESS, variant=-1, tune_reps=2)
-    tune_s = time.time() - t0
-    res = plan.run()
-    for _ in range(2):
-        plan.run()
-    ms_b = _time_ms(stream, plan.run, reps)
-    kern_b = plan.last_ms
-    ref = [o[: r.out_len].clone() for o, r in zip(outs, res)]
-
-    def per_shard_c():
-        for x, o, i in shards:
-            zs.zs_compress(d, x, zs.PREPROCESS, o, i)
-    per_shard_c()
-    ms_p = _time_ms(stream, per_shard_c, reps)
-    same_c = all(torch.equal(o[: r.out_len], c) for o, r, c in zip(outs, res, ref))
-    del ref
-    comps = [o[: r.out_len] for o, r in zip(outs, res)]
-    douts = [torch.empty(d.decompress_bound(c.numel()) // 2 + n + 64, dtype=torch.uint8, device=dev)
-             for c, n in zip(comps, sizes)]
-    dsh = [(c, o, None) for c, o in zip(comps, douts)]
-    dplan = zs.Plan(d, zs.OP_DECOMPRESS, dsh, variant=-1, tune_reps=2)
-    dres = dplan.run()
-    ms_db = _time_ms(stream, dplan.run, reps)
-    kern_db = dplan.last_ms
-    dref = [o[: r.out_len].clone() for o, r in zip(douts, dres)]
-
-    def per_shard_d():
-        for c, o, _ in dsh:
-            zs.zs_decompress(d, c, o)
-    per_shard_d()
-    ms_dp = _time_ms(stream, per_shard_d, reps)
-    same_d = all(torch.equal(o[: r.out_len], x) for o, r, x in zip(douts, dres, dref))
-    nbytes, cbytes = sum(sizes), sum(c.numel() for c in comps)
-    # algorithmic bytes: compress reads the text and writes the stream and the index (n_lines + 1 entries a
-    # shard); decompress reads the stream and writes the text
-    c_alg = nbytes + cbytes + 8 * (sum(counts) + len(counts))
-    d_alg = cbytes + nbytes
-    out = {
-        "workload": f"{len(specs)} shards, {sum(counts):,} synthetic lines, {nbytes / 1e9:.2f} GB, line counts "
-                    "log-uniform 1k-5M, per-shard mean length 25-70",
-        "compress": {"batched_ms": ms_b, "batched_kernel_ms": kern_b, "per_shard_ms": ms_p,
-                     "speedup": ms_p / ms_b, "batched_gbps_in": nbytes / ms_b / 1e6,
-                     "per_shard_gbps_in": nbytes / ms_p / 1e6, "variant": zs.zs_kernel_variant_name(0, plan.variant),
-                     "tuned_ms": {zs.zs_kernel_variant_name(0, v): plan.tuned_ms(v)
-                                  for v in range(zs.zs_kernel_variants(0))},
-                     "autotune_s": tune_s, "identical_output": bool(same_c),
-                     "hbm_gbps": c_alg / kern_b / 1e6, "hbm_frac": c_alg / kern_b / 1e6 / peak,
-                     "hbm_frac_nominal": c_alg / kern_b / 1e6 / HBM_NOMINAL_GBS},
-        "decompress": {"batched_ms": ms_db, "per_shard_ms": ms_dp, "speedup": ms_dp / ms_db,
-                       "batched_gbps_in": cbytes / ms_db / 1e6, "per_shard_gbps_in": cbytes / ms_dp / 1e6,
-                       "variant": zs.zs_kernel_variant_name(1, dplan.variant),
-                       "tuned_ms": {zs.zs_kernel_variant_name(1, v): dplan.tuned_ms(v)
-                                    for v in range(zs.zs_kernel_variants(1))},
-                       "identical_output": bool(same_d), "batched_kernel_ms": kern_db,
-                       "hbm_gbps": d_alg / kern_db / 1e6, "hbm_frac": d_alg / kern_db / 1e6 / peak,
-                       "hbm_frac_nominal": d_alg / kern_db / 1e6 / HBM_NOMINAL_GBS},
-        "how": "batched = zs_plan_run of an autotuned plan replaying one CUDA graph (clear, one persistent "
-               "launch over all shards, result copy); per-shard = one zs_compress / zs_decompress call per shard; "
-               f"wall time per pass with CUDA events, mean of {reps} passes",
-    }
-    plan.close()
-    dplan.close()
-    return out
-
-
 def bench_serving(zs, d, dev, lines: int, n_req: int, rates):
     """Open-loop Poisson request streams (1-100,000 random ids per request, log-uniform) against a
-    resident store of `lines` lines: the continuous-batching server vs one launch per request."""
+    resident store of `lines` lines: the continuous-batching server vs one launch per request. The request
+    sizes and ids are drawn once; each rate scales the arrival times (Poisson arrivals at rate r are those at
+    rate 1 divided by r)."""
     import torch
     nbytes = synth.lines_size(synth.CFG4, 0, lines)
     host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     synth.generate_into(synth.CFG4, 0, lines, host.data_ptr(), nbytes)
     x = host.to(dev)
+    del host
     comp, idx, _ = zs.compress(d, x)
     comp, idx = comp.clone(), idx.clone()
     del x
+    base = synth.requests(n_req, 7, lines, rate=1.0)
+    nid = sum(len(i) for _, i in base)
     srv = zs.Server(d, comp, idx, arena_bytes=2 << 30, max_inflight=4)
     rows = []
     for rate in rates:
-        reqs = synth.requests(n_req, 7, lines, rate=float(rate))
-        nid = sum(len(i) for _, i in reqs)
+        reqs = [(t / float(rate), ids) for t, ids in base]
+        b0 = srv.stats()["batches"]
         lat, mk = srv.replay(reqs)
+        nb = srv.stats()["batches"] - b0
         lat2, mk2 = zs.zs_serial_replay(d, comp, idx, reqs)
         rows.append({"rate_req_s": rate, "requests": n_req, "ids": nid,
                      "server": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                                "lines_per_s": nid / mk},
+                                "lines_per_s": nid / mk, "launches": nb, "requests_per_launch": n_req / max(1, nb)},
                      "per_request": {"p50_ms": float(np.percentile(lat2, 50)),
                                      "p99_ms": float(np.percentile(lat2, 99)), "lines_per_s": nid / mk2}})
     st = srv.stats()
     srv.close()
     return {"workload": f"resident store of {lines:,} synthetic lines ({nbytes / 1e9:.2f} GB raw, "
-                        f"{comp.numel() / 1e9:.2f} GB compressed + {idx.numel() * 8 / 1e9:.2f} GB index)",
+                        f"{comp.numel() / 1e9:.2f} GB compressed + {idx.numel() * 8 / 1e9:.2f} GB index); "
+                        f"{n_req:,} requests per rate, 1-100,000 ids each (log-uniform), ids uniform without "
+                        "replacement",
             "rates": rows, "mean_requests_per_launch": st["mean_batch_requests"],
             "max_inflight": st["max_inflight"],
             "how": "zs_server_replay (continuous batching, 4 launches in flight, memory admission) vs "
@@ -381,6 +347,9 @@ ABLATION = [  # (dictionary file, what it varies), the paper's sweeps (Sec. V-C)
     ("zs_no_alphabet.zsd", "no pre-populated alphabet"),
     ("zs_raw_train.zsd", "trained on lines without ring-ID renumbering"),
     ("zs_outer_train.zsd", "trained on lines renumbered in opening order (the other reading of Sec. IV-A)"),
+    ("zs_printable.zsd", "every printable byte pre-populated (Table I 'Printable'; 95 learned patterns)"),
+    ("zs_printable_raw.zsd", "printable pre-population, trained on lines without ring-ID renumbering"),
+    ("zs_no_alphabet_raw.zsd", "no pre-populated alphabet, trained on lines without ring-ID renumbering"),
 ]
 
 
@@ -425,6 +394,73 @@ def run_ablation(args):
     print(json.dumps({"ablation": rows, "workload": workload_desc(lines, nbytes)}), flush=True)
 
 
+def _concat_host(specs, first_of):
+    """The shards' lines back to back in one pinned host buffer (lines are independent, so the shards'
+    concatenation is one valid stream whose coding is the shards' codings back to back)."""
+    import torch
+    sizes = [synth.lines_size(sh, first_of(c), c) for sh, c in specs]
+    host = torch.empty(max(1, sum(sizes)), dtype=torch.uint8, pin_memory=True)
+    at = 0
+    for (sh, c), n in zip(specs, sizes):
+        synth.generate_into(sh, first_of(c), c, host.data_ptr() + at, n)
+        at += n
+    return host[:at], sizes
+
+
+def bench_stream(zs, d, dev, shape, lines: int, peak: float, reps: int, first: int = 0, index: bool = True,
+                 line_index: bool = False):
+    """One stream through zs_compress and zs_decompress (one launch each): kernel times (median of reps, CUDA
+    events), GB/s, HBM fractions of the algorithmic bytes."""
+    import torch
+    nbytes = synth.lines_size(shape, first, lines)
+    host = np.empty(nbytes, dtype=np.uint8)
+    synth.generate_into(shape, first, lines, host.ctypes.data, nbytes)
+    x = torch.from_numpy(host).to(dev)
+    del host
+    comp = torch.empty(zs.zs_compress_bound(nbytes), dtype=torch.uint8, device=dev)
+    idx = torch.empty(lines + 2, dtype=torch.int64, device=dev) if index else None
+    kc, kd = [], []
+    for k in range(reps + 1):
+        r = zs.zs_compress(d, x, zs.PREPROCESS, comp, idx)
+        if k:
+            kc.append(zs.zs_last_kernel_ms())
+    assert r.n_lines == lines, (r.n_lines, lines)
+    c = comp[: r.out_len]
+    dec = torch.empty(nbytes + nbytes // 8 + 64, dtype=torch.uint8, device=dev)  # decoded <= input + %nn growth
+    for k in range(reps + 1):
+        rd = zs.zs_decompress(d, c, dec)
+        if k:
+            kd.append(zs.zs_last_kernel_ms())
+    assert rd.n_lines == lines
+    kc, kd = float(np.median(kc)), float(np.median(kd))
+    ca = nbytes + r.out_len + (8 * (lines + 1) if index else 0)
+    da = r.out_len + rd.out_len
+    out = {"lines": lines, "bytes": nbytes, "ratio": r.out_len / nbytes,
+           "compress": {"kernel_ms": kc, "gbps_in": nbytes / kc / 1e6, "lines_per_s": lines / (kc * 1e-3),
+                        "hbm_gbps": ca / kc / 1e6, "hbm_frac": ca / kc / 1e6 / peak,
+                        "algorithmic_bytes": ca},
+           "decompress": {"kernel_ms": kd, "gbps_in": r.out_len / kd / 1e6, "gbps_out": rd.out_len / kd / 1e6,
+                          "hbm_gbps": da / kd / 1e6, "hbm_frac": da / kd / 1e6 / peak, "algorithmic_bytes": da},
+           "decoded_bytes": rd.out_len}
+    if line_index and index:  # the index rebuilt from the compressed stream alone, against the compressor's
+        idx2 = torch.empty(lines + 2, dtype=torch.int64, device=dev)
+        li = []
+        for k in range(reps + 1):
+            n_li = zs.zs_build_line_index(c, idx2)
+            if k:
+                li.append(zs.zs_last_kernel_ms())
+        lk = float(np.median(li))
+        la = r.out_len + 8 * (lines + 1)
+        out["line_index"] = {"kernel_ms": lk, "gbps_in": r.out_len / lk / 1e6, "hbm_gbps": la / lk / 1e6,
+                             "hbm_frac": la / lk / 1e6 / peak,
+                             "identical_to_compress_index": bool(n_li == lines and torch.equal(idx2[: lines + 1],
+                                                                                                 idx[: lines + 1]))}
+        del idx2
+    del x, comp, idx, dec
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_2404_19391_gb300 import zsmiles as zs
@@ -438,41 +474,53 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
     zs.load_library()
     d = zs.Dictionary()
+    peak, peak_kind = hbm_peak()
+    stream = torch.cuda.current_stream(dev)
 
-    shape = synth.CFG1
-    lines = args.lines
-    first = rank_first_line(rank, lines)
-    nbytes = synth.lines_size(shape, first, lines)
-    host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-    synth.generate_into(shape, first, lines, host_in.data_ptr(), nbytes)
-    x = host_in.to(dev)
-
-    comp = torch.empty(zs.zs_compress_bound(nbytes), dtype=torch.uint8, device=dev)
-    idx = torch.empty(lines + 2, dtype=torch.int64, device=dev)
-    dec = torch.empty(d.decompress_bound(nbytes) // 2 + nbytes, dtype=torch.uint8, device=dev)
+    # ---- the workload: config 2, 64 shards in one batched plan each way. Rank r takes the lines
+    # [r * count, (r + 1) * count) of every shard's seeded stream (weak scaling, no collective) ----
+    specs = synth.batched_shards()
+    first_of = (lambda c: rank * c)
+    ins, sizes, counts = _aligned_shards(zs, specs, dev, first_of)
+    nbytes, nlines = sum(sizes), sum(counts)
+    outs = [torch.empty(zs.zs_compress_bound(n), dtype=torch.uint8, device=dev) for n in sizes]
+    idxs = [torch.empty(c + 2, dtype=torch.int64, device=dev) for c in counts]
+    shards = list(zip(ins, outs, idxs))
+    t0 = time.time()
+    plan_c = zs.Plan(d, zs.OP_COMPRESS, shards, flags=zs.PREPROCESS, variant=-1, tune_reps=2)
+    tune_c = time.time() - t0
+    res_c = plan_c.run()
+    assert [r.n_lines for r in res_c] == counts
+    comps = [o[: r.out_len] for o, r in zip(outs, res_c)]
+    cbytes = sum(r.out_len for r in res_c)
+    douts = [torch.empty(n + n // 8 + 64, dtype=torch.uint8, device=dev) for n in sizes]
+    dsh = [(c, o, None) for c, o in zip(comps, douts)]
+    t0 = time.time()
+    plan_d = zs.Plan(d, zs.OP_DECOMPRESS, dsh, variant=-1, tune_reps=2)
+    tune_d = time.time() - t0
+    res_d = plan_d.run()
+    dbytes = sum(r.out_len for r in res_d)
+    assert [r.n_lines for r in res_d] == counts
+    big = int(np.argmax(counts))  # random access reads the largest shard's stream and index
+    store, store_idx = comps[big], idxs[big][: counts[big] + 1]
     rng = np.random.default_rng(1000 + rank)
-    ids_host = torch.from_numpy(rng.integers(0, lines, size=RA_IDS).astype(np.int64)).pin_memory()
+    ids_host = torch.from_numpy(rng.integers(0, counts[big], size=RA_IDS).astype(np.int64)).pin_memory()
     ids = ids_host.to(dev)
     ra_out = torch.empty(RA_IDS * 256, dtype=torch.uint8, device=dev)
     ra_off = torch.empty(RA_IDS + 1, dtype=torch.int64, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
     kms = {"compress": [], "decompress": [], "lines": []}
-    sizes = {}
 
     def step(record=True):
-        r = zs.zs_compress(d, x, zs.PREPROCESS, comp, idx)
-        kc = zs.zs_last_kernel_ms()
-        c = comp[: r.out_len]
-        rd = zs.zs_decompress(d, c, dec)
-        kd = zs.zs_last_kernel_ms()
-        rl = zs.zs_decompress_lines(d, c, idx[: r.n_lines + 1], ids, ra_out, ra_off)
+        plan_c.run()
+        kc = plan_c.last_ms
+        plan_d.run()
+        kd = plan_d.last_ms
+        zs.zs_decompress_lines(d, store, store_idx, ids, ra_out, ra_off)
         kl = zs.zs_last_kernel_ms()
         if record:
             kms["compress"].append(kc)
             kms["decompress"].append(kd)
             kms["lines"].append(kl)
-        sizes.update(comp=r.out_len, n_lines=r.n_lines, dec=rd.out_len, ra=rl.out_len)
 
     def barrier():
         if world > 1:
@@ -481,8 +529,6 @@ def run_gpu(args):
 
     for _ in range(max(3, args.warmup)):
         step(record=False)
-    assert sizes["n_lines"] == lines and sizes["dec"] >= nbytes * 0.9
-
     visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
     smi_index = int(visible[local]) if len(visible) > local and visible[local].strip().isdigit() else local
     clocks = ClockSampler(smi_index)
@@ -502,28 +548,16 @@ def run_gpu(args):
     barrier()
     ms_total = e0.elapsed_time(e1)
 
-    # ---- end to end through the host-buffer API: every step compresses the pinned host input into pinned host
-    # buffers (zs_compress_host: copies in, kernels and copies out overlapped chunk by chunk), decompresses that
-    # host result (zs_decompress_host), and answers the 100,000-id request from host ids into host memory
-    # against the device-resident store (ids H2D, zs_decompress_lines, lines and offsets D2H) ----
-    host_comp = torch.empty(comp.numel(), dtype=torch.uint8, pin_memory=True)
-    host_idx = torch.empty(idx.numel(), dtype=torch.int64, pin_memory=True)
-    host_dec = torch.empty(dec.numel(), dtype=torch.uint8, pin_memory=True)
+    # ---- end to end through the host-buffer API: the 64 shards back to back in pinned host memory (one
+    # stream), zs_compress_host to pinned host stream + index, zs_decompress_host of that to pinned host
+    # text, and the 100,000-id request from host ids into host memory against the device-resident store ----
+    host_in, _ = _concat_host(specs, first_of)
+    host_comp = torch.empty(cbytes + 64, dtype=torch.uint8, pin_memory=True)
+    host_idx = torch.empty(nlines + 2, dtype=torch.int64, pin_memory=True)
+    host_dec = torch.empty(dbytes + 64, dtype=torch.uint8, pin_memory=True)
     host_ra = torch.empty(ra_out.numel(), dtype=torch.uint8, pin_memory=True)
     host_off = torch.empty(ra_off.numel(), dtype=torch.int64, pin_memory=True)
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
-    r0 = zs.zs_compress(d, x, zs.PREPROCESS, comp, idx)  # the resident store random access reads
-    store, store_idx = comp[: r0.out_len], idx[: r0.n_lines + 1]
-    # ---- the line index rebuilt from the compressed stream alone (zs_build_line_index), checked against the
-    # index the compressor wrote; outside the timed step ----
-    idx2 = torch.empty(idx.numel(), dtype=torch.int64, device=dev)
-    li_ms = []
-    for k in range(6):
-        n_li = zs.zs_build_line_index(store, idx2)
-        if k:
-            li_ms.append(zs.zs_last_kernel_ms())
-    li_same = n_li == r0.n_lines and torch.equal(idx2[: n_li + 1], store_idx)
-    del idx2
     io = {}
 
     def e2e_step():
@@ -534,8 +568,9 @@ def run_gpu(args):
         host_ra[: rl.out_len].copy_(ra_out[: rl.out_len], non_blocking=True)
         host_off.copy_(ra_off, non_blocking=True)
         torch.cuda.synchronize(dev)
-        io.update(h2d=nbytes + r.out_len + ids_host.numel() * 8,
-                  d2h=r.out_len + (r.n_lines + 1) * 8 + rd.out_len + rl.out_len + ra_off.numel() * 8)
+        io.update(h2d=host_in.numel() + r.out_len + ids_host.numel() * 8,
+                  d2h=r.out_len + (r.n_lines + 1) * 8 + rd.out_len + rl.out_len + ra_off.numel() * 8,
+                  same=(r.out_len == cbytes and r.n_lines == nlines and rd.out_len == dbytes))
 
     e2e_step()
     torch.cuda.synchronize(dev)
@@ -547,68 +582,138 @@ def run_gpu(args):
     e2e_ms = (time.perf_counter() - w0) * 1e3 / e2e_steps
     barrier()
     clocks.stop()
-    h2d, d2h = io["h2d"], io["d2h"]
+    del host_in, host_comp, host_idx, host_dec
 
     (ms_step, e2e_ms), (total_bytes,) = reduce_over_ranks([ms_total / args.steps, e2e_ms], [nbytes], dev)
-
     value = total_bytes / (ms_step * 1e-3) / 1e9
-    peak, peak_kind = hbm_peak()
     kc = float(np.mean(kms["compress"]))
     kd = float(np.mean(kms["decompress"]))
     kl = float(np.mean(kms["lines"]))
-    li_k = float(np.median(li_ms))
-    li_alg = sizes["comp"] + 8 * (sizes["n_lines"] + 1)  # read the stream, write n_lines + 1 offsets
-    comp_bytes = nbytes + sizes["comp"] + 8 * (sizes["n_lines"] + 1)   # read input, write output + index
-    dec_bytes = sizes["comp"] + sizes["dec"]                            # read compressed, write decoded
-    achieved_c = comp_bytes / (kc * 1e-3) / 1e9
-    achieved_d = dec_bytes / (kd * 1e-3) / 1e9
-    traffic = kernel_traffic("compress_warp_kernel")
+    c_alg = nbytes + cbytes + 8 * (nlines + len(counts))  # read the text, write the streams and the indexes
+    d_alg = cbytes + dbytes                                # read the streams, write the text
+    achieved_c, achieved_d = c_alg / kc / 1e6, d_alg / kd / 1e6
+    cvar = zs.zs_kernel_variant_name(zs.OP_COMPRESS, plan_c.variant)
+    dvar = zs.zs_kernel_variant_name(zs.OP_DECOMPRESS, plan_d.variant)
+    ckernel = "compress_span_kernel" if "span" in cvar else "compress_warp_kernel"
+    traffic = kernel_traffic(ckernel)
+    if traffic is not None:
+        traffic *= nbytes  # the committed figure is per input byte
 
     if rank == 0:
+        # ---- the same shards one launch per shard (zs_compress / zs_decompress per shard, as a caller without
+        # the batched form would), identical output; wall time and the shards' kernel times summed ----
+        ref_c = [o[: r.out_len].clone() for o, r in zip(outs, res_c)]
+        ref_d = [o[: r.out_len].clone() for o, r in zip(douts, res_d)]
+
+        def per_shard(op):
+            ks = []
+            for (x, o, i), c, dd in zip(shards, comps, douts):
+                if op == "c":
+                    zs.zs_compress(d, x, zs.PREPROCESS, o, i)
+                else:
+                    zs.zs_decompress(d, c, dd)
+                ks.append(zs.zs_last_kernel_ms())
+            return sum(ks)
+
+        per = {}
+        for op in ("c", "d"):
+            per_shard(op)
+            ks = []
+            w0 = torch.cuda.Event(enable_timing=True)
+            w1 = torch.cuda.Event(enable_timing=True)
+            w0.record(stream)
+            for _ in range(3):
+                ks.append(per_shard(op))
+            w1.record(stream)
+            torch.cuda.synchronize(dev)
+            per[op] = (w0.elapsed_time(w1) / 3, float(np.mean(ks)))
+        same_c = all(torch.equal(o[: r.out_len], c) for o, r, c in zip(outs, res_c, ref_c))
+        same_d = all(torch.equal(o[: r.out_len], c) for o, r, c in zip(douts, res_d, ref_d))
+        del ref_c, ref_d
+        batched = {
+            "compress": {"batched_kernel_ms": kc, "batched_step_ms": None, "per_shard_wall_ms": per["c"][0],
+                         "per_shard_kernel_ms_sum": per["c"][1], "speedup_wall": per["c"][0] / kc,
+                         "speedup_kernel": per["c"][1] / kc, "identical_output": bool(same_c),
+                         "variant": cvar, "autotune_s": tune_c,
+                         "tuned_ms": {zs.zs_kernel_variant_name(0, v): plan_c.tuned_ms(v)
+                                      for v in range(zs.zs_kernel_variants(0))}},
+            "decompress": {"batched_kernel_ms": kd, "per_shard_wall_ms": per["d"][0],
+                           "per_shard_kernel_ms_sum": per["d"][1], "speedup_wall": per["d"][0] / kd,
+                           "speedup_kernel": per["d"][1] / kd, "identical_output": bool(same_d),
+                           "variant": dvar, "autotune_s": tune_d,
+                           "tuned_ms": {zs.zs_kernel_variant_name(1, v): plan_d.tuned_ms(v)
+                                        for v in range(zs.zs_kernel_variants(1))}},
+            "how": "batched = zs_plan_run of an autotuned plan replaying one CUDA graph (clear, one persistent "
+                   "launch over all shards, result copy), kernel time from events captured around the launch; "
+                   "per shard = one zs_compress / zs_decompress call per shard (wall, mean of 3 passes; and the "
+                   "shards' own kernel times summed)"}
+    plan_c.close()
+    plan_d.close()
+    del ins, outs, idxs, shards, comps, douts, dsh, ra_out, store, store_idx
+    torch.cuda.empty_cache()
+
+    if rank == 0:
+        # ---- the other configurations: config 1 (one 10M-line stream, one launch each way, plus the line index
+        # rebuilt from its compressed stream) and config 3 (the long-tail mix at its full 100M lines) ----
+        cfg1 = bench_stream(zs, d, dev, synth.CFG1, args.lines, peak, reps=5, line_index=True)
+        cfg1["workload"] = workload_desc(args.lines, cfg1["bytes"])
+        cfg3 = None
+        if args.cfg3_lines > 0:
+            cfg3 = bench_stream(zs, d, dev, synth.CFG3, args.cfg3_lines, peak, reps=3)
+            cfg3["workload"] = (f"batched long tail: {args.cfg3_lines:,} synthetic lines ({cfg3['bytes'] / 1e9:.2f} "
+                                "GB), 90% drug-like, 10% of 150-400 chars with bracket atoms, stereo bonds and "
+                                "%nn ring labels; one stream, one launch each way")
         line = {
             "metric": metric_name(), "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": workload_desc(lines, nbytes), "lines_per_rank": lines,
-                       "bytes_per_rank": nbytes, "dictionary": "frozen default (Algorithm 1, seed-1 100k-line "
-                                                               "training set, L_max 8, T 146)",
+            "config": {"workload": workload_desc_cfg2(len(specs), nlines, nbytes), "shards": len(specs),
+                       "lines_per_rank": nlines, "bytes_per_rank": nbytes,
+                       "dictionary": "frozen default (Algorithm 1, seed-1 100k-line training set, L_max 8, T 146)",
                        "dictionary_sha256": hashlib.sha256(open(zs.DEFAULT_DICTIONARY, "rb").read()).hexdigest(),
-                       "step": f"zs_compress + zs_decompress + zs_decompress_lines({RA_IDS:,} random ids)",
+                       "step": "zs_plan_run of the compression plan (64 shards, one launch) + zs_plan_run of the "
+                               f"decompression plan + zs_decompress_lines({RA_IDS:,} random ids of the largest shard)",
+                       "value": "uncompressed bytes of the 64 shards per second of step",
                        "l2": "inputs (and outputs) larger than the 129 MB L2; no flush",
                        "parallelism": f"{world} independent replica(s)"},
             "clocks": clocks.summary(),
-            "e2e": {"value": total_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                    "how": "wall clock per step of zs_compress_host (pinned host input to pinned host stream and "
-                           "index) + zs_decompress_host (that host stream to pinned host text) + 100,000 random "
-                           "ids H2D, zs_decompress_lines on the device-resident store, lines and offsets D2H"},
+            "compress_gbps_in": nbytes / kc / 1e6, "compress_hbm_frac": achieved_c / peak,
+            "decompress_gbps_in": cbytes / kd / 1e6, "decompress_hbm_frac": achieved_d / peak,
+            "random_access_p99_ms": float(np.percentile(kms["lines"], 99)),
+            "e2e": {"value": total_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": io["h2d"],
+                    "d2h_bytes_per_step": io["d2h"], "ms_per_step": e2e_ms, "same_sizes_as_device_step": io["same"],
+                    "how": "wall clock per step of zs_compress_host (the 64 shards back to back in pinned host "
+                           "memory, to a pinned host stream and index) + zs_decompress_host (that stream to pinned "
+                           f"host text) + {RA_IDS:,} random ids H2D, zs_decompress_lines on the device-resident "
+                           "largest shard, lines and offsets D2H"},
             "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved_c, "peak": peak, "unit": "GB/s",
-                         "frac": achieved_c / peak, "traffic": traffic, "kernel": "compress_warp_kernel",
+                         "frac": achieved_c / peak, "traffic": traffic, "kernel": ckernel,
                          "peak_kind": f"{peak_kind} (copy, MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6.8 TB/s",
-                         "algorithmic_bytes_per_launch": comp_bytes, "kernel_ms": kc},
-            "compress": {"kernel_ms": kc, "gbps_in": nbytes / (kc * 1e-3) / 1e9,
-                         "lines_per_s": lines / (kc * 1e-3), "hbm_gbps": achieved_c, "hbm_frac": achieved_c / peak,
-                         "hbm_frac_nominal": achieved_c / HBM_NOMINAL_GBS, "ratio": sizes["comp"] / nbytes},
-            "decompress": {"kernel_ms": kd, "gbps_in": sizes["comp"] / (kd * 1e-3) / 1e9,
-                           "gbps_out": sizes["dec"] / (kd * 1e-3) / 1e9, "hbm_gbps": achieved_d,
-                           "hbm_frac": achieved_d / peak, "hbm_frac_nominal": achieved_d / HBM_NOMINAL_GBS},
-            "line_index": {"kernel_ms": li_k, "gbps_in": sizes["comp"] / (li_k * 1e-3) / 1e9,
-                           "hbm_gbps": li_alg / (li_k * 1e-3) / 1e9, "hbm_frac": li_alg / (li_k * 1e-3) / 1e9 / peak,
-                           "identical_to_compress_index": bool(li_same)},
+                         "algorithmic_bytes_per_launch": c_alg, "kernel_ms": kc},
+            "compress": {"kernel_ms": kc, "gbps_in": nbytes / kc / 1e6, "lines_per_s": nlines / (kc * 1e-3),
+                         "hbm_gbps": achieved_c, "hbm_frac": achieved_c / peak,
+                         "hbm_frac_nominal": achieved_c / HBM_NOMINAL_GBS, "ratio": cbytes / nbytes,
+                         "algorithmic_bytes": c_alg, "variant": cvar},
+            "decompress": {"kernel_ms": kd, "gbps_in": cbytes / kd / 1e6, "gbps_out": dbytes / kd / 1e6,
+                           "hbm_gbps": achieved_d, "hbm_frac": achieved_d / peak,
+                           "hbm_frac_nominal": achieved_d / HBM_NOMINAL_GBS, "algorithmic_bytes": d_alg,
+                           "variant": dvar},
             "random_access": {"ids": RA_IDS, "kernel_ms": kl, "lines_per_s": RA_IDS / (kl * 1e-3),
                               "p50_ms": float(np.percentile(kms["lines"], 50)),
                               "p99_ms": float(np.percentile(kms["lines"], 99))},
+            "batched": batched,
+            "config1": cfg1,
         }
-        if world == 1 and not args.no_batched:
-            line["batched"] = bench_batched(zs, d, dev, reps=5, peak=peak)
+        if cfg3 is not None:
+            line["config3"] = cfg3
         if world == 1 and not args.no_serving:
             line["serving"] = bench_serving(zs, d, dev, args.serve_lines, args.serve_requests,
                                             [int(r) for r in args.serve_rates.split(",")])
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_sample_lines, shape)
+            line["cpu_baseline"] = cpu_baseline_cfg2(args.cpu_sample_bytes)
             line["cpu_oracle_cfg0"] = {t: cpu_baseline(synth.CFG0_LINES, synth.CFG0, threads=n,
                                                        stream="the 10,000-line config-0 stream")
                                        for t, n in (("single_thread", 1), ("all_threads", None))}
@@ -624,16 +729,19 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--lines", type=int, default=synth.CFG1_LINES)
+    ap.add_argument("--lines", type=int, default=synth.CFG1_LINES, help="lines of the config-1 stream")
+    ap.add_argument("--cfg3-lines", type=int, default=synth.CFG3_LINES,
+                    help="lines of the config-3 long-tail stream (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=40)
-    ap.add_argument("--cpu-sample-lines", type=int, default=synth.CFG1_LINES)
-    ap.add_argument("--ref-sample-lines", type=int, default=400_000)
+    ap.add_argument("--cpu-sample-bytes", type=int, default=1_000_000_000,
+                    help="bytes of the batched workload the CPU oracle codes for the cpu_baseline key")
+    ap.add_argument("--ref-sample-bytes", type=int, default=20_000_000,
+                    help="largest per-step sample of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 64-shard batched-form comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form request replay")
     ap.add_argument("--serve-lines", type=int, default=synth.CFG4_LINES)
-    ap.add_argument("--serve-requests", type=int, default=300)
-    ap.add_argument("--serve-rates", default="1000,10000,100000")
+    ap.add_argument("--serve-requests", type=int, default=20_000)
+    ap.add_argument("--serve-rates", default="1000,3000,10000,30000,100000")
     ap.add_argument("--ablation", action="store_true",
                     help="instead of the benchmark line: ratio and kernel times of the ablation dictionaries")
     args = ap.parse_args()

@@ -18,6 +18,15 @@ and one varies the reading of Sec. IV-A: the training lines are pre-processed wi
 opening order (the outermost of a nest gets the lower ID):
 
     python -m oracle.make_dictionary --outer --out paper_2404_19391_gb300/data/zs_outer_train.zsd
+
+Table I's pre-population rows are {printable ASCII, SMILES alphabet, none}, each with and without
+pre-processing. The printable pre-population takes every printable byte 0x21-0x7E as a single-character entry,
+which leaves 0xA1-0xFF (95 symbols) for learned patterns:
+
+    python -m oracle.make_dictionary --printable --out paper_2404_19391_gb300/data/zs_printable.zsd
+    python -m oracle.make_dictionary --printable --no-preprocess --out paper_2404_19391_gb300/data/zs_printable_raw.zsd
+    python -m oracle.make_dictionary --no-alphabet --no-preprocess \
+        --out paper_2404_19391_gb300/data/zs_no_alphabet_raw.zsd
 """
 from __future__ import annotations
 
@@ -50,9 +59,15 @@ def main() -> None:
     ap.add_argument("--no-alphabet", action="store_true", help="no pre-populated SMILES alphabet (Sec. IV-B)")
     ap.add_argument("--no-preprocess", action="store_true", help="train on lines without ring-ID renumbering")
     ap.add_argument("--outer", action="store_true", help="renumber ring IDs in opening order (outermost lower)")
+    ap.add_argument("--printable", action="store_true",
+                    help="pre-populate every printable byte (Table I 'Printable'); T is cut to the 95 free symbols")
     args = ap.parse_args()
-    text = build_default(lmax=args.lmax, T=args.T, alphabet=b"" if args.no_alphabet else dictgen.SMILES_ALPHABET,
-                         preprocess=not args.no_preprocess, outer=args.outer)
+    if args.printable and args.no_alphabet:
+        ap.error("--printable and --no-alphabet exclude each other")
+    alphabet = b"" if args.no_alphabet else (dictgen.PRINTABLE_ALPHABET if args.printable else dictgen.SMILES_ALPHABET)
+    T = min(args.T, len(dictgen.code_space(alphabet)))
+    text = build_default(lmax=args.lmax, T=T, alphabet=alphabet, preprocess=not args.no_preprocess,
+                         outer=args.outer)
     with open(args.out, "wb") as f:
         f.write(text)
     print(args.out, len(text), hashlib.sha256(text).hexdigest())

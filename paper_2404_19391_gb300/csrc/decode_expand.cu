@@ -23,11 +23,16 @@
 namespace zs {
 namespace {
 
-template <int W, int TB, int OUTB>
+template <int W, int TB, int OUTB, int SLOTS, bool ORW>
 struct DxGeom {
-    static constexpr int kWarps = W;  // warps per CTA (one CTA per SM)
-    static constexpr int kTile = TB;  // compressed bytes per warp tile
-    static constexpr int kOut = OUTB; // staged output bytes per tile
+    static constexpr int kWarps = W;    // warps per CTA (one CTA per SM)
+    static constexpr int kTile = TB;    // compressed bytes per warp tile
+    static constexpr int kOut = OUTB;   // staged output bytes per tile
+    static constexpr int kSlots = SLOTS;  // 2: a tile's look-back and copy-out wait until the next tile is
+                                          // expanded (software pipeline); 1: they follow at once
+    static constexpr bool kOr = ORW;    // patterns land by shared-memory atomic OR into a cleared stage, each at
+                                        // its own offset (no chain from one pattern to the next); else by
+                                        // a funnel of aligned word stores
 };
 
 constexpr unsigned kAllX = 0xffffffffu;
@@ -65,7 +70,7 @@ struct DX {
 
     struct alignas(16) WarpMem {
         uint8_t in[16 + kTB + 16];  // the 16 bytes before the tile, the tile
-        OutSlot os[2];
+        OutSlot os[Geo::kSlots];
         uint64_t bar;
     };
 
@@ -186,6 +191,30 @@ struct DX {
         }
     }
 
+    // The byte loop of a slow chunk writing by atomic OR into the cleared stage (lanes share boundary words).
+    static __device__ __forceinline__ void slow_or(const Ctx &C, uint32_t p0, uint32_t p1, bool lit, uint32_t pos,
+                                                   uint8_t *stg)
+    {
+        const uint8_t *in = C.M->in + 16;
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(stg);
+        auto put = [&](uint32_t w, uint8_t v) { atomicOr(w32 + (w >> 2), (uint32_t)v << (8 * (w & 3u))); };
+        for (uint32_t p = p0; p < p1; ++p) {
+            const uint8_t b = in[p];
+            if (!lit && b == kEsc) {
+                lit = true;
+                continue;
+            }
+            if (lit || b == kNl) {
+                lit = false;
+                put(pos++, b);
+                continue;
+            }
+            const uint32_t l = C.plen[b];
+            for (uint32_t k = 0; k < l; ++k) put(pos + k, C.pat[16u * b + k]);
+            pos += l;
+        }
+    }
+
     // One round's lanes: the chunk of lane `lane`, its 16 entries (fast path) or the byte-loop sizes.
     struct Chunk {
         uint32_t lo[16], hi[16];
@@ -235,34 +264,74 @@ struct DX {
         }
     }
 
-    // Funnel of a fast chunk's patterns into aligned words of the stage from byte offset pos; returns the
-    // pending partial word (bytes [*wpos, *wpos + *n)) for the second phase. first: pos is where this
-    // round begins, so the stage's word there already holds the previous round's bytes below pos.
-    static __device__ __forceinline__ uint32_t funnel(const Chunk &K, uint8_t *stg, uint32_t pos, bool first,
-                                                      uint32_t *wpos_out, uint32_t *n_out)
+    // Funnel of patterns [k0, k0 + 8) of a fast chunk into aligned words of the stage from byte offset pos:
+    // the chunk's two halves are two independent chains, interleaved. A chain's first word may start below
+    // its first byte: those bytes (of the chain or lane before) are written as zeros here, or taken from the
+    // stage when `first` (the round's first byte: the previous round's bytes are already there). Each chain's
+    // last partial word is left in *a, *wpos, *n for the second phase.
+    struct Funnel {
+        uint32_t a, wpos, n, p0;
+    };
+
+    static __device__ __forceinline__ void funnel2(const Chunk &K, uint8_t *stg, uint32_t pos, bool first,
+                                                   Funnel &F0, Funnel &F1)
     {
-        uint32_t wpos = pos & ~3u, n = pos & 3u;
-        uint32_t a = 0;
-        if (first && n) a = *reinterpret_cast<const uint32_t *>(stg + wpos) & ((1u << (8 * n)) - 1u);
+        uint32_t half = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) half += (K.hi[k] >> 24) & 7u;
+        F0.p0 = pos;
+        F1.p0 = pos + half;
+        F0.wpos = pos & ~3u;
+        F0.n = pos & 3u;
+        F1.wpos = F1.p0 & ~3u;
+        F1.n = F1.p0 & 3u;
+        F0.a = (first && F0.n) ? *reinterpret_cast<const uint32_t *>(stg + F0.wpos) & ((1u << (8 * F0.n)) - 1u) : 0u;
+        F1.a = 0;
+        auto push = [&](Funnel &F, uint32_t lo, uint32_t hi) {
+            const uint32_t len = (hi >> 24) & 7u;
+            const uint32_t h = hi & 0x00FFFFFFu;
+            const uint32_t sh = 8u * F.n;
+            const uint32_t w0 = F.a | (lo << sh);
+            const uint32_t w1 = __funnelshift_l(lo, h, sh);
+            const uint32_t w2 = __funnelshift_l(h, 0u, sh);
+            const uint32_t tot = F.n + len;
+            if (tot >= 4) *reinterpret_cast<uint32_t *>(stg + F.wpos) = w0;
+            if (tot >= 8) *reinterpret_cast<uint32_t *>(stg + F.wpos + 4) = w1;
+            F.a = tot >= 8 ? w2 : (tot >= 4 ? w1 : w0);
+            F.n = tot & 3u;
+            F.wpos += tot & ~3u;
+        };
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            push(F0, K.lo[k], K.hi[k]);
+            push(F1, K.lo[8 + k], K.hi[8 + k]);
+        }
+    }
+
+    // Each pattern of a fast chunk ORed into the (cleared) stage at its own offset: the offsets are a prefix of
+    // the lengths, so the 16 patterns are independent; a pattern's up to 7 bytes touch at most three words.
+    static __device__ __forceinline__ void or_patterns(const Chunk &K, uint8_t *stg, uint32_t pos)
+    {
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(stg);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const uint32_t l = K.hi[k] >> 24;  // no flag on a fast chunk: the length (no newline bit: below)
-            const uint32_t len = l & 7u;
+            const uint32_t len = (K.hi[k] >> 24) & 7u;
             const uint32_t h = K.hi[k] & 0x00FFFFFFu;
-            const uint32_t sh = 8u * n;
-            const uint32_t w0 = a | (K.lo[k] << sh);
-            const uint32_t w1 = __funnelshift_l(K.lo[k], h, sh);
-            const uint32_t w2 = __funnelshift_l(h, 0u, sh);
-            const uint32_t tot = n + len;
-            if (tot >= 4) *reinterpret_cast<uint32_t *>(stg + wpos) = w0;
-            if (tot >= 8) *reinterpret_cast<uint32_t *>(stg + wpos + 4) = w1;
-            a = tot >= 8 ? w2 : (tot >= 4 ? w1 : w0);
-            n = tot & 3u;
-            wpos += tot & ~3u;
+            const uint32_t sh = 8u * (pos & 3u);
+            uint32_t *q = w32 + (pos >> 2);
+            atomicOr(q, K.lo[k] << sh);
+            const uint32_t end = (pos & 3u) + len;  // bytes from the first word's start
+            if (end > 4) atomicOr(q + 1, __funnelshift_l(K.lo[k], h, sh));
+            if (end > 8) atomicOr(q + 2, __funnelshift_l(h, 0u, sh));
+            pos += len;
         }
-        *wpos_out = wpos;
-        *n_out = n;
-        return a;
+    }
+
+    // Second phase: a chain's last partial word, byte by byte, never below the chain's first byte.
+    static __device__ __forceinline__ void funnel_tail(uint8_t *stg, const Funnel &F)
+    {
+        const uint32_t j0 = F.wpos == (F.p0 & ~3u) ? (F.p0 & 3u) : 0u;
+        for (uint32_t j = j0; j < F.n; ++j) stg[F.wpos + j] = (uint8_t)(F.a >> (8 * j));
     }
 
     // Sizes of one round, warp scan; returns the round's total; *pos = the lane's output offset in the round.
@@ -282,6 +351,11 @@ struct DX {
         uint8_t *stg = O.out;
         uint32_t run = 0, nls = 0;
         bool fits = true;
+        if (Geo::kOr) {  // patterns are ORed in: the stage starts at zero
+            uint4 *s16 = reinterpret_cast<uint4 *>(stg);
+            for (uint32_t j = C.lane; j < (uint32_t)(kOutB + 32) / 16; j += 32) s16[j] = make_uint4(0, 0, 0, 0);
+            __syncwarp();
+        }
         for (int r = 0; r < kRounds; ++r) {
             if ((uint32_t)r * 512u >= nown) break;
             Chunk K;
@@ -290,14 +364,17 @@ struct DX {
             const uint32_t rt = place(C, K, &pos);
             nls += K.nls;
             if (fits && run + rt + 32u > (uint32_t)kOutB) fits = false;
-            if (fits) {
-                uint32_t wpos = 0, n = 0, a = 0;
-                if (K.fast) a = funnel(K, stg, run + pos, pos == 0, &wpos, &n);
+            if (fits && Geo::kOr) {
+                if (K.fast) or_patterns(K, stg, run + pos);
+                else if (K.p1 > K.p0) slow_or(C, K.p0, K.p1, K.lit, run + pos, stg);
                 __syncwarp();
-                if (K.fast) {  // the pending partial word, byte by byte, never below the lane's first byte
-                    const uint32_t p0 = run + pos;
-                    const uint32_t j0 = wpos == (p0 & ~3u) ? (p0 & 3u) : 0u;
-                    for (uint32_t j = j0; j < n; ++j) stg[wpos + j] = (uint8_t)(a >> (8 * j));
+            } else if (fits) {
+                Funnel F0, F1;
+                if (K.fast) funnel2(K, stg, run + pos, pos == 0, F0, F1);
+                __syncwarp();
+                if (K.fast) {  // the chains' pending partial words
+                    funnel_tail(stg, F0);
+                    funnel_tail(stg, F1);
                 } else if (K.p1 > K.p0) {
                     slow_write<true>(C, K.p0, K.p1, K.lit, run + pos, stg, 0);
                 }
@@ -436,6 +513,10 @@ struct DX {
                 finish_staged(Cp, M.os[s ^ 1u]);
                 pending = false;
             }
+            if (Geo::kSlots == 1 && fits) {  // no pipeline: finish this tile now
+                finish_staged(Cs, O);
+                continue;
+            }
             if (!fits) {  // look back first, then write straight to memory
                 uint64_t ea = 0, eb = 0;
                 if (t > 0) lookback_warp(O.sv.tiles, t, &ea, &eb, P->limit_ns, C.status);
@@ -447,6 +528,7 @@ struct DX {
                 pending = true;
                 s ^= 1u;
             }
+            if (Geo::kSlots == 1) s = 0;
         }
         if (pending) {
             Ctx Cp = C;
@@ -462,12 +544,15 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) decompress_expand_kernel(
     DX<Geo>::run(&P);
 }
 
-// Compiled geometries: 2048-byte tiles (four rounds) with a stage of 2.25 x the tile, 16 warps per SM beside
-// the 36 KB of tables; and 1024-byte tiles (2.5 x) with 24 warps.
-using DxV0 = DxGeom<16, 2048, 4608>;
-using DxV1 = DxGeom<24, 1024, 2560>;
-static_assert(16 * sizeof(DX<DxV0>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "shared memory");
-static_assert(24 * sizeof(DX<DxV1>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "shared memory");
+// Compiled geometries, all with 2048-byte tiles (four rounds) and stages of 2.25 x the tile beside the 36 KB of
+// tables: one stage and 24 warps per SM (more warps to hide latency, the look-back not pipelined), patterns
+// ORed in or funnelled; and two stages (pipelined look-back) with 16 warps, ORed in.
+using DxV0 = DxGeom<24, 2048, 4608, 1, true>;
+using DxV1 = DxGeom<24, 2048, 4608, 1, false>;
+using DxV2 = DxGeom<16, 2048, 4608, 2, true>;
+static_assert(DxV0::kWarps * sizeof(DX<DxV0>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
+static_assert(DxV1::kWarps * sizeof(DX<DxV1>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
+static_assert(DxV2::kWarps * sizeof(DX<DxV2>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
 
 template <class Geo>
 size_t dx_smem()
@@ -518,8 +603,9 @@ constexpr DxEntry dx_entry(const char *name)
 }
 
 const DxEntry kDx[] = {
-    dx_entry<DxV0>("decompress expand w16 t2048"),
-    dx_entry<DxV1>("decompress expand w24 t1024"),
+    dx_entry<DxV0>("decompress expand w24 t2048 or"),
+    dx_entry<DxV1>("decompress expand w24 t2048 funnel"),
+    dx_entry<DxV2>("decompress expand w16 t2048 or 2-stage"),
 };
 constexpr int kNumDx = (int)(sizeof(kDx) / sizeof(kDx[0]));
 

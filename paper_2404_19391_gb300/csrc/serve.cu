@@ -110,18 +110,22 @@ struct Batch {
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    uint64_t *h_ids = nullptr, *d_ids = nullptr, *h_off = nullptr, *d_off = nullptr;
+    // h_ids, h_off and h_res are pinned and mapped: the kernels read the ids and write the offsets and the
+    // result record through their device addresses (d_ids, h_off_dev, h_res_dev), with no copy calls
+    uint64_t *h_ids = nullptr, *d_ids = nullptr, *h_off = nullptr, *h_off_dev = nullptr, *d_off = nullptr;
     void *d_scratch = nullptr;
-    zs::DevResult *h_res = nullptr;
+    zs::DevResult *h_res = nullptr, *h_res_dev = nullptr;
     int state = 0;  // 0 free, 1 batch in flight
     std::shared_ptr<Batch> batch;
     size_t K = 0;
 };
 
 // Copies the r->out_len decoded bytes of a batch from the device arena to the mapped host arena (both
-// regions 256-byte aligned): 16-byte loads and stores, grid-stride.
+// regions 256-byte aligned) with 16-byte loads and stores, grid-stride, and the batch's K + 1 output offsets
+// and its result record to their mapped host copies, so the batch needs no copy calls of its own.
 __global__ void copy_out_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst, const zs::DevResult *r,
-                                uint64_t cap)
+                                uint64_t cap, const uint64_t *__restrict__ off, uint64_t *__restrict__ h_off,
+                                uint64_t n_off, zs::DevResult *h_res)
 {
     const uint64_t n = min((uint64_t)r->out_len, cap);
     const uint64_t n16 = n >> 4;
@@ -130,6 +134,8 @@ __global__ void copy_out_kernel(const uint8_t *__restrict__ src, uint8_t *__rest
     for (uint64_t i = tid; i < n16; i += stride)
         reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
     for (uint64_t i = (n16 << 4) + tid; i < n; i += stride) dst[i] = src[i];
+    for (uint64_t i = tid; i < n_off; i += stride) h_off[i] = off[i];
+    if (tid == 0) *h_res = *r;
 }
 
 // The longest decoded line of a store (with its '\n'), and a count of index entries or lines that do
@@ -266,10 +272,8 @@ zs_status store_max_line(const zs_dict *d, const uint8_t *comp, size_t comp_len,
 cudaError_t issue_batch(zs_server *S, Slot &s)
 {
     const size_t K = s.K;
-    cudaError_t e = cudaMemcpyAsync(s.d_ids, s.h_ids, K * sizeof(uint64_t), cudaMemcpyHostToDevice, s.st);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(s.d_scratch, 0,
-                            sizeof(zs::DevResult) + zs::lines_tiles(K) * sizeof(zs::TileState), s.st);
+    cudaError_t e = cudaMemsetAsync(s.d_scratch, 0,
+                                    sizeof(zs::DevResult) + zs::lines_tiles(K) * sizeof(zs::TileState), s.st);
     zs::DevResult *dr = reinterpret_cast<zs::DevResult *>(s.d_scratch);
     zs::TileState *tiles = reinterpret_cast<zs::TileState *>(dr + 1);
     if (e == cudaSuccess)
@@ -277,12 +281,10 @@ cudaError_t issue_batch(zs_server *S, Slot &s)
                              S->d_arena + s.batch->dev_off, s.batch->bound, s.d_off, dr, tiles, s.st);
     if (e == cudaSuccess) {
         copy_out_kernel<<<copy_blocks(s.batch->bound), 256, 0, s.st>>>(
-            S->d_arena + s.batch->dev_off, S->h_arena_dev + s.batch->host_off, dr, s.batch->bound);
+            S->d_arena + s.batch->dev_off, S->h_arena_dev + s.batch->host_off, dr, s.batch->bound, s.d_off,
+            s.h_off_dev, K + 1, s.h_res_dev);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.h_off, s.d_off, (K + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_res, dr, sizeof(zs::DevResult), cudaMemcpyDeviceToHost, s.st);
     if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
     return e;
 }
@@ -467,10 +469,15 @@ extern "C" zs_status zs_server_create(const zs_dict *d, const uint8_t *d_comp, s
     for (Slot &s : S->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&s.h_ids), K * sizeof(uint64_t));
-        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&s.h_off), (K + 1) * sizeof(uint64_t));
-        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&s.h_res), sizeof(zs::DevResult));
-        if (e == cudaSuccess) e = cudaMalloc(&s.d_ids, K * sizeof(uint64_t));
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_ids), K * sizeof(uint64_t), cudaHostAllocMapped);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_off), (K + 1) * sizeof(uint64_t), cudaHostAllocMapped);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_res), sizeof(zs::DevResult), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s.d_ids), s.h_ids, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s.h_off_dev), s.h_off, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s.h_res_dev), s.h_res, 0);
         if (e == cudaSuccess) e = cudaMalloc(&s.d_off, (K + 1) * sizeof(uint64_t));
         if (e == cudaSuccess)
             e = cudaMalloc(&s.d_scratch, sizeof(zs::DevResult) + S->scratch_tiles * sizeof(zs::TileState));
@@ -517,7 +524,6 @@ extern "C" void zs_server_destroy(zs_server *S)
         if (s.h_ids) cudaFreeHost(s.h_ids);
         if (s.h_off) cudaFreeHost(s.h_off);
         if (s.h_res) cudaFreeHost(s.h_res);
-        if (s.d_ids) cudaFree(s.d_ids);
         if (s.d_off) cudaFree(s.d_off);
         if (s.d_scratch) cudaFree(s.d_scratch);
     }
@@ -575,6 +581,16 @@ extern "C" zs_status zs_server_submit(zs_server *S, const uint64_t *ids, size_t 
     }
     S->queue.push_back(p);
     ++S->changes;
+    // a free slot takes the request at once, from this thread: no hand-off to the scheduler at low load
+    for (Slot &s : S->slots) {
+        if (s.state != 0 || S->fatal != ZS_OK) continue;
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != S->device) cudaSetDevice(S->device);
+        S->admit(s);
+        if (cur >= 0 && cur != S->device) cudaSetDevice(cur);
+        break;
+    }
     S->cv.notify_all();
     return ZS_OK;
 }

@@ -404,10 +404,12 @@ def test_long_pattern_dictionary(zs, long_dicts):
 
 
 @pytest.mark.parametrize("name", ["zs_lmax5.zsd", "zs_lmax15.zsd", "zs_no_alphabet.zsd", "zs_raw_train.zsd",
-                                  "zs_outer_train.zsd"])
+                                  "zs_outer_train.zsd", "zs_printable.zsd", "zs_printable_raw.zsd",
+                                  "zs_no_alphabet_raw.zsd"])
 def test_ablation_dictionaries(zs, name):
-    """Every ablation dictionary (L_max 5 / 15, no alphabet, raw training, opening-order training) codes
-    exactly like the oracle, with pre-processing off and in either reading."""
+    """Every ablation dictionary (L_max 5 / 15; pre-population printable, SMILES alphabet or none, trained with
+    and without ring renumbering; opening-order training) codes exactly like the oracle, with pre-processing
+    off and in either reading."""
     data = open(os.path.join(ROOT, "paper_2404_19391_gb300", "data", name), "rb").read()
     pair = (zs.Dictionary(data), oracle.Dict(data))
     raw = synth.generate(synth.CFG0, 900, 3000)

@@ -118,7 +118,8 @@ def test_ablation_dictionaries_load():
     data_dir = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2404_19391_gb300",
                             "data")
     want = {"zs_lmax5.zsd": (5, True), "zs_lmax15.zsd": (15, True), "zs_no_alphabet.zsd": (8, False),
-            "zs_raw_train.zsd": (8, True), "zs_outer_train.zsd": (8, True)}
+            "zs_raw_train.zsd": (8, True), "zs_outer_train.zsd": (8, True), "zs_printable.zsd": (8, True),
+            "zs_printable_raw.zsd": (8, True), "zs_no_alphabet_raw.zsd": (8, False)}
     for name, (lmax, alpha) in want.items():
         text = open(os.path.join(data_dir, name), "rb").read()
         lines = text.decode().splitlines()
@@ -126,3 +127,18 @@ def test_ablation_dictionaries_load():
         assert int(lines[1].split()[1]) == lmax
         assert (lines[2] != "alphabet -") == alpha
         oracle.Dict(text)  # parses and validates
+        if name.startswith("zs_printable"):  # Table I "Printable": every printable byte pre-populated, so the
+            # learned patterns take the 95 symbols 0xA1-0xFF
+            assert bytes.fromhex(lines[2].split()[1]) == bytes(range(0x21, 0x7F))
+            assert int(lines[1].split()[2]) == 95
+            assert all(0xA1 <= int(ln.split()[0], 16) <= 0xFF for ln in lines[3:] if ln)
+
+
+def test_printable_dictionary_regenerates():
+    """The committed Table I 'Printable' dictionary is what Algorithm 1 writes for the seed-1 training set with
+    the printable pre-population (T cut to the 95 free symbols)."""
+    from oracle.make_dictionary import build_default
+    path = os.path.join(ROOT, "paper_2404_19391_gb300", "data", "zs_printable.zsd")
+    with open(path, "rb") as f:
+        committed = f.read()
+    assert build_default(T=95, alphabet=dictgen.PRINTABLE_ALPHABET) == committed
