@@ -408,9 +408,10 @@ def _concat_host(specs, first_of):
 
 
 def bench_stream(zs, d, dev, shape, lines: int, peak: float, reps: int, first: int = 0, index: bool = True,
-                 line_index: bool = False):
-    """One stream through zs_compress and zs_decompress (one launch each): kernel times (median of reps, CUDA
-    events), GB/s, HBM fractions of the algorithmic bytes."""
+                 line_index: bool = False, plan: bool = False):
+    """One stream through zs_compress and zs_decompress (one launch each), or (plan) through an autotuned
+    plan each way (the geometry timed on the stream itself): kernel times (median of reps, CUDA events),
+    GB/s, HBM fractions of the algorithmic bytes."""
     import torch
     nbytes = synth.lines_size(shape, first, lines)
     host = np.empty(nbytes, dtype=np.uint8)
@@ -420,17 +421,35 @@ def bench_stream(zs, d, dev, shape, lines: int, peak: float, reps: int, first: i
     comp = torch.empty(zs.zs_compress_bound(nbytes), dtype=torch.uint8, device=dev)
     idx = torch.empty(lines + 2, dtype=torch.int64, device=dev) if index else None
     kc, kd = [], []
-    for k in range(reps + 1):
-        r = zs.zs_compress(d, x, zs.PREPROCESS, comp, idx)
-        if k:
-            kc.append(zs.zs_last_kernel_ms())
-    assert r.n_lines == lines, (r.n_lines, lines)
-    c = comp[: r.out_len]
+    variants = {}
     dec = torch.empty(nbytes + nbytes // 8 + 64, dtype=torch.uint8, device=dev)  # decoded <= input + %nn growth
-    for k in range(reps + 1):
-        rd = zs.zs_decompress(d, c, dec)
-        if k:
-            kd.append(zs.zs_last_kernel_ms())
+    if plan:
+        pc = zs.Plan(d, zs.OP_COMPRESS, [(x, comp, idx)], flags=zs.PREPROCESS, variant=-1, tune_reps=2)
+        for k in range(reps + 1):
+            r = pc.run()[0]
+            if k:
+                kc.append(pc.last_ms)
+        variants["compress"] = zs.zs_kernel_variant_name(zs.OP_COMPRESS, pc.variant)
+        pc.close()
+        c = comp[: r.out_len]
+        pd = zs.Plan(d, zs.OP_DECOMPRESS, [(c, dec, None)], variant=-1, tune_reps=2)
+        for k in range(reps + 1):
+            rd = pd.run()[0]
+            if k:
+                kd.append(pd.last_ms)
+        variants["decompress"] = zs.zs_kernel_variant_name(zs.OP_DECOMPRESS, pd.variant)
+        pd.close()
+    else:
+        for k in range(reps + 1):
+            r = zs.zs_compress(d, x, zs.PREPROCESS, comp, idx)
+            if k:
+                kc.append(zs.zs_last_kernel_ms())
+        c = comp[: r.out_len]
+        for k in range(reps + 1):
+            rd = zs.zs_decompress(d, c, dec)
+            if k:
+                kd.append(zs.zs_last_kernel_ms())
+    assert r.n_lines == lines, (r.n_lines, lines)
     assert rd.n_lines == lines
     kc, kd = float(np.median(kc)), float(np.median(kd))
     ca = nbytes + r.out_len + (8 * (lines + 1) if index else 0)
@@ -442,6 +461,8 @@ def bench_stream(zs, d, dev, shape, lines: int, peak: float, reps: int, first: i
            "decompress": {"kernel_ms": kd, "gbps_in": r.out_len / kd / 1e6, "gbps_out": rd.out_len / kd / 1e6,
                           "hbm_gbps": da / kd / 1e6, "hbm_frac": da / kd / 1e6 / peak, "algorithmic_bytes": da},
            "decoded_bytes": rd.out_len}
+    if variants:
+        out["variants"] = variants
     if line_index and index:  # the index rebuilt from the compressed stream alone, against the compressor's
         idx2 = torch.empty(lines + 2, dtype=torch.int64, device=dev)
         li = []
@@ -659,10 +680,10 @@ def run_gpu(args):
         cfg1["workload"] = workload_desc(args.lines, cfg1["bytes"])
         cfg3 = None
         if args.cfg3_lines > 0:
-            cfg3 = bench_stream(zs, d, dev, synth.CFG3, args.cfg3_lines, peak, reps=3)
+            cfg3 = bench_stream(zs, d, dev, synth.CFG3, args.cfg3_lines, peak, reps=3, plan=True)
             cfg3["workload"] = (f"batched long tail: {args.cfg3_lines:,} synthetic lines ({cfg3['bytes'] / 1e9:.2f} "
                                 "GB), 90% drug-like, 10% of 150-400 chars with bracket atoms, stereo bonds and "
-                                "%nn ring labels; one stream, one launch each way")
+                                "%nn ring labels; one stream, one autotuned plan (CUDA graph) each way")
         line = {
             "metric": metric_name(), "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,

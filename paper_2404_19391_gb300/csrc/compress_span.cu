@@ -50,6 +50,7 @@ constexpr uint32_t kPosBits = 13, kPosMask = (1u << kPosBits) - 1u;  // emission
 // call was marked for the general kernel): every later tile's output and index offsets then lie past any
 // buffer's capacity, so nothing is written past what the general kernel's run will write.
 constexpr uint64_t kPoison = 1ull << 40;
+constexpr uint32_t kLongLine = 1u << 30;  // a line this long (or longer) is refused (ZS_ERR_INVALID_ARG)
 
 // Launch-wide arguments; the per-shard ones are in the ShardView of each claimed tile.
 struct SpArgs {
@@ -64,6 +65,8 @@ struct SpArgs {
     uint32_t q0;          // start state
     uint32_t rep_col;     // 2 * a byte below 0x80 that acts like every byte >= 0x80
     DevResult *g;
+    uint8_t *slow;        // scratch of the lines coded one at a time (SlowLayout each)
+    uint64_t slow_cap;
     uint64_t limit_ns;
     int64_t stall_tile;
 };
@@ -71,7 +74,7 @@ struct SpArgs {
 // Per-byte SIMD classification (bytes of a 32-bit word; the high bit of each result byte is the answer).
 // Bytes >= 0x80 are in no class. Range tests add to the low seven bits, which never carries out of a byte.
 struct Classes {
-    uint32_t nl, dig, ob, cb, sp;  // '\n'; '0'-'9'; '['; ']'; '%', ' ' or tab
+    uint32_t nl, dig, ob, cb, sp;  // '\n'; '0'-'9' and '%' (ring labels); '['; ']'; ' ' or tab
 };
 
 __device__ __forceinline__ Classes classify(uint32_t x)
@@ -79,11 +82,10 @@ __device__ __forceinline__ Classes classify(uint32_t x)
     const uint32_t y = x & 0x7F7F7F7Fu, h = 0x80808080u & ~x;
     Classes c;
     c.nl = ~((y ^ 0x0A0A0A0Au) + 0x7F7F7F7Fu) & h;
-    c.dig = (y + 0x50505050u) & ~(y + 0x46464646u) & h;  // >= 0x30 and < 0x3A
+    c.dig = (((y + 0x50505050u) & ~(y + 0x46464646u)) | ~((y ^ 0x25252525u) + 0x7F7F7F7Fu)) & h;  // 0-9, %
     c.ob = ~((y ^ 0x5B5B5B5Bu) + 0x7F7F7F7Fu) & h;
     c.cb = ~((y ^ 0x5D5D5D5Du) + 0x7F7F7F7Fu) & h;
-    c.sp = ~(((y ^ 0x25252525u) + 0x7F7F7F7Fu) & ((y ^ 0x20202020u) + 0x7F7F7F7Fu) &
-             ((y ^ 0x09090909u) + 0x7F7F7F7Fu)) & h;
+    c.sp = ~(((y ^ 0x20202020u) + 0x7F7F7F7Fu) & ((y ^ 0x09090909u) + 0x7F7F7F7Fu)) & h;
     return c;
 }
 
@@ -149,9 +151,9 @@ struct SP {
     struct alignas(16) WarpMem {
         uint8_t text[kSt + 16];
         uint32_t nmask[kMaskWords];  // one bit per staged byte: '\n'
-        uint32_t dmask[kMaskWords];  // digits
-        uint32_t omask[kMaskWords];  // '[', and '%' ' ' tab
-        uint32_t cmask[kMaskWords];  // ']', and '%' ' ' tab (a byte in both masks always makes an exception)
+        uint32_t dmask[kMaskWords];  // digits and '%'
+        uint32_t omask[kMaskWords];  // '[', and ' ' tab
+        uint32_t cmask[kMaskWords];  // ']', and ' ' tab (a byte in both masks always makes an exception)
         uint16_t ring[(20 + 2 * kOpen2) * 32];  // per lane (entry k of lane l at [k * 32 + l]): open positions
                                                  // of labels 0-9, latest closes of new labels 0-9, open %nn
         OutSlot os[2];
@@ -318,6 +320,117 @@ struct SP {
         return s;
     }
 
+    // ---- lines coded one at a time ---------------------------------------------------------------------
+    // A line that needs a ring label above 9, more open %nn labels than a lane follows, or that runs past the
+    // staged bytes is coded alone in global scratch (the exact slow pre-processing, then the byte transducer
+    // one byte at a time) and emitted from there; the lane's other lines take the fast path around it.
+    // Up to kMaxSlow such lines per lane; more make the call run again by the general kernel.
+    static constexpr uint32_t kMaxSlow = 2;
+    struct Slow {
+        uint32_t n;
+        uint32_t a[kMaxSlow], b[kMaxSlow];  // staged positions (after compaction) the line occupies
+        uint32_t ga[kMaxSlow];              // its first byte as an original staged position
+        uint32_t out[kMaxSlow];             // output bytes (with the '\n' of a line past the staged bytes)
+        uint64_t ws[kMaxSlow];              // its work space in the scratch (offset), or ~0 if not coded
+        uint32_t past;                      // bit k: line k runs past the staged bytes (found in memory)
+    };
+
+    static __device__ __forceinline__ bool add_slow(Slow &S, uint32_t a, uint32_t b, uint32_t ga, bool past = false)
+    {
+        if (S.n >= kMaxSlow) return false;
+        S.a[S.n] = a;
+        S.b[S.n] = b;
+        S.ga[S.n] = ga;
+        S.out[S.n] = 0;
+        S.ws[S.n] = ~0ull;
+        if (past) S.past |= 1u << S.n;
+        ++S.n;
+        return true;
+    }
+
+    // Codes the lane's slow lines one at a time in the scratch: the exact slow pre-processing into the work
+    // space's text (labels up to 99, any number of %nn), then the byte transducer, last byte first, into its
+    // choices; notes each line's output bytes. A work space records {input bytes, coded bytes, '\n' follows}.
+    static __device__ void code_slow(const Ctx &C, Slow &SL, uint64_t base)
+    {
+        const ShardView &A = *C.A;
+        const uint8_t *tab = C.tab;
+        const uint32_t rep = C.P->rep_col;
+        for (uint32_t k = 0; k < SL.n; ++k) {
+            const uint64_t gs = base - 16 + SL.ga[k];  // the line's first byte in memory
+            uint64_t glen = SL.b[k] - SL.a[k];
+            bool nl_after = false;
+            if ((SL.past >> k) & 1u) {  // find its end in memory
+                uint64_t ge = base - 16 + SL.ga[k] + glen;
+                while (ge < A.n && A.in[ge] != kNl) ++ge;
+                nl_after = ge < A.n;
+                glen = ge - gs;
+            }
+            if (glen >= kLongLine) {
+                atomicOr(C.status, kStTooBig);
+                continue;
+            }
+            const SlowLayout sl = slow_layout((uint32_t)glen);
+            const unsigned long long off = atomicAdd(&C.P->g->slow_used, (unsigned long long)sl.need);
+            if (off + sl.need > C.P->slow_cap) {  // the host retries with a larger scratch
+                atomicOr(C.status, kStSlowOverflow);
+                continue;
+            }
+            uint8_t *ws = C.P->slow + off;
+            uint8_t *tx = ws + sl.text, *ch = ws + sl.chs;
+            uint32_t m;
+            if (C.P->flags & ZS_PREPROCESS) {
+                m = preprocess_slow(A.in + gs, (uint32_t)glen, tx, ws + sl.tok, reinterpret_cast<int32_t *>(ws + sl.tables),
+                                    reinterpret_cast<int32_t *>(ws + sl.tables) + 100, OUTER);
+            } else {
+                for (uint32_t i = 0; i < (uint32_t)glen; ++i) tx[i] = A.in[gs + i];
+                m = (uint32_t)glen;
+            }
+            uint32_t st = C.P->q0;
+            for (uint32_t i = m; i-- > 0;) {
+                const uint32_t b = tx[i];
+                st = look(tab, st, b >= 0x80u ? rep : (b << 1), 0x3204);
+                ch[i] = (uint8_t)(st >> 8);
+            }
+            uint32_t outb = nl_after ? 1u : 0u;
+            for (uint32_t i = 0; i < m;) {
+                const uint32_t e = C.meta[ch[i]];
+                i += e & kPosMask;
+                outb += e >> kPosBits;
+            }
+            reinterpret_cast<uint32_t *>(ws)[0] = (uint32_t)glen;
+            reinterpret_cast<uint32_t *>(ws)[1] = m;
+            reinterpret_cast<uint32_t *>(ws)[2] = nl_after ? 1u : 0u;
+            SL.out[k] = outb;
+            SL.ws[k] = off;
+        }
+    }
+
+    // Emission of a slow line from its work space at output offset w; returns the offset after it.
+    template <class Sink>
+    static __device__ uint32_t emit_slow(const Ctx &C, uint64_t wsoff, uint32_t w, Sink &S)
+    {
+        if (wsoff == ~0ull) return w;
+        const uint8_t *ws = C.P->slow + wsoff;
+        const uint32_t glen = reinterpret_cast<const uint32_t *>(ws)[0];
+        const uint32_t m = reinterpret_cast<const uint32_t *>(ws)[1];
+        const bool nl_after = reinterpret_cast<const uint32_t *>(ws)[2] != 0;
+        const SlowLayout sl = slow_layout(glen);
+        const uint8_t *tx = ws + sl.text, *ch = ws + sl.chs;
+        for (uint32_t i = 0; i < m;) {
+            const uint32_t c = ch[i];
+            i += C.meta[c] & kPosMask;
+            if (c > kChEsc) {
+                S.put(w++, (uint8_t)c);
+            } else {
+                S.put(w++, kEsc);
+                S.put(w++, c == kChEsc ? tx[i - 1] : (uint8_t)('0' + c - kChEscDigit));
+            }
+        }
+        if (nl_after) S.put(w++, kNl);
+        return w;
+    }
+
     // ---- pre-processing ---------------------------------------------------------------------------------
     // Walks the token bits of the lane's span [a, b) line by line and relabels ring IDs in place (closing
     // order by default: a ring takes, when it closes, the smallest label whose latest ring closed before this
@@ -327,7 +440,8 @@ struct SP {
     // the rest of the span down. Returns the span's end after compaction; *lines = lines in the span;
     // *shifted = some line was compacted; *fallback = a line needs the general kernel.
     static __device__ uint32_t relabel_general(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
-                                               uint32_t *lines_out, bool *shifted, bool *fallback)
+                                               uint32_t *lines_out, bool *shifted, bool last_slow, Slow &SL,
+                                               bool *fallback)
     {
         WarpMem &M = *C.M;
         uint8_t *text = M.text;
@@ -338,10 +452,12 @@ struct SP {
         // per-line state
         uint32_t ls = a;  // line start (original positions)
         uint32_t dopen = 0, lcv = 0, held = 0, nopen2 = 0, skip_to = 0;
-        bool in_br = false, field_done = false, bad = false, any_pct = false, wrote = false;
+        bool in_br = false, field_done = false, bad = false, any_pct = false, wrote = false, slow = false;
         auto finish_line = [&](uint32_t le) {  // le: the line's end (its '\n' or the span end), original
             const uint32_t cls = ls - shift, cle = le - shift;
-            if (wrote && (bad || in_br || dopen != 0 || nopen2 != 0)) {  // left as it is
+            if (slow || (last_slow && le == b)) {  // coded alone; its bytes here are skipped
+                if (!add_slow(SL, cls, cle, ls, last_slow && le == b)) fb = true;
+            } else if (wrote && (bad || in_br || dopen != 0 || nopen2 != 0)) {  // left as it is
                 for (uint32_t k = cls; k < cle; ++k) text[k] = raw[k + shift];
             } else if (wrote && any_pct) {  // squeeze out the deleted digits, then move the rest down
                 uint32_t w = cls;
@@ -360,7 +476,7 @@ struct SP {
                 for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
             dopen = lcv = held = nopen2 = 0;
             skip_to = 0;
-            in_br = field_done = bad = any_pct = wrote = false;
+            in_br = field_done = bad = any_pct = wrote = slow = false;
         };
         for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
         if (a < b) {
@@ -382,7 +498,7 @@ struct SP {
                     finish_line(p);
                     continue;
                 }
-                if (!pre || field_done || bad || p < skip_to || fb) continue;
+                if (!pre || field_done || bad || slow || p < skip_to || fb) continue;
                 if (c == ' ' || c == '\t') {  // the SMILES field ends at the first space or tab
                     field_done = true;
                     continue;
@@ -434,7 +550,7 @@ struct SP {
                         oslot = 21u + 2u * (uint32_t)empty;
                         ++nopen2;
                     } else {
-                        fb = true;  // more open %nn labels than the lane follows
+                        slow = true;  // more open %nn labels than the lane follows
                         continue;
                     }
                 }
@@ -444,7 +560,7 @@ struct SP {
                     if (opening) {
                         const uint32_t fr = ~held & 0x3FFu;
                         if (fr == 0) {  // would need a two-digit label
-                            fb = true;
+                            slow = true;
                             continue;
                         }
                         nl = (uint32_t)__ffs(fr) - 1u;
@@ -468,7 +584,7 @@ struct SP {
                         }
                     }
                     if (nl == 10) {  // would need a two-digit label
-                        fb = true;
+                        slow = true;
                         continue;
                     }
                     text[o] = (uint8_t)('0' + nl);
@@ -496,10 +612,11 @@ struct SP {
         return b - shift;
     }
 
-    // Whether the span [a, b) can take the fast relabelling: no '%', space or tab, and every bracket atom
-    // opens and closes within its line, without nesting and without a digit inside. Bit arithmetic over the
-    // class masks, one 32-bit word at a time: the prefix XOR of the bracket bits is 1 from a '[' up to its ']'.
-    // '%', space and tab are in both bracket masks, so each one is a '[' inside an atom or a ']' outside one.
+    // Whether the span [a, b) can take the fast relabelling: no space or tab (a second field), and every
+    // bracket atom opens and closes within its line, without nesting and without a digit or '%' inside. Bit
+    // arithmetic over the class masks, one 32-bit word at a time: the prefix XOR of the bracket bits is 1 from
+    // a '[' up to its ']'. Space and tab are in both bracket masks, so each one is a '[' inside an atom or a ']'
+    // outside one.
     static __device__ __forceinline__ bool exception_free(const WarpMem &M, uint32_t a, uint32_t b)
     {
         uint32_t in = 0;  // inside a bracket atom at the start of the word
@@ -513,8 +630,8 @@ struct SP {
             const uint32_t px = prefix_xor(t) ^ (0u - in);   // 1 from each '[' up to, not including, its ']'
             const uint32_t before = px ^ t;                  // the state just before each bit
             bad |= (o & before)                              // '[' inside a bracket atom
-                   | (c & ~before)                           // ']' outside one ('%', space, tab: always one
-                                                             //  of the two, being in both masks)
+                   | (c & ~before)                           // ']' outside one (space, tab: always one of
+                                                             //  the two, being in both masks)
                    | (M.dmask[w] & keep & px & ~t)           // a digit inside one
                    | (M.nmask[w] & keep & px);               // a line ending inside one
             in = (px >> 31) & 1u;
@@ -522,16 +639,17 @@ struct SP {
         return bad == 0 && in == 0;
     }
 
-    // Digits of the line [ls, le) back to their input bytes (a line found invalid at its end).
+    // Ring-label bytes (digits and '%') of the line at original positions [ls, le) back to their input
+    // bytes, the line sitting `shift` bytes lower in the stage (a line found invalid at its end).
     static __device__ __forceinline__ void restore_digits(const WarpMem &M, uint8_t *text, const uint8_t *raw,
-                                                          uint32_t ls, uint32_t le)
+                                                          uint32_t ls, uint32_t le, uint32_t shift)
     {
         for (uint32_t w = ls >> 5; (w << 5) < le; ++w) {
             uint32_t bits = M.dmask[w];
             while (bits) {
                 const uint32_t q = (w << 5) + (uint32_t)(__ffs(bits) - 1);
                 bits &= bits - 1;
-                if (q >= ls && q < le) text[q] = raw[q];
+                if (q >= ls && q < le) text[q - shift] = raw[q];
             }
         }
     }
@@ -540,15 +658,41 @@ struct SP {
     // of a line are decided as in relabel_general; the latest close of each new label is kept in 16-bit
     // halves of five registers (label x in register x % 5, high half for x >= 5), so finding the smallest
     // label free since the ring opened is five subtractions and one find-first-set, without branches.
-    static __device__ __forceinline__ void relabel_fast(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
-                                                        bool *fallback)
+    static __device__ __forceinline__ uint32_t relabel_fast(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
+                                                            bool last_slow, Slow &SL, bool *shifted, bool *fallback)
     {
         WarpMem &M = *C.M;
         uint8_t *text = M.text;
-        uint16_t *openp = M.ring + C.lane;  // open position + 1 of digit label d at openp[32 * d]
-        uint32_t ls = a, dopen = 0, held = 0;
+        // ring[32 * d]: open position + 1 of digit label d (bit 15: written %0d); ring[32 * (20 + 2 j)]: label + 1
+        // of open %nn slot j, ring[32 * (21 + 2 j)]: its open position + 1 (bit 15 set)
+        uint16_t *ring = M.ring + C.lane;
+        uint32_t ls = a, dopen = 0, held = 0, nopen2 = 0, skip_to = 0, shift = 0;
         uint32_t L0 = 0, L1 = 0, L2 = 0, L3 = 0, L4 = 0;
-        bool fb = false;
+        bool fb = false, slow = false, bad = false, any_pct = false;
+        for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
+        auto end_line = [&](uint32_t le) {  // le: the line's end (its '\n' or b), an original position
+            const uint32_t cls = ls - shift, cle = le - shift;
+            if (slow || (last_slow && le == b)) {  // coded alone; its bytes here are skipped
+                if (!add_slow(SL, cls, cle, ls, last_slow && le == b)) fb = true;
+            } else if (bad || dopen != 0 || nopen2 != 0) {  // an unclosed ring or a bad %: left as it is
+                restore_digits(M, text, raw, ls, le, shift);
+            } else if (any_pct) {  // squeeze out the deleted digits of %nn labels, then move the rest down
+                uint32_t w2 = cls;
+                for (uint32_t r = cls; r < cle; ++r) {
+                    const uint8_t v = text[r];
+                    if (v != kDel) text[w2++] = v;
+                }
+                const uint32_t d = cle - w2, bend = b - shift;
+                for (uint32_t r = cle; r < bend; ++r) text[r - d] = text[r];
+                shift += d;
+            }
+            if (nopen2)
+                for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
+            dopen = held = nopen2 = 0;
+            L0 = L1 = L2 = L3 = L4 = 0;
+            slow = bad = any_pct = false;
+            skip_to = 0;
+        };
         uint32_t w = a >> 5;
         uint32_t bits = (M.dmask[w] | M.nmask[w]) & (kAll << (a & 31));
         for (;;) {
@@ -561,79 +705,131 @@ struct SP {
             const uint32_t p = (w << 5) + (uint32_t)(__ffs(bits) - 1);
             bits &= bits - 1;
             if (p >= b) break;
-            const uint32_t c = text[p];
-            if (c == kNl) {  // end of a line: one with an unclosed ring stays as it is
-                if (dopen) restore_digits(M, text, raw, ls, p);
-                dopen = held = 0;
-                L0 = L1 = L2 = L3 = L4 = 0;
+            const uint32_t q = p - shift;  // where the byte sits now
+            const uint32_t c = text[q];
+            if (c == kNl) {
+                end_line(p);
                 ls = p + 1u;
                 continue;
             }
-            const uint32_t d = c - '0';
-            const uint32_t bit = 1u << d;
-            if (dopen & bit) {  // closes the ring opened at o
-                const uint32_t o = (uint32_t)openp[32 * d] - 1u;
-                uint32_t nl;
-                if (OUTER) {
-                    nl = (uint32_t)text[o] - '0';
-                    held &= ~(1u << nl);
-                } else {
-                    const uint32_t orep = (o * 0x00010001u) | 0x80008000u;
-                    const uint32_t g = (((orep - L0) & 0x80008000u) >> 15) | (((orep - L1) & 0x80008000u) >> 14) |
-                                       (((orep - L2) & 0x80008000u) >> 13) | (((orep - L3) & 0x80008000u) >> 12) |
-                                       (((orep - L4) & 0x80008000u) >> 11);
-                    const uint32_t f = (g & 0x1Fu) | ((g >> 11) & 0x3E0u);  // labels free since o, in order
-                    if (f == 0) {  // would need a two-digit label
-                        fb = true;
-                        break;
-                    }
-                    nl = (uint32_t)__ffs(f) - 1u;
-                    text[o] = (uint8_t)('0' + nl);
-                    const uint32_t r = nl < 5 ? nl : nl - 5u;
-                    const uint32_t hm = nl < 5 ? 0x0000FFFFu : 0xFFFF0000u;
-                    const uint32_t v = ((p + 1u) * 0x00010001u) & hm;
-                    L0 = r == 0 ? (L0 & ~hm) | v : L0;
-                    L1 = r == 1 ? (L1 & ~hm) | v : L1;
-                    L2 = r == 2 ? (L2 & ~hm) | v : L2;
-                    L3 = r == 3 ? (L3 & ~hm) | v : L3;
-                    L4 = r == 4 ? (L4 & ~hm) | v : L4;
+            if (slow || bad || p < skip_to) continue;
+            uint32_t label;
+            bool pct = false;
+            if (c == '%') {  // %nn: two digits must follow within the line
+                const uint32_t d1 = (uint32_t)text[q + 1] - '0', d2 = (uint32_t)text[q + 2] - '0';
+                if (p + 2 >= b || d1 > 9 || d2 > 9) {
+                    bad = true;
+                    continue;
                 }
-                text[p] = (uint8_t)('0' + nl);
-            } else {  // opens a ring
-                openp[32 * d] = (uint16_t)(p + 1u);
-                if (OUTER) {
-                    const uint32_t fr = ~held & 0x3FFu;
-                    if (fr == 0) {
-                        fb = true;
-                        break;
-                    }
-                    const uint32_t nl = (uint32_t)__ffs(fr) - 1u;
-                    held |= 1u << nl;
-                    text[p] = (uint8_t)('0' + nl);
+                label = d1 * 10 + d2;
+                pct = true;
+                skip_to = p + 3;
+            } else {
+                label = c - '0';
+            }
+            uint32_t open_e = 0, oslot = label;  // open_e: the ring's open token if this token closes it
+            if (label < 10) {
+                if ((dopen >> label) & 1u) open_e = ring[32 * label];
+                dopen ^= 1u << label;
+            } else {
+                int hit = -1, empty = -1;
+#pragma unroll
+                for (int j = 0; j < (int)kOpen2; ++j) {
+                    const uint32_t v = ring[32 * (20 + 2 * j)];
+                    if (v == label + 1) hit = j;
+                    if (v == 0 && empty < 0) empty = j;
+                }
+                if (hit >= 0) {
+                    open_e = ring[32 * (21 + 2 * hit)];
+                    ring[32 * (20 + 2 * hit)] = 0;
+                    --nopen2;
+                } else if (empty >= 0) {
+                    ring[32 * (20 + 2 * empty)] = (uint16_t)(label + 1);
+                    oslot = 21u + 2u * (uint32_t)empty;
+                    ++nopen2;
+                } else {  // more open %nn labels than the lane follows: the line is coded alone
+                    slow = true;
+                    continue;
                 }
             }
-            dopen ^= bit;
+            uint32_t nl;
+            if (open_e == 0) {  // opens a ring
+                ring[32 * oslot] = (uint16_t)((q + 1u) | (pct ? 0x8000u : 0u));
+                if (!OUTER) continue;
+                const uint32_t fr = ~held & 0x3FFu;
+                if (fr == 0) {  // would need a two-digit label
+                    slow = true;
+                    continue;
+                }
+                nl = (uint32_t)__ffs(fr) - 1u;
+                held |= 1u << nl;
+            } else if (OUTER) {  // closes a ring: it repeats the label taken when it opened
+                nl = (uint32_t)text[(open_e & 0x7FFFu) - 1u] - '0';
+                held &= ~(1u << nl);
+            } else {  // closes the ring opened at o: the smallest label free since o
+                const uint32_t o = (open_e & 0x7FFFu) - 1u;
+                const uint32_t orep = (o * 0x00010001u) | 0x80008000u;
+                const uint32_t g = (((orep - L0) & 0x80008000u) >> 15) | (((orep - L1) & 0x80008000u) >> 14) |
+                                   (((orep - L2) & 0x80008000u) >> 13) | (((orep - L3) & 0x80008000u) >> 12) |
+                                   (((orep - L4) & 0x80008000u) >> 11);
+                const uint32_t f = (g & 0x1Fu) | ((g >> 11) & 0x3E0u);  // labels free since o, in order
+                if (f == 0) {  // would need a two-digit label: the line is coded alone
+                    slow = true;
+                    continue;
+                }
+                nl = (uint32_t)__ffs(f) - 1u;
+                text[o] = (uint8_t)('0' + nl);
+                if (open_e & 0x8000u) {
+                    text[o + 1] = kDel;
+                    text[o + 2] = kDel;
+                    any_pct = true;
+                }
+                const uint32_t r = nl < 5 ? nl : nl - 5u;
+                const uint32_t hm = nl < 5 ? 0x0000FFFFu : 0xFFFF0000u;
+                const uint32_t v = ((q + 1u) * 0x00010001u) & hm;
+                L0 = r == 0 ? (L0 & ~hm) | v : L0;
+                L1 = r == 1 ? (L1 & ~hm) | v : L1;
+                L2 = r == 2 ? (L2 & ~hm) | v : L2;
+                L3 = r == 3 ? (L3 & ~hm) | v : L3;
+                L4 = r == 4 ? (L4 & ~hm) | v : L4;
+            }
+            text[q] = (uint8_t)('0' + nl);
+            if (pct) {
+                text[q + 1] = kDel;
+                text[q + 2] = kDel;
+                any_pct = true;
+            }
         }
-        if (!fb && dopen) restore_digits(M, text, raw, ls, b);
+        if (ls < b) end_line(b);  // the span's last line has no '\n' here
+        *shifted = shift != 0;
         *fallback = fb;
+        return b - shift;
     }
 
     // Pre-processing of the lane's span (Sec. IV-A): the fast relabelling when the span allows it, else the
     // general walk. Returns the span's end after compaction; *lines = lines in the span.
     static __device__ __forceinline__ uint32_t preprocess(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
-                                                          uint32_t *lines, bool *shifted, bool *fallback)
+                                                          bool last_slow, uint32_t *lines, bool *shifted, Slow &SL,
+                                                          bool *fallback)
     {
         const WarpMem &M = *C.M;
         *lines = a < b ? count_bits(M.nmask, a, b) + (M.text[b - 1] != kNl ? 1u : 0u) : 0u;
         *shifted = false;
         *fallback = false;
-        if (!(C.P->flags & ZS_PREPROCESS) || a >= b) return b;
-        if (exception_free(M, a, b)) {
-            relabel_fast(C, a, b, raw, fallback);
+        SL.n = 0;
+        SL.past = 0;
+        if (a >= b) return b;
+        if (!(C.P->flags & ZS_PREPROCESS)) {
+            if (last_slow) {  // the last line runs past the staged bytes: coded alone
+                const uint32_t q = prev_nl(M, b, a);
+                const uint32_t ls = q == kNone ? a : q + 1u;
+                add_slow(SL, ls, b, ls, true);
+            }
             return b;
         }
+        if (exception_free(M, a, b)) return relabel_fast(C, a, b, raw, last_slow, SL, shifted, fallback);
         uint32_t l2 = 0;
-        return relabel_general(C, a, b, raw, &l2, shifted, fallback);
+        return relabel_general(C, a, b, raw, &l2, shifted, last_slow, SL, fallback);
     }
 
     // ---- parse ------------------------------------------------------------------------------------------
@@ -739,7 +935,7 @@ struct SP {
     // Write walk of the span [a, e) from output offset w, the lane's first line being line `rank` of the
     // tile: symbols as they are, escapes as ' ' + byte, and each new line's start offset.
     template <class Sink>
-    static __device__ __forceinline__ void write_out(const Ctx &C, uint32_t a, uint32_t e, uint32_t w, uint32_t rank,
+    static __device__ __forceinline__ void write_out(const Ctx &C, uint32_t a, uint32_t e, uint32_t &w, uint32_t &rank,
                                                      const uint8_t *raw, Sink &S)
     {
         const uint8_t *text = C.M->text;
@@ -767,7 +963,46 @@ struct SP {
         uint32_t off;       // its output offset within the tile
         uint32_t rank;      // its first line within the tile
         uint32_t total, lines;
+        Slow sl;            // its lines coded one at a time (skipped by the walks over the span)
     };
+
+    // The walks over the lane's span, around its slow lines: parse, output bytes, writes.
+    template <bool HIGH>
+    static __device__ __forceinline__ void parse_all(const Ctx &C, const Enc &E)
+    {
+        uint32_t p = E.a;
+        for (uint32_t k = 0; k < E.sl.n; ++k) {
+            parse<HIGH>(C, p, E.sl.a[k]);
+            p = E.sl.b[k];
+        }
+        parse<HIGH>(C, p, E.e);
+    }
+
+    static __device__ __forceinline__ uint32_t count_all(const Ctx &C, const Enc &E, bool check, bool *gen_esc)
+    {
+        uint32_t p = E.a, n = 0;
+        bool ge = false, g2 = false;
+        for (uint32_t k = 0; k < E.sl.n; ++k) {
+            n += count_out(C, p, E.sl.a[k], check, &g2) + E.sl.out[k];
+            ge |= g2;
+            p = E.sl.b[k];
+        }
+        n += count_out(C, p, E.e, check, &g2);
+        *gen_esc = ge | g2;
+        return n;
+    }
+
+    template <class Sink>
+    static __device__ __forceinline__ void write_all(const Ctx &C, const Enc &E, const uint8_t *raw, Sink &S)
+    {
+        uint32_t w = E.off, rank = E.rank, p = E.a;
+        for (uint32_t k = 0; k < E.sl.n; ++k) {
+            write_out(C, p, E.sl.a[k], w, rank, raw, S);
+            w = emit_slow(C, E.sl.ws[k], w, S);
+            p = E.sl.b[k];
+        }
+        write_out(C, p, E.e, w, rank, raw, S);
+    }
 
     // Everything up to the tile's aggregate: masks, spans, pre-processing, parse, sizes (and, when the tile
     // fits its stage, the staged output). Publishes the aggregate.
@@ -797,24 +1032,24 @@ struct SP {
         }
         const uint32_t tail_end = lastnl != kNone ? lastnl + 1u : stage_end;
         high |= mask_chunks(C, (16u + nown) >> 4, (tail_end + 15u) >> 4);
-        bool fb = lastnl == kNone && stage_hi != A.n;  // the last line runs past the halo
+        // the tile's last line runs past the halo: lane 31 codes it alone, reading it from memory
+        const bool past = lastnl == kNone && stage_hi != A.n;
         const Span sp = spans(C, t, nown, tail_end, stage_hi == A.n);
+        Enc E;
         uint32_t lines = 0;
-        bool shifted = false, pfb = false;
-        const uint32_t e = preprocess(C, sp.a, sp.b, raw, &lines, &shifted, &pfb);
-        fb |= pfb;
+        bool shifted = false, fb = false;
+        E.a = sp.a;
+        E.e = preprocess(C, sp.a, sp.b, raw, past && sp.a < sp.b && sp.b == sp.B32, &lines, &shifted, E.sl, &fb);
         __syncwarp();
-        if (high) parse<true>(C, sp.a, e);
-        else parse<false>(C, sp.a, e);
+        if (E.sl.n) code_slow(C, E.sl, base);
+        if (high) parse_all<true>(C, E);
+        else parse_all<false>(C, E);
         bool gen_esc = false;
-        const uint32_t ob = count_out(C, sp.a, e, shifted, &gen_esc);
+        const uint32_t ob = count_all(C, E, shifted, &gen_esc);
         fb |= shifted && gen_esc;  // an escaped input byte no longer sits at its input position
         fb = __any_sync(kAll, fb);
         if (fb && lane == 0) atomicOr(C.status, kStFallback);
         const uint32_t oinc = warp_incl_u32(ob), linc = warp_incl_u32(lines);
-        Enc E;
-        E.a = sp.a;
-        E.e = e;
         E.off = oinc - ob;
         E.rank = linc - lines;
         E.total = __shfl_sync(kAll, oinc, 31);
@@ -823,11 +1058,12 @@ struct SP {
         if (staged) {
             SmemOut so{O.out, O.idx, E.lines};
             if (lane == 0) O.idx[0] = 0;
-            write_out(C, E.a, E.e, E.off, E.rank, raw, so);
+            write_all(C, E, raw, so);
         }
         if (fb) {  // the call is run again by the general kernel: this tile and every later one write nothing
             E.total = E.lines = 0;
             E.e = E.a;
+            E.sl.n = 0;
         }
         if (lane == 0) {
             O.total = E.total;
@@ -881,7 +1117,7 @@ struct SP {
             publish(&A.tiles[t], 2u, ea + E.total, eb + E.lines);
         if (C.lane == 0 && A.index && E.lines > 0 && eb < A.index_cap) A.index[eb] = ea;
         GlobalOut go{A.out, A.out_cap, ea, A.index, A.index_cap, eb, E.lines};
-        write_out(C, E.a, E.e, E.off, E.rank, A.in + tile_base(t) - 16, go);
+        write_all(C, E, A.in + tile_base(t) - 16, go);
         finish_result(C, t, ea + E.total, eb + E.lines);
         __syncwarp();
     }
@@ -997,6 +1233,8 @@ cudaError_t sp_launch_as(const zs_dict *d, const TiledLaunch &L, unsigned flags,
     a.q0 = d->blayout.q0;
     a.rep_col = d->blayout.rep_col;
     a.g = L.g;
+    a.slow = L.slow;
+    a.slow_cap = L.slow_cap;
     a.limit_ns = wait_limit_ns();
     a.stall_tile = injected_stall_tile();
     const int smem = (int)sp_smem<Geo>(d);

@@ -107,20 +107,18 @@ def test_plan_every_variant(zs, dicts, expected):
 
 def test_autotuned_plan(zs, dicts, expected):
     """The autotuner times every geometry that can run the batch and keeps the fastest. RAW holds a line
-    longer than a span tile plus its halo, which the span kernel leaves to the general one: its geometries
-    are then reported untimed (-1). Without that line every geometry is timed."""
+    longer than a span tile plus its halo: the span kernel codes it in place (one lane, from memory), so its
+    geometries are timed too, with and without that line."""
     d, _ = dicts
     nv = zs.zs_kernel_variants(zs.OP_COMPRESS)
     span = {v for v in range(nv) if "span" in zs.zs_kernel_variant_name(zs.OP_COMPRESS, v)}
     assert span
-    for raws, exp, span_timed in ((RAW, expected, False), (RAW[:-2], expected[:-2], True)):
+    for raws, exp in ((RAW, expected), (RAW[:-2], expected[:-2])):
         shards, outs, idxs = _compress_shards(zs, raws)
         p = zs.Plan(d, zs.OP_COMPRESS, shards, flags=1, variant=-1, tune_reps=2)
         times = [p.tuned_ms(v) for v in range(nv)]
-        assert all(times[v] > 0 for v in range(nv) if v not in span)
-        assert all((times[v] > 0) == span_timed for v in span)
-        timed = {v: t for v, t in enumerate(times) if t > 0}
-        assert p.variant == min(timed, key=timed.get)
+        assert all(t > 0 for t in times), times
+        assert p.variant == min(range(nv), key=lambda v: times[v])
         _check_compressed(p.run(), shards, outs, idxs, exp)
         assert p.last_ms > 0
         p.close()
