@@ -51,6 +51,13 @@ int64_t injected_stall_tile()
     return -1;
 }
 
+int64_t span_cut_min_override()
+{
+    const char *v = getenv("ZS_SPAN_CUT_MIN");
+    if (v && *v) return atoll(v);
+    return -1;
+}
+
 ScratchPool::~ScratchPool() { release_all(); }
 
 void ScratchPool::release_all()

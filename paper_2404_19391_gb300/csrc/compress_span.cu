@@ -9,19 +9,28 @@
 //     one bit per byte marks the bytes pre-processing looks at (digits, '%', '[', ']', ' ', tab, '\n'),
 //     plus bytes >= 0x80 so that a tile holding any is known.
 //   - Spans: lane l owns the lines that start between two boundaries, each the line start closest to
-//     l / 32 of the tile, so every lane gets about 1/32 of the bytes whatever the line lengths.
-//   - Pre-processing: each lane walks only the token bits of its span; ring labels are rewritten in place
-//     when a ring closes (or opens, for the other reading), %nn labels shrink and the span is compacted.
+//     l / 32 of the tile, so every lane gets about 1/32 of the bytes whatever the line lengths. In geometries
+//     that enable it, a target inside a long line may take a reset point of that line instead (a position
+//     after a ring-bond token that leaves no ring open, found by all lanes at once over their own chunks with
+//     segmented scans), so one line can be shared by several lanes.
+//   - Pre-processing: each lane walks only the token bits of its span (digits inside bracket atoms masked
+//     out); ring labels are rewritten in place when a ring closes (or opens, for the other reading), %nn labels
+//     shrink (up to six open ones are followed in registers) and the span is compacted. Both relabelling rules
+//     restart exactly at a reset point, so the units of a cut line are relabelled independently.
 //   - Parse: the backward shortest-path scan is the minimal transducer of the dictionary, re-indexed by
 //     the raw byte: per byte one byte-permute builds (state << 8 | 2 * byte) and one 16-bit shared load
 //     gives the next state and the symbol chosen there. '\n' resets the state, so a whole span is one
-//     scan, and the chosen symbols overwrite the text in place.
+//     scan, and the chosen symbols overwrite the text in place. A span ending at a cut starts from a short
+//     read-ahead of the next span and is repaired from the true state (the next span's exit state) until the
+//     two scans meet.
 //   - Emission: a count walk over the chosen pieces gives each lane's output bytes, a warp scan places
 //     them, and a write walk stores them into a per-warp staging buffer (and the line starts into an
-//     index stage), which the finishing step copies out with aligned 16-byte stores.
-//   - Anything outside this fast path (a line that needs a label above 9, more open %nn labels than a lane
-//     follows, a line longer than tile + halo, an escape of an input byte in a compacted span) sets
-//     kStFallback, and the call is run again by the general kernel.
+//     index stage), which the finishing step copies out with aligned 16-byte stores. A span entered at a cut
+//     starts where the previous span's walk left off and joins its own speculative chain where they meet.
+//   - A line outside this fast path (a label above 9, more than six open %nn labels, longer than the stage)
+//     is coded alone by its lane in global scratch. A cut that cannot be kept makes the tile be coded again
+//     without cuts. Anything else (more such lines than a lane follows, an escaped input byte in a compacted
+//     span) sets kStFallback, and the call is run again by the general kernel.
 #include <algorithm>
 
 #include "compress_shared.cuh"
@@ -30,8 +39,9 @@ namespace zs {
 namespace {
 using namespace cx;
 
-template <int W, int TB, int HB, int OUTB, int MAXL>
+template <int W, int TB, int HB, int OUTB, int MAXL, bool CUT>
 struct SpGeom {
+    static constexpr bool kCut = CUT;   // long lines are cut between lanes by default
     static constexpr int kWarps = W;    // warps per CTA (one CTA per SM)
     static constexpr int kTile = TB;    // owned input bytes per warp tile
     static constexpr int kHalo = HB;    // bytes staged past the tile for its last line
@@ -42,7 +52,7 @@ struct SpGeom {
 constexpr unsigned kAll = 0xffffffffu;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint8_t kDel = 0xFF;           // a deleted byte (digits of a rewritten %nn label); never staged text
-constexpr uint32_t kOpen2 = 4;           // open %nn labels (>= 10) a lane follows
+constexpr uint32_t kOpen2 = 6;           // open %nn labels (>= 10) a lane follows (in registers)
 constexpr uint32_t kChEscDigit = 0x10;   // choice 0x10 + d: escape of the (new) digit d
 constexpr uint32_t kChEsc = 0x20;        // choice ' ': escape of the input byte at that position
 constexpr uint32_t kPosBits = 13, kPosMask = (1u << kPosBits) - 1u;  // emission walks: position | out bytes << 13
@@ -69,6 +79,8 @@ struct SpArgs {
     uint64_t slow_cap;
     uint64_t limit_ns;
     int64_t stall_tile;
+    uint32_t cut_min;     // lines this long (or longer) may be cut between lanes at reset points; 0: never
+    uint32_t cut_slack;   // a lane takes a cut only if its target is farther than this from a line start
 };
 
 // Per-byte SIMD classification (bytes of a 32-bit word; the high bit of each result byte is the answer).
@@ -154,8 +166,8 @@ struct SP {
         uint32_t dmask[kMaskWords];  // digits and '%'
         uint32_t omask[kMaskWords];  // '[', and ' ' tab
         uint32_t cmask[kMaskWords];  // ']', and ' ' tab (a byte in both masks always makes an exception)
-        uint16_t ring[(20 + 2 * kOpen2) * 32];  // per lane (entry k of lane l at [k * 32 + l]): open positions
-                                                 // of labels 0-9, latest closes of new labels 0-9, open %nn
+        uint16_t ring[20 * 32];  // per lane (entry k of lane l at [k * 32 + l]): open positions of labels 0-9,
+                                  // latest closes of new labels 0-9
         OutSlot os[2];
         uint64_t bar;
         uint32_t high;  // the staged tile holds a byte >= 0x80
@@ -266,12 +278,174 @@ struct SP {
         uint32_t a, b;      // this lane's lines: staged positions [a, b)
         uint32_t B0, B32;   // the tile's lines: [B0, B32)
         bool long_last;     // the tile's last line runs past the staged bytes
+        bool cut_a, cut_b;  // the span starts (ends) inside a line, at a reset point
     };
+
+    // ---- cuts inside long lines ---------------------------------------------------------------------------
+    // A reset point is the position just after a ring-bond token (outside bracket atoms, before any space or
+    // tab) that leaves no ring open. Both relabelling rules restart there exactly: every earlier ring has closed
+    // before any later one opens, so all labels are free again (closing order), or none is held (opening
+    // order). A long line can therefore be relabelled in independent units cut at reset points; the parse and
+    // the emission walks are mended at each cut afterwards (their state does not restart there).
+    static constexpr uint32_t kSync = 20;               // bytes recorded at a cut for the parse repair
+    static constexpr uint32_t kLook = 12;               // bytes of the next span read ahead at a cut
+
+    // Ring-token bits of word w within keep: digits and '%' outside bracket atoms and before the first space or
+    // tab of their line, given the state at the word's start (inb: inside an atom, fd: past the field), which is
+    // advanced to the last kept bit (a newline starts both afresh). The bracket state is the parity of the
+    // bracket bytes since the line start; a malformed line only misplaces cuts, which the relabelling catches.
+    static __device__ __forceinline__ uint32_t ring_tokens(const WarpMem &M, uint32_t w, uint32_t keep, uint32_t &inb,
+                                                           uint32_t &fd)
+    {
+        const uint32_t om = M.omask[w] & keep, cm = M.cmask[w] & keep;
+        const uint32_t sp = om & cm, t = (om | cm) & ~sp, d = M.dmask[w] & keep;
+        uint32_t nl = M.nmask[w] & keep, rest = keep, toks = 0;
+        while (rest) {
+            const uint32_t seg = nl ? rest & ((nl & (0u - nl)) * 2u - 1u) : rest;  // up to the next newline
+            const uint32_t ss = sp & seg;
+            const uint32_t px = (prefix_xor(t & seg) ^ (0u - inb)) & seg;
+            uint32_t live = fd ? 0u : seg;
+            if (ss) live &= (ss & (0u - ss)) - 1u;
+            toks |= d & live & ~px;
+            if (!nl) {
+                inb = (px >> (31 - __clz(seg))) & 1u;
+                fd |= ss != 0;
+                break;
+            }
+            rest &= ~seg;
+            nl &= nl - 1u;
+            inb = fd = 0;
+        }
+        return toks;
+    }
+
+    // Walk over the ring tokens and newlines of the chunk [c0, c1) from the given state: label parities P (bit
+    // label % 32 of P[label / 32]) and open rings, restarted at each newline. FIND: note the first and last reset
+    // points reached. *nl: the chunk holds a newline. skip_to: the two digits of a %nn that starts before c0.
+    template <bool FIND>
+    static __device__ __forceinline__ void chunk_walk(const WarpMem &M, uint32_t c0, uint32_t c1, uint32_t inb,
+                                                      uint32_t fd, uint32_t skip_to, uint32_t P[4], uint32_t &open,
+                                                      bool *nl, uint32_t *first, uint32_t *last)
+    {
+        for (uint32_t w = c0 >> 5; (w << 5) < c1; ++w) {
+            uint32_t keep = kAll;
+            if ((w << 5) < c0) keep &= kAll << (c0 & 31);
+            if (((w + 1) << 5) > c1) keep &= (1u << (c1 & 31)) - 1u;
+            const uint32_t n = M.nmask[w] & keep;
+            uint32_t ev = ring_tokens(M, w, keep, inb, fd) | n;
+            while (ev) {
+                const uint32_t b = (uint32_t)(__ffs(ev) - 1), p = (w << 5) + b;
+                ev &= ev - 1u;
+                if ((n >> b) & 1u) {
+                    P[0] = P[1] = P[2] = P[3] = 0;
+                    open = 0;
+                    skip_to = 0;
+                    *nl = true;
+                    continue;
+                }
+                if (p < skip_to) continue;
+                const uint32_t ch = M.text[p];
+                uint32_t label, end;
+                if (ch == '%') {
+                    const uint32_t d1 = (uint32_t)M.text[p + 1] - '0', d2 = (uint32_t)M.text[p + 2] - '0';
+                    if (d1 > 9 || d2 > 9) continue;  // a bad %: the relabelling finds the line invalid
+                    label = d1 * 10 + d2;
+                    end = p + 3;
+                    skip_to = end;
+                } else {
+                    label = ch - '0';
+                    end = p + 1;
+                }
+                const uint32_t bit = 1u << (label & 31), q = label >> 5;
+                const uint32_t was = (q == 0 ? P[0] : q == 1 ? P[1] : q == 2 ? P[2] : P[3]) & bit;
+                P[0] ^= q == 0 ? bit : 0u;
+                P[1] ^= q == 1 ? bit : 0u;
+                P[2] ^= q == 2 ? bit : 0u;
+                P[3] ^= q == 3 ? bit : 0u;
+                open = was ? open - 1u : open + 1u;
+                if (FIND && open == 0) {
+                    if (*first == kNone) *first = end;
+                    *last = end;
+                }
+            }
+        }
+    }
+
+    // Reset points near the lane targets, all lanes at once. Lane l takes the chunk [c0, c1) between its target
+    // and the next one. A first pass gives each chunk's effect on the bracket and field state of its last line,
+    // a segmented scan over the lanes (a newline ends a segment) the state at each chunk's start; a second pass
+    // and scan do the same for the label parities; a third pass finds the reset points of the chunk. *first and
+    // *last: the first and last reset points reached in the chunk (kNone: none).
+    static __device__ void chunk_resets(const Ctx &C, uint32_t c0, uint32_t c1, uint32_t *first, uint32_t *last)
+    {
+        const WarpMem &M = *C.M;
+        const uint32_t lane = C.lane;
+        c1 = max(c0, c1);
+        // pass 1: bracket and field state
+        uint32_t inb = 0, fd = 0;
+        bool nl = false;
+        for (uint32_t w = c0 >> 5; (w << 5) < c1; ++w) {
+            uint32_t keep = kAll;
+            if ((w << 5) < c0) keep &= kAll << (c0 & 31);
+            if (((w + 1) << 5) > c1) keep &= (1u << (c1 & 31)) - 1u;
+            nl |= (M.nmask[w] & keep) != 0;
+            ring_tokens(M, w, keep, inb, fd);
+        }
+        uint32_t f = nl ? 1u : 0u;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {  // inclusive segmented scan
+            const uint32_t i2 = __shfl_up_sync(kAll, inb, k), f2 = __shfl_up_sync(kAll, fd, k);
+            const uint32_t g2 = __shfl_up_sync(kAll, f, k);
+            if ((int)lane >= k && !f) {
+                inb ^= i2;
+                fd |= f2;
+            }
+            if ((int)lane >= k) f |= g2;
+        }
+        uint32_t inb0 = __shfl_up_sync(kAll, inb, 1), fd0 = __shfl_up_sync(kAll, fd, 1);
+        if (lane == 0) inb0 = fd0 = 0;
+        // the two digits of a %nn whose '%' lies just before the chunk belong to the previous lane's token
+        uint32_t skip_to = 0;
+        if (!inb0 && !fd0) {
+            if (M.text[c0 - 1] == '%') skip_to = c0 + 2;
+            else if (M.text[c0 - 2] == '%' && (uint32_t)(M.text[c0 - 1] - '0') <= 9u) skip_to = c0 + 1;
+        }
+        // pass 2: label parities
+        uint32_t P[4] = {0, 0, 0, 0}, open = 0, dummy = kNone;
+        bool nl2 = false;
+        chunk_walk<false>(M, c0, c1, inb0, fd0, skip_to, P, open, &nl2, &dummy, &dummy);
+        f = nl2 ? 1u : 0u;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            uint32_t q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = __shfl_up_sync(kAll, P[j], k);
+            const uint32_t g2 = __shfl_up_sync(kAll, f, k);
+            if ((int)lane >= k && !f) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) P[j] ^= q[j];
+            }
+            if ((int)lane >= k) f |= g2;
+        }
+        uint32_t P0[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            P0[j] = __shfl_up_sync(kAll, P[j], 1);
+            if (lane == 0) P0[j] = 0;
+        }
+        // pass 3: the reset points
+        open = (uint32_t)(__popc(P0[0]) + __popc(P0[1]) + __popc(P0[2]) + __popc(P0[3]));
+        *first = *last = kNone;
+        bool nl3 = false;
+        chunk_walk<true>(M, c0, c1, inb0, fd0, skip_to, P0, open, &nl3, first, last);
+    }
 
     // Tile segmentation and span boundaries. Line starts owned by the tile are staged positions
     // [16, 16 + nown) preceded by '\n'. Lane l's first line is the line start closest to 16 + l * nown / 32.
+    // With cut_min > 0, a target inside a line of at least cut_min bytes (ending in the stage) may instead take
+    // the closest reset point of that line; an inclusive max over the lanes keeps the boundaries in order.
     static __device__ __forceinline__ Span spans(const Ctx &C, uint64_t t, uint32_t nown, uint32_t stage_end,
-                                                 bool stream_end_staged)
+                                                 bool stream_end_staged, uint32_t cut_min)
     {
         const WarpMem &M = *C.M;
         const uint32_t lane = C.lane;
@@ -287,6 +461,7 @@ struct SP {
         if (B0 == kNone) {  // no line starts in this tile
             s.a = s.b = s.B0 = s.B32 = 16;
             s.long_last = false;
+            s.cut_a = s.cut_b = false;
             return s;
         }
         if (lane == 31) {
@@ -301,14 +476,48 @@ struct SP {
         B32 = __shfl_sync(kAll, B32, 31);
         long_last = __shfl_sync(kAll, long_last, 31);
         uint32_t Bl = B0;
+        const uint32_t target = 16u + (uint32_t)(((uint64_t)lane * nown) >> 5);
+        bool want = false;
+        uint32_t sm = kNone, sp = B32, le = kNone;
         if (lane > 0) {
-            const uint32_t target = 16u + (uint32_t)(((uint64_t)lane * nown) >> 5);
             const uint32_t qm = prev_nl(M, target, B0 - 1u);
             const uint32_t qp = next_nl(M, target - 1u, own_nl);
-            const uint32_t sm = qm == kNone ? kNone : qm + 1;
-            const uint32_t sp = qp == kNone ? B32 : qp + 1;
+            sm = qm == kNone ? kNone : qm + 1;
+            sp = qp == kNone ? B32 : qp + 1;
             Bl = (sm != kNone && target - sm <= sp - target) ? sm : sp;
-            Bl = min(max(Bl, B0), B32);
+            // the target's line is [sm, le), le its '\n' (or the end of the data)
+            le = qp;
+            if (le == kNone) le = long_last ? kNone : (M.text[B32 - 1] == kNl ? B32 - 1u : B32);
+            want = cut_min && sm != kNone && le != kNone && sm < target && target < sp && le - sm >= cut_min &&
+                   min(target - sm, sp - target) > C.P->cut_slack;
+        }
+        if (__any_sync(kAll, want)) {
+            const uint32_t tn = __shfl_down_sync(kAll, target, 1);  // every lane takes part in the shuffle
+            const uint32_t c1 = lane == 31 ? 16u + nown : tn;
+            uint32_t first, last;
+            chunk_resets(C, lane == 0 ? 16u : target, min(c1, 16u + nown), &first, &last);
+            const uint32_t rl = __shfl_up_sync(kAll, last, 1);  // the previous chunk's last reset point
+            if (want) {
+                uint32_t best = Bl, bd = Bl > target ? Bl - target : target - Bl;
+                if (rl != kNone && rl > sm && rl < le) {
+                    const uint32_t d = rl > target ? rl - target : target - rl;
+                    if (d < bd || (d == bd && rl < best)) {
+                        best = rl;
+                        bd = d;
+                    }
+                }
+                if (first != kNone && first > sm && first < le) {
+                    const uint32_t d = first - target;
+                    if (d < bd || (d == bd && first < best)) best = first;
+                }
+                Bl = best;
+            }
+        }
+        if (lane > 0) Bl = min(max(Bl, B0), B32);
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const uint32_t v = __shfl_up_sync(kAll, Bl, k);
+            if ((int)lane >= k) Bl = max(Bl, v);
         }
         uint32_t Bn = __shfl_down_sync(kAll, Bl, 1);
         if (lane == 31) Bn = B32;
@@ -317,6 +526,8 @@ struct SP {
         s.B0 = B0;
         s.B32 = B32;
         s.long_last = long_last;
+        s.cut_a = Bl < B32 && M.text[Bl - 1] != kNl;
+        s.cut_b = __shfl_down_sync(kAll, s.cut_a, 1) && lane < 31;
         return s;
     }
 
@@ -432,6 +643,42 @@ struct SP {
     }
 
     // ---- pre-processing ---------------------------------------------------------------------------------
+    // Open %nn labels (>= 10) of the current line, in registers: slot j holds (label + 1) << 16 | (open position
+    // + 1) with bit 15 set (the open token is a written %nn), or 0 when free.
+    static constexpr uint32_t kNoSlot = 0xFFu;
+    struct OpenPct {
+        uint32_t s[kOpen2];
+        __device__ __forceinline__ void clear()
+        {
+#pragma unroll
+            for (int j = 0; j < (int)kOpen2; ++j) s[j] = 0;
+        }
+        // The open entry of label, its slot freed; 0 if label is not open.
+        __device__ __forceinline__ uint32_t take(uint32_t label)
+        {
+            uint32_t e = 0;
+#pragma unroll
+            for (int j = 0; j < (int)kOpen2; ++j)
+                if ((s[j] >> 16) == label + 1u) {
+                    e = s[j] & 0xFFFFu;
+                    s[j] = 0;
+                }
+            return e;
+        }
+        // Records label as opened at position q; false if every slot is taken.
+        __device__ __forceinline__ bool put(uint32_t label, uint32_t q)
+        {
+            bool done = false;
+#pragma unroll
+            for (int j = 0; j < (int)kOpen2; ++j)
+                if (!done && s[j] == 0) {
+                    s[j] = ((label + 1u) << 16) | (q + 1u) | 0x8000u;
+                    done = true;
+                }
+            return done;
+        }
+    };
+
     // Walks the token bits of the lane's span [a, b) line by line and relabels ring IDs in place (closing
     // order by default: a ring takes, when it closes, the smallest label whose latest ring closed before this
     // one opened; opening order with OUTER: a ring takes, when it opens, the smallest label no open ring
@@ -441,7 +688,7 @@ struct SP {
     // *shifted = some line was compacted; *fallback = a line needs the general kernel.
     static __device__ uint32_t relabel_general(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
                                                uint32_t *lines_out, bool *shifted, bool last_slow, Slow &SL,
-                                               bool *fallback)
+                                               bool *fallback, uint32_t cutf, bool *retry)
     {
         WarpMem &M = *C.M;
         uint8_t *text = M.text;
@@ -453,9 +700,15 @@ struct SP {
         uint32_t ls = a;  // line start (original positions)
         uint32_t dopen = 0, lcv = 0, held = 0, nopen2 = 0, skip_to = 0;
         bool in_br = false, field_done = false, bad = false, any_pct = false, wrote = false, slow = false;
+        bool rt = false;
+        OpenPct op;
+        op.clear();
         auto finish_line = [&](uint32_t le) {  // le: the line's end (its '\n' or the span end), original
             const uint32_t cls = ls - shift, cle = le - shift;
-            if (slow || (last_slow && le == b)) {  // coded alone; its bytes here are skipped
+            const bool split = ((cutf & 1u) && ls == a) || ((cutf & 2u) && le == b);  // a unit of a cut line
+            if (split && (slow || bad || in_br || dopen != 0 || nopen2 != 0)) {
+                rt = true;  // a cut line the units cannot code alone: the tile is coded again without cuts
+            } else if (slow || (last_slow && le == b)) {  // coded alone; its bytes here are skipped
                 if (!add_slow(SL, cls, cle, ls, last_slow && le == b)) fb = true;
             } else if (wrote && (bad || in_br || dopen != 0 || nopen2 != 0)) {  // left as it is
                 for (uint32_t k = cls; k < cle; ++k) text[k] = raw[k + shift];
@@ -472,13 +725,11 @@ struct SP {
             }
             ++lines;
             ls = le + 1;
-            if (nopen2 != 0)
-                for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
+            op.clear();
             dopen = lcv = held = nopen2 = 0;
             skip_to = 0;
             in_br = field_done = bad = any_pct = wrote = slow = false;
         };
-        for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
         if (a < b) {
             uint32_t w = a >> 5;
             uint32_t bits = (M.nmask[w] | M.dmask[w] | M.omask[w] | M.cmask[w]) & (kAll << (a & 31));
@@ -534,20 +785,11 @@ struct SP {
                     if ((dopen >> label) & 1u) open_e = ring[32 * label];
                     dopen ^= 1u << label;
                 } else {
-                    int hit = -1, empty = -1;
-#pragma unroll
-                    for (int j = 0; j < (int)kOpen2; ++j) {
-                        const uint32_t v = ring[32 * (20 + 2 * j)];
-                        if (v == label + 1) hit = j;
-                        if (v == 0 && empty < 0) empty = j;
-                    }
-                    if (hit >= 0) {
-                        open_e = ring[32 * (21 + 2 * hit)];
-                        ring[32 * (20 + 2 * hit)] = 0;
+                    open_e = op.take(label);
+                    if (open_e) {
                         --nopen2;
-                    } else if (empty >= 0) {
-                        ring[32 * (20 + 2 * empty)] = (uint16_t)(label + 1);
-                        oslot = 21u + 2u * (uint32_t)empty;
+                    } else if (op.put(label, q)) {
+                        oslot = kNoSlot;
                         ++nopen2;
                     } else {
                         slow = true;  // more open %nn labels than the lane follows
@@ -565,14 +807,14 @@ struct SP {
                         }
                         nl = (uint32_t)__ffs(fr) - 1u;
                         held |= 1u << nl;
-                        ring[32 * oslot] = (uint16_t)((q + 1) | (pct ? 0x8000u : 0u));
+                        if (oslot != kNoSlot) ring[32 * oslot] = (uint16_t)((q + 1) | (pct ? 0x8000u : 0u));
                     } else {
                         nl = (uint32_t)text[(open_e & 0x7FFFu) - 1u] - '0';
                         held &= ~(1u << nl);
                     }
                 } else {
                     if (opening) {
-                        ring[32 * oslot] = (uint16_t)((q + 1) | (pct ? 0x8000u : 0u));
+                        if (oslot != kNoSlot) ring[32 * oslot] = (uint16_t)((q + 1) | (pct ? 0x8000u : 0u));
                         continue;
                     }
                     const uint32_t o = (open_e & 0x7FFFu) - 1u;  // position of the open token
@@ -605,18 +847,19 @@ struct SP {
                 wrote = true;
             }
         }
-        if (ls < b) finish_line(b);  // the stream's last line, without '\n'
+        if (ls < b) finish_line(b);  // the stream's last line, without '\n' (or a unit ending at a cut)
         *lines_out = lines;
         *shifted = shift != 0;
         *fallback = fb;
+        *retry = rt;
         return b - shift;
     }
 
     // Whether the span [a, b) can take the fast relabelling: no space or tab (a second field), and every
-    // bracket atom opens and closes within its line, without nesting and without a digit or '%' inside. Bit
-    // arithmetic over the class masks, one 32-bit word at a time: the prefix XOR of the bracket bits is 1 from
-    // a '[' up to its ']'. Space and tab are in both bracket masks, so each one is a '[' inside an atom or a ']'
-    // outside one.
+    // bracket atom opens and closes within its line, without nesting. Bit arithmetic over the class masks, one
+    // 32-bit word at a time: the prefix XOR of the bracket bits is 1 from a '[' up to its ']'. Space and tab are
+    // in both bracket masks, so each one is a '[' inside an atom or a ']' outside one. Digits inside an atom
+    // (isotopes, charges, H counts) are not ring labels; the fast relabelling masks them out the same way.
     static __device__ __forceinline__ bool exception_free(const WarpMem &M, uint32_t a, uint32_t b)
     {
         uint32_t in = 0;  // inside a bracket atom at the start of the word
@@ -632,7 +875,6 @@ struct SP {
             bad |= (o & before)                              // '[' inside a bracket atom
                    | (c & ~before)                           // ']' outside one (space, tab: always one of
                                                              //  the two, being in both masks)
-                   | (M.dmask[w] & keep & px & ~t)           // a digit inside one
                    | (M.nmask[w] & keep & px);               // a line ending inside one
             in = (px >> 31) & 1u;
         }
@@ -654,25 +896,30 @@ struct SP {
         }
     }
 
-    // Relabelling of an exception-free span: only the digit bits are visited, all of them ring labels. Labels
+    // Relabelling of an exception-free span: only the digit bits outside bracket atoms (all of them ring labels)
+    // and the newlines are visited. Labels
     // of a line are decided as in relabel_general; the latest close of each new label is kept in 16-bit
     // halves of five registers (label x in register x % 5, high half for x >= 5), so finding the smallest
     // label free since the ring opened is five subtractions and one find-first-set, without branches.
     static __device__ __forceinline__ uint32_t relabel_fast(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
-                                                            bool last_slow, Slow &SL, bool *shifted, bool *fallback)
+                                                            bool last_slow, Slow &SL, bool *shifted, bool *fallback,
+                                                            uint32_t cutf, bool *retry)
     {
         WarpMem &M = *C.M;
         uint8_t *text = M.text;
-        // ring[32 * d]: open position + 1 of digit label d (bit 15: written %0d); ring[32 * (20 + 2 j)]: label + 1
-        // of open %nn slot j, ring[32 * (21 + 2 j)]: its open position + 1 (bit 15 set)
+        // ring[32 * d]: open position + 1 of digit label d (bit 15: written %0d); op: the open %nn labels
         uint16_t *ring = M.ring + C.lane;
         uint32_t ls = a, dopen = 0, held = 0, nopen2 = 0, skip_to = 0, shift = 0;
         uint32_t L0 = 0, L1 = 0, L2 = 0, L3 = 0, L4 = 0;
-        bool fb = false, slow = false, bad = false, any_pct = false;
-        for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
+        bool fb = false, slow = false, bad = false, any_pct = false, rt = false;
+        OpenPct op;
+        op.clear();
         auto end_line = [&](uint32_t le) {  // le: the line's end (its '\n' or b), an original position
             const uint32_t cls = ls - shift, cle = le - shift;
-            if (slow || (last_slow && le == b)) {  // coded alone; its bytes here are skipped
+            const bool split = ((cutf & 1u) && ls == a) || ((cutf & 2u) && le == b);  // a unit of a cut line
+            if (split && (slow || bad || dopen != 0 || nopen2 != 0)) {
+                rt = true;  // a cut line the units cannot code alone: the tile is coded again without cuts
+            } else if (slow || (last_slow && le == b)) {  // coded alone; its bytes here are skipped
                 if (!add_slow(SL, cls, cle, ls, last_slow && le == b)) fb = true;
             } else if (bad || dopen != 0 || nopen2 != 0) {  // an unclosed ring or a bad %: left as it is
                 restore_digits(M, text, raw, ls, le, shift);
@@ -686,20 +933,28 @@ struct SP {
                 for (uint32_t r = cle; r < bend; ++r) text[r - d] = text[r];
                 shift += d;
             }
-            if (nopen2)
-                for (uint32_t j = 0; j < kOpen2; ++j) ring[32 * (20 + 2 * j)] = 0;
+            op.clear();
             dopen = held = nopen2 = 0;
             L0 = L1 = L2 = L3 = L4 = 0;
             slow = bad = any_pct = false;
             skip_to = 0;
         };
+        // token bits of word w: newlines, and digits and '%' outside bracket atoms (inb: inside one at the
+        // word's start; the span is exception-free, so the bracket masks hold only '[' and ']')
+        uint32_t inb = 0;
+        auto word_tokens = [&](uint32_t w, uint32_t keep) -> uint32_t {
+            const uint32_t t = (M.omask[w] | M.cmask[w]) & keep;
+            const uint32_t px = prefix_xor(t) ^ (0u - inb);
+            inb = px >> 31;
+            return ((M.dmask[w] & ~px) | M.nmask[w]) & keep;
+        };
         uint32_t w = a >> 5;
-        uint32_t bits = (M.dmask[w] | M.nmask[w]) & (kAll << (a & 31));
+        uint32_t bits = word_tokens(w, kAll << (a & 31));
         for (;;) {
             while (bits == 0) {
                 ++w;
                 if ((w << 5) >= b) break;
-                bits = M.dmask[w] | M.nmask[w];
+                bits = word_tokens(w, kAll);
             }
             if (bits == 0) break;
             const uint32_t p = (w << 5) + (uint32_t)(__ffs(bits) - 1);
@@ -732,20 +987,11 @@ struct SP {
                 if ((dopen >> label) & 1u) open_e = ring[32 * label];
                 dopen ^= 1u << label;
             } else {
-                int hit = -1, empty = -1;
-#pragma unroll
-                for (int j = 0; j < (int)kOpen2; ++j) {
-                    const uint32_t v = ring[32 * (20 + 2 * j)];
-                    if (v == label + 1) hit = j;
-                    if (v == 0 && empty < 0) empty = j;
-                }
-                if (hit >= 0) {
-                    open_e = ring[32 * (21 + 2 * hit)];
-                    ring[32 * (20 + 2 * hit)] = 0;
+                open_e = op.take(label);
+                if (open_e) {
                     --nopen2;
-                } else if (empty >= 0) {
-                    ring[32 * (20 + 2 * empty)] = (uint16_t)(label + 1);
-                    oslot = 21u + 2u * (uint32_t)empty;
+                } else if (op.put(label, q)) {
+                    oslot = kNoSlot;
                     ++nopen2;
                 } else {  // more open %nn labels than the lane follows: the line is coded alone
                     slow = true;
@@ -754,7 +1000,7 @@ struct SP {
             }
             uint32_t nl;
             if (open_e == 0) {  // opens a ring
-                ring[32 * oslot] = (uint16_t)((q + 1u) | (pct ? 0x8000u : 0u));
+                if (oslot != kNoSlot) ring[32 * oslot] = (uint16_t)((q + 1u) | (pct ? 0x8000u : 0u));
                 if (!OUTER) continue;
                 const uint32_t fr = ~held & 0x3FFu;
                 if (fr == 0) {  // would need a two-digit label
@@ -800,22 +1046,26 @@ struct SP {
                 any_pct = true;
             }
         }
-        if (ls < b) end_line(b);  // the span's last line has no '\n' here
+        if (ls < b) end_line(b);  // the span's last line has no '\n' here (or is a unit ending at a cut)
         *shifted = shift != 0;
         *fallback = fb;
+        *retry = rt;
         return b - shift;
     }
 
     // Pre-processing of the lane's span (Sec. IV-A): the fast relabelling when the span allows it, else the
-    // general walk. Returns the span's end after compaction; *lines = lines in the span.
+    // general walk. Returns the span's end after compaction; *lines = lines starting in the span (a span that
+    // starts at a cut continues the previous lane's line). cutf: bit 0 the span starts at a cut, bit 1 it ends
+    // at one; *retry: a unit of a cut line needs what only a whole line can have.
     static __device__ __forceinline__ uint32_t preprocess(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
-                                                          bool last_slow, uint32_t *lines, bool *shifted, Slow &SL,
-                                                          bool *fallback)
+                                                          bool last_slow, uint32_t cutf, uint32_t *lines,
+                                                          bool *shifted, Slow &SL, bool *fallback, bool *retry)
     {
         const WarpMem &M = *C.M;
-        *lines = a < b ? count_bits(M.nmask, a, b) + (M.text[b - 1] != kNl ? 1u : 0u) : 0u;
+        *lines = a < b ? count_bits(M.nmask, a, b) + (M.text[b - 1] != kNl ? 1u : 0u) - (cutf & 1u) : 0u;
         *shifted = false;
         *fallback = false;
+        *retry = false;
         SL.n = 0;
         SL.past = 0;
         if (a >= b) return b;
@@ -827,9 +1077,9 @@ struct SP {
             }
             return b;
         }
-        if (exception_free(M, a, b)) return relabel_fast(C, a, b, raw, last_slow, SL, shifted, fallback);
+        if (exception_free(M, a, b)) return relabel_fast(C, a, b, raw, last_slow, SL, shifted, fallback, cutf, retry);
         uint32_t l2 = 0;
-        return relabel_general(C, a, b, raw, &l2, shifted, last_slow, SL, fallback);
+        return relabel_general(C, a, b, raw, &l2, shifted, last_slow, SL, fallback, cutf, retry);
     }
 
     // ---- parse ------------------------------------------------------------------------------------------
@@ -841,17 +1091,26 @@ struct SP {
     }
 
     // Backward scan of the lane's span [a, e): each byte is replaced by the choice made there. HIGH: the tile
-    // holds bytes >= 0x80, which read the column of rep_col (they match no pattern).
+    // holds bytes >= 0x80, which read the column of rep_col (they match no pattern). Returns the last table
+    // entry (the state at a in its low byte). rec (a span ending at a cut, where the scan starts from the start
+    // state on speculation): the first kSync bytes scanned and the state after each, as byte | state << 8.
     template <bool HIGH>
-    static __device__ __forceinline__ void parse(const Ctx &C, uint32_t a, uint32_t e)
+    static __device__ __forceinline__ uint32_t parse(const Ctx &C, uint32_t a, uint32_t e, uint16_t *rec, uint32_t st)
     {
         uint8_t *text = C.M->text;
         const uint8_t *tab = C.tab;
         const uint32_t rep = C.P->rep_col;
-        uint32_t st = C.P->q0;
         int32_t p = (int32_t)e - 1;
         const int32_t lo = (int32_t)a;
         auto col = [&](uint32_t b) -> uint32_t { return (HIGH && b >= 0x80u) ? rep : (b << 1); };
+        if (rec) {
+            for (uint32_t k = 0; k < kSync && p >= lo; ++k, --p) {
+                const uint32_t b = text[p];
+                st = look(tab, st, col(b), 0x3204);
+                text[p] = (uint8_t)(st >> 8);
+                rec[32 * k] = (uint16_t)(b | (st << 8));
+            }
+        }
         while (p >= lo && ((p + 1) & 3) != 0) {
             st = look(tab, st, col(text[p]), 0x3204);
             text[p] = (uint8_t)(st >> 8);
@@ -885,17 +1144,77 @@ struct SP {
             text[p] = (uint8_t)(st >> 8);
             --p;
         }
+        return st;
+    }
+
+    // State at a cut, read ahead from the bytes [b0, lim) that follow it (the start of the next span): exact if
+    // they hold a newline (the scan starts there), else a guess that the repair below checks.
+    template <bool HIGH>
+    static __device__ __forceinline__ uint32_t lookahead(const Ctx &C, uint32_t b0, uint32_t lim)
+    {
+        const uint8_t *text = C.M->text;
+        const uint32_t rep = C.P->rep_col;
+        for (uint32_t p = b0; p < lim; ++p)
+            if (text[p] == kNl) {
+                lim = p + 1;
+                break;
+            }
+        uint32_t st = C.P->q0;
+        for (uint32_t p = lim; p-- > b0;) {
+            const uint32_t b = text[p];
+            st = look(C.tab, st, (HIGH && b >= 0x80u) ? rep : (b << 1), 0x3204);
+        }
+        return st;
+    }
+
+    // Repair of a span that ends at a cut: the recorded bytes are scanned again from the true state there (the
+    // state the next span's scan reached at its start), rewriting their choices, until the state meets the one
+    // the speculative scan had at the same byte; from there on the two scans agree. lo: the start of the scan
+    // that ends at the cut. Returns false if they do not meet within the recorded bytes.
+    template <bool HIGH>
+    static __device__ bool repair_parse(const Ctx &C, uint32_t e, uint32_t lo, uint32_t st, const uint16_t *rec)
+    {
+        uint8_t *text = C.M->text;
+        const uint8_t *tab = C.tab;
+        const uint32_t rep = C.P->rep_col;
+        int32_t p = (int32_t)e - 1;
+        for (uint32_t k = 0; k < kSync && p >= (int32_t)lo; ++k, --p) {
+            const uint32_t r = rec[32 * k];
+            const uint32_t b = r & 0xFFu;
+            st = look(tab, st, (HIGH && b >= 0x80u) ? rep : (b << 1), 0x3204);
+            text[p] = (uint8_t)(st >> 8);
+            if ((st & 0xFFu) == (r >> 8)) return true;
+        }
+        return false;
     }
 
     // ---- emission ---------------------------------------------------------------------------------------
-    // Output bytes of the pieces chosen along the span [a, e) (position in bits 0-12 of the walk, output
-    // bytes above). *gen_esc: an escape of an input byte was chosen.
-    static __device__ __forceinline__ uint32_t count_out(const Ctx &C, uint32_t a, uint32_t e, bool check, bool *gen_esc)
+    // Walk over the pieces chosen along [a, e): returns position | output bytes << 13 after the last piece (the
+    // position may lie past e, inside the piece that crosses it). *gen_esc: an escape of an input byte was chosen.
+    // head (a span starting at a cut, entered on speculation): *V gets bit r for each of the first 64 positions
+    // a + r where a piece starts, *E2 bit r where that piece emits two bytes.
+    static __device__ __forceinline__ uint32_t count_out(const Ctx &C, uint32_t a, uint32_t e, bool check, bool *gen_esc,
+                                                         bool head = false, uint64_t *V = nullptr, uint64_t *E2 = nullptr)
     {
         const uint8_t *text = C.M->text;
         const uint32_t *meta = C.meta;
         uint32_t acc = a;
         bool ge = false;
+        if (head) {
+            uint64_t v = 0, e2 = 0;
+            while ((acc & kPosMask) < e) {
+                const uint32_t pos = acc & kPosMask, r = pos - a;
+                if (r >= 64) break;
+                const uint32_t c = text[pos];
+                const uint32_t m = meta[c];
+                v |= 1ull << r;
+                e2 |= (uint64_t)((m >> kPosBits) == 2u) << r;
+                ge |= c == kChEsc;
+                acc += m;
+            }
+            *V = v;
+            *E2 = e2;
+        }
         if (!check) {
             while ((acc & kPosMask) < e) acc += meta[text[acc & kPosMask]];
         } else {
@@ -906,7 +1225,7 @@ struct SP {
             }
         }
         *gen_esc = ge;
-        return acc >> kPosBits;
+        return acc;
     }
 
     struct SmemOut {
@@ -960,34 +1279,48 @@ struct SP {
     // ---- one tile -----------------------------------------------------------------------------------------
     struct Enc {
         uint32_t a, e;      // the lane's span after pre-processing
+        uint32_t entry;     // where its first piece starts (past a for a span entered at a cut)
         uint32_t off;       // its output offset within the tile
-        uint32_t rank;      // its first line within the tile
+        uint32_t rank;      // the line its first piece belongs to, within the tile
         uint32_t total, lines;
+        bool retry;         // a cut could not be kept: the tile is staged and coded again without cuts
         Slow sl;            // its lines coded one at a time (skipped by the walks over the span)
     };
 
-    // The walks over the lane's span, around its slow lines: parse, output bytes, writes.
+    // The walks over the lane's span, around its slow lines: parse (returns the span's exit state, the state
+    // at its start), output bytes, writes.
     template <bool HIGH>
-    static __device__ __forceinline__ void parse_all(const Ctx &C, const Enc &E)
+    static __device__ __forceinline__ uint32_t parse_all(const Ctx &C, const Enc &E, uint16_t *rec, uint32_t st0)
     {
-        uint32_t p = E.a;
+        uint32_t p = E.a, x = 0;
         for (uint32_t k = 0; k < E.sl.n; ++k) {
-            parse<HIGH>(C, p, E.sl.a[k]);
+            const uint32_t st = parse<HIGH>(C, p, E.sl.a[k], nullptr, C.P->q0);
+            if (k == 0) x = st;
             p = E.sl.b[k];
         }
-        parse<HIGH>(C, p, E.e);
+        const uint32_t st = parse<HIGH>(C, p, E.e, rec, st0);
+        return E.sl.n ? x : st;
     }
 
-    static __device__ __forceinline__ uint32_t count_all(const Ctx &C, const Enc &E, bool check, bool *gen_esc)
+    // Output bytes of the span; *xend: where the walk of its last stretch ended (a position past e when the
+    // piece crossing a cut runs into the next span). head, V, E2: as count_out, for the span's first stretch.
+    static __device__ __forceinline__ uint32_t count_all(const Ctx &C, const Enc &E, bool check, bool *gen_esc,
+                                                         uint32_t *xend, bool head, uint64_t *V, uint64_t *E2,
+                                                         uint32_t *n1)
     {
         uint32_t p = E.a, n = 0;
         bool ge = false, g2 = false;
         for (uint32_t k = 0; k < E.sl.n; ++k) {
-            n += count_out(C, p, E.sl.a[k], check, &g2) + E.sl.out[k];
+            const uint32_t c = count_out(C, p, E.sl.a[k], check, &g2, head && k == 0, V, E2) >> kPosBits;
+            if (k == 0) *n1 = c;
+            n += c + E.sl.out[k];
             ge |= g2;
             p = E.sl.b[k];
         }
-        n += count_out(C, p, E.e, check, &g2);
+        const uint32_t acc = count_out(C, p, E.e, check, &g2, head && E.sl.n == 0, V, E2);
+        if (E.sl.n == 0) *n1 = acc >> kPosBits;
+        n += acc >> kPosBits;
+        *xend = acc & kPosMask;
         *gen_esc = ge | g2;
         return n;
     }
@@ -995,7 +1328,7 @@ struct SP {
     template <class Sink>
     static __device__ __forceinline__ void write_all(const Ctx &C, const Enc &E, const uint8_t *raw, Sink &S)
     {
-        uint32_t w = E.off, rank = E.rank, p = E.a;
+        uint32_t w = E.off, rank = E.rank, p = E.entry;
         for (uint32_t k = 0; k < E.sl.n; ++k) {
             write_out(C, p, E.sl.a[k], w, rank, raw, S);
             w = emit_slow(C, E.sl.ws[k], w, S);
@@ -1005,8 +1338,9 @@ struct SP {
     }
 
     // Everything up to the tile's aggregate: masks, spans, pre-processing, parse, sizes (and, when the tile
-    // fits its stage, the staged output). Publishes the aggregate.
-    static __device__ Enc encode(const Ctx &C, OutSlot &O, uint64_t t)
+    // fits its stage, the staged output). Publishes the aggregate, unless a cut could not be kept (E.retry:
+    // nothing published, the stage overwritten; the caller stages the tile again and codes it without cuts).
+    static __device__ Enc encode(const Ctx &C, OutSlot &O, uint64_t t, bool cuts)
     {
         const ShardView &A = *C.A;
         WarpMem &M = *C.M;
@@ -1034,24 +1368,95 @@ struct SP {
         high |= mask_chunks(C, (16u + nown) >> 4, (tail_end + 15u) >> 4);
         // the tile's last line runs past the halo: lane 31 codes it alone, reading it from memory
         const bool past = lastnl == kNone && stage_hi != A.n;
-        const Span sp = spans(C, t, nown, tail_end, stage_hi == A.n);
+        const Span sp = spans(C, t, nown, tail_end, stage_hi == A.n, cuts ? C.P->cut_min : 0u);
+        const uint32_t cutf = (sp.cut_a ? 1u : 0u) | (sp.cut_b ? 2u : 0u);
+        const bool any_cut = __any_sync(kAll, cutf != 0);
         Enc E;
         uint32_t lines = 0;
-        bool shifted = false, fb = false;
+        bool shifted = false, fb = false, rt = false;
         E.a = sp.a;
-        E.e = preprocess(C, sp.a, sp.b, raw, past && sp.a < sp.b && sp.b == sp.B32, &lines, &shifted, E.sl, &fb);
+        E.retry = false;
+        E.e = preprocess(C, sp.a, sp.b, raw, past && sp.a < sp.b && sp.b == sp.B32, cutf, &lines, &shifted, E.sl,
+                         &fb, &rt);
+        E.entry = E.a;
         __syncwarp();
         if (E.sl.n) code_slow(C, E.sl, base);
-        if (high) parse_all<true>(C, E);
-        else parse_all<false>(C, E);
+        uint16_t *rec = (cutf & 2u) ? M.ring + lane : nullptr;  // the relabelling is done with the ring entries
+        const uint32_t ne = __ballot_sync(kAll, sp.a < sp.b);  // lanes with a span
+        const uint32_t nx = ne & ~((2u << lane) - 1u), pv = ne & ((1u << lane) - 1u);
+        const int next_lane = nx ? __ffs(nx) - 1 : (int)lane, prev_lane = pv ? 31 - __clz(pv) : (int)lane;
+        uint32_t st0 = C.P->q0;
+        if (any_cut) {  // a span ending at a cut starts its scan from a short read-ahead into the next span
+            const uint32_t nend = __shfl_sync(kAll, E.e, next_lane);
+            if ((cutf & 2u) && sp.a < sp.b)
+                st0 = high ? lookahead<true>(C, sp.b, min(nend, sp.b + kLook)) : lookahead<false>(C, sp.b, min(nend, sp.b + kLook));
+            __syncwarp();  // read before the next span's scan overwrites it
+        }
+        const uint32_t xst = high ? parse_all<true>(C, E, rec, st0) : parse_all<false>(C, E, rec, st0);
+        if (any_cut) {  // the parse at each cut: the true state there is the next span's exit state
+            const uint32_t T = __shfl_sync(kAll, xst, next_lane);
+            if ((cutf & 2u) && sp.a < sp.b) {
+                const uint32_t lo = E.sl.n ? E.sl.b[E.sl.n - 1] : E.a;
+                const bool ok = high ? repair_parse<true>(C, E.e, lo, T, rec) : repair_parse<false>(C, E.e, lo, T, rec);
+                rt |= !ok;
+            }
+        }
         bool gen_esc = false;
-        const uint32_t ob = count_all(C, E, shifted, &gen_esc);
+        uint32_t xend = 0, n1 = 0;
+        uint64_t V = 0, E2 = 0;
+        uint32_t ob = count_all(C, E, shifted, &gen_esc, &xend, (cutf & 1u) != 0, &V, &E2, &n1);
+        if (any_cut) {
+            // the walk at each cut: a span entered at a cut starts where the previous span's walk left it (its
+            // exit, past the cut, as a position of this span), joins its own speculative chain where the two
+            // meet, and walks its first stretch out exactly if they do not meet within 64 bytes. A changed exit
+            // changes the next span's entry: repeat until no exit changes.
+            const uint32_t ob0 = ob, x0 = xend;
+            uint32_t last_in = kNone;
+            for (int it = 0; it < 32; ++it) {
+                const uint32_t xo = (cutf & 2u) ? xend - E.e + sp.b : 0u;
+                const uint32_t xin = __shfl_sync(kAll, xo, prev_lane);
+                bool changed = false;
+                if ((cutf & 1u) && sp.a < sp.b && xin != last_in) {
+                    last_in = xin;
+                    const uint32_t lim = E.sl.n ? E.sl.a[0] : E.e;
+                    uint32_t pos = xin, extra = 0;
+                    bool joined = false;
+                    while (pos < lim) {
+                        const uint32_t r = pos - E.a;
+                        if (r < 64u && ((V >> r) & 1ull)) {
+                            const uint64_t below = (1ull << r) - 1ull;
+                            ob = ob0 + extra - (uint32_t)(__popcll(V & below) + __popcll(E2 & below));
+                            joined = true;
+                            break;
+                        }
+                        const uint32_t c = M.text[pos];
+                        const uint32_t m = C.meta[c];
+                        gen_esc |= c == kChEsc;
+                        extra += m >> kPosBits;
+                        pos += m & kPosMask;
+                    }
+                    uint32_t nx_end = x0;
+                    if (!joined) {
+                        ob = ob0 - n1 + extra;
+                        if (E.sl.n == 0) nx_end = pos;
+                    }
+                    changed = nx_end != xend;
+                    xend = nx_end;
+                    E.entry = xin;
+                }
+                if (!__any_sync(kAll, changed)) break;
+            }
+        }
+        if (__any_sync(kAll, rt)) {
+            E.retry = true;
+            return E;
+        }
         fb |= shifted && gen_esc;  // an escaped input byte no longer sits at its input position
         fb = __any_sync(kAll, fb);
         if (fb && lane == 0) atomicOr(C.status, kStFallback);
         const uint32_t oinc = warp_incl_u32(ob), linc = warp_incl_u32(lines);
         E.off = oinc - ob;
-        E.rank = linc - lines;
+        E.rank = linc - lines - (cutf & 1u);  // a span entered at a cut starts inside the previous lane's line
         E.total = __shfl_sync(kAll, oinc, 31);
         E.lines = __shfl_sync(kAll, linc, 31);
         const bool staged = !fb && E.total + 16u <= (uint32_t)kOutB && E.lines <= (uint32_t)kMaxL;
@@ -1174,7 +1579,17 @@ struct SP {
             }
             ph ^= 1u;
             __syncwarp();
-            const Enc E = encode(Cs, O, t);
+            Enc E = encode(Cs, O, t, P->cut_min != 0);
+            if (E.retry) {  // a cut could not be kept: stage the tile again and code it whole-line only
+                stage_issue(Cs, t);
+                if (!mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status)) {
+                    mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status);
+                    return;
+                }
+                ph ^= 1u;
+                __syncwarp();
+                E = encode(Cs, O, t, false);
+            }
             if (pending) {
                 Ctx Cp = C;
                 Cp.A = &M.os[s ^ 1u].sv;
@@ -1205,8 +1620,10 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_span_kernel(cons
 // Compiled geometries: 2048-byte tiles (about 44 lines of 46 bytes, so a lane span holds one or two lines)
 // with 20 warps per SM, the most whose stages fit beside a 170-state table; a variant with 4096-byte tiles
 // (longer spans, better balance across lanes, 11 warps) for long-line mixes.
-using SpV0 = SpGeom<20, 2048, 512, 1152, 128>;
-using SpV1 = SpGeom<11, 4096, 512, 2560, 320>;
+// Cuts: with 2048-byte tiles the reset-point search costs about what the balance gains on the long-tail mix
+// (measured), so they are off by default; with 4096-byte tiles they are on.
+using SpV0 = SpGeom<20, 2048, 512, 1152, 128, false>;
+using SpV1 = SpGeom<11, 4096, 512, 2560, 320, true>;
 // beside the table of a 170-state transducer (the frozen default dictionary; larger tables are checked at
 // run time by span_fits)
 static_assert(20 * sizeof(SP<SpV0, false>::WarpMem) + 170 * 256 + 1024 <= 227 * 1024, "shared memory");
@@ -1237,6 +1654,11 @@ cudaError_t sp_launch_as(const zs_dict *d, const TiledLaunch &L, unsigned flags,
     a.slow_cap = L.slow_cap;
     a.limit_ns = wait_limit_ns();
     a.stall_tile = injected_stall_tile();
+    // lines of at least 3/64 of a tile (1.5 lane shares) may be cut, in the geometries where that pays (Geo::kCut);
+    // a target within 1/128 of a tile of a line start takes the line start
+    const int64_t cm = span_cut_min_override();
+    a.cut_min = cm >= 0 ? (uint32_t)cm : (Geo::kCut ? (uint32_t)(3 * Geo::kTile / 64) : 0u);
+    a.cut_slack = Geo::kTile / 128;
     const int smem = (int)sp_smem<Geo>(d);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

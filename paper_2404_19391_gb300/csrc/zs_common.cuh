@@ -170,7 +170,9 @@ uint64_t wait_limit_ns();
 // Debug/fault-injection knobs, set from the environment of the calling process (tests only):
 //   ZS_WAIT_LIMIT_MS    overrides the wait limit
 //   ZS_INJECT_STALL     tile index whose look-back record is never published
+//   ZS_SPAN_CUT_MIN     shortest line the span kernel may cut between lanes (0: never); -1 when unset
 int64_t injected_stall_tile();
+int64_t span_cut_min_override();
 
 }  // namespace zs
 
