@@ -81,6 +81,8 @@ struct SpArgs {
     int64_t stall_tile;
     uint32_t cut_min;     // lines this long (or longer) may be cut between lanes at reset points; 0: never
     uint32_t cut_slack;   // a lane takes a cut only if its target is farther than this from a line start
+    uint64_t slots_need;  // bytes of the tile slots at the start of the scratch (lines longer than the stage)
+    uint64_t slots_bytes; // slots_need if the scratch holds them (lines are then coded before the launch), else 0
 };
 
 // Per-byte SIMD classification (bytes of a 32-bit word; the high bit of each result byte is the answer).
@@ -544,7 +546,21 @@ struct SP {
         uint32_t out[kMaxSlow];             // output bytes (with the '\n' of a line past the staged bytes)
         uint64_t ws[kMaxSlow];              // its work space in the scratch (offset), or ~0 if not coded
         uint32_t past;                      // bit k: line k runs past the staged bytes (found in memory)
+        uint32_t pre;                       // bit k: line k was coded before the launch (its tile's slot)
     };
+
+    // Allocates need bytes of the scratch after the tile slots; ~0 when they do not fit (the call runs again with
+    // more: the first overflow also counts the slots, so that the host's new size holds both).
+    static __device__ __forceinline__ uint64_t slow_alloc(const SpArgs *P, uint32_t *status, uint64_t need)
+    {
+        const unsigned long long o = atomicAdd(&P->g->slow_used, (unsigned long long)need);
+        if (P->slots_bytes + o + need > P->slow_cap) {
+            if (!(atomicOr(status, kStSlowOverflow) & kStSlowOverflow))
+                atomicAdd(&P->g->slow_used, (unsigned long long)P->slots_need);
+            return ~0ull;
+        }
+        return P->slots_bytes + o;
+    }
 
     static __device__ __forceinline__ bool add_slow(Slow &S, uint32_t a, uint32_t b, uint32_t ga, bool past = false)
     {
@@ -568,6 +584,15 @@ struct SP {
         const uint8_t *tab = C.tab;
         const uint32_t rep = C.P->rep_col;
         for (uint32_t k = 0; k < SL.n; ++k) {
+            if (((SL.past >> k) & 1u) && C.P->slots_bytes) {  // coded before the launch?
+                const uint32_t sl = reinterpret_cast<const uint32_t *>(C.P->slow)[A.tile0 + base / (uint64_t)kTB];
+                if (sl) {
+                    SL.ws[k] = (uint64_t)sl << 4;
+                    SL.out[k] = reinterpret_cast<const uint32_t *>(C.P->slow + SL.ws[k])[3];
+                    SL.pre |= 1u << k;
+                    continue;
+                }
+            }
             const uint64_t gs = base - 16 + SL.ga[k];  // the line's first byte in memory
             uint64_t glen = SL.b[k] - SL.a[k];
             bool nl_after = false;
@@ -582,11 +607,8 @@ struct SP {
                 continue;
             }
             const SlowLayout sl = slow_layout((uint32_t)glen);
-            const unsigned long long off = atomicAdd(&C.P->g->slow_used, (unsigned long long)sl.need);
-            if (off + sl.need > C.P->slow_cap) {  // the host retries with a larger scratch
-                atomicOr(C.status, kStSlowOverflow);
-                continue;
-            }
+            const uint64_t off = slow_alloc(C.P, C.status, sl.need);
+            if (off == ~0ull) continue;  // the host retries with a larger scratch
             uint8_t *ws = C.P->slow + off;
             uint8_t *tx = ws + sl.text, *ch = ws + sl.chs;
             uint32_t m;
@@ -640,6 +662,449 @@ struct SP {
         }
         if (nl_after) S.put(w++, kNl);
         return w;
+    }
+
+    // ---- lines coded by the whole warp ----------------------------------------------------------------------
+    // A line the lanes cannot code in the stage (longer than the stage, a label above 9, more open %nn labels
+    // than a lane follows) is coded by all 32 lanes together in a work space of global scratch:
+    //   header (32 bytes): input bytes n, pre-processed bytes m, flags (bit 0: a '\n' follows and is coded with
+    //   the line), output bytes, then where the span kernel placed it (address, room); then the copied line (text), its pre-processed form (text2, up to 3n bytes:
+    //   a label above 9 takes %nn), the choice and the state at each byte, the class masks (4 words per 32
+    //   bytes), a nibble per byte with its digit value, the lane table (first piece, chunk end, output offset)
+    //   and the tables of the one-lane exact pre-processing (taken when a label above 9 is needed).
+    struct LongLayout {
+        uint64_t text, text2, ch, st, masks, dv, table, tok, tables, need;
+    };
+
+    static __device__ __forceinline__ LongLayout long_layout(uint32_t n)
+    {
+        LongLayout L;
+        const uint64_t n16 = ((uint64_t)n + 31u) & ~15ull;  // 16 bytes of slack for 16-byte reads
+        const uint64_t nw = ((uint64_t)n + 31u) >> 5;
+        L.text = 32;
+        L.text2 = L.text + n16;
+        L.ch = L.text2 + 3ull * n16;
+        L.st = L.ch + 3ull * n16;
+        L.masks = L.st + 3ull * n16;
+        L.dv = L.masks + 16ull * nw;      // a nibble per byte: its digit value, 10 for '%', 15 otherwise
+        L.table = L.dv + 16ull * (nw + 1);
+        L.tok = L.table + 16ull * 32;
+        L.tables = (L.tok + n + 16u + 15u) & ~15ull;
+        L.need = (L.tables + 800u + 15u) & ~15ull;
+        return L;
+    }
+
+    // Position (in the input) of the first '\n' at or after `from`, or the end of the input: all lanes, 512
+    // bytes a round.
+    static __device__ uint64_t find_nl_warp(const Ctx &C, uint64_t from)
+    {
+        const ShardView &A = *C.A;
+        for (uint64_t base = from; base < A.n; base += 512) {
+            const uint64_t p0 = base + 16u * C.lane;
+            uint32_t bits = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < 16; ++j)
+                if (p0 + j < A.n && A.in[p0 + j] == kNl) bits |= 1u << j;
+            const uint32_t any = __ballot_sync(kAll, bits != 0);
+            if (any) {
+                const int l = __ffs(any) - 1;
+                const uint32_t b = __shfl_sync(kAll, bits, l);
+                return base + 16u * (uint32_t)l + (uint32_t)(__ffs(b) - 1);
+            }
+        }
+        return A.n;
+    }
+
+    // Copies the line (n bytes at src) into text, zero past its end, and writes its class masks: per 32 bytes,
+    // the digits and '%', '[', ']', and space or tab. All lanes, 32 bytes each a round.
+    static __device__ void long_copy(const Ctx &C, const uint8_t *src, uint32_t n, uint8_t *text, uint32_t *masks,
+                                     uint32_t *dv)
+    {
+        const uint32_t nw = (n + 31u) >> 5;
+        for (uint32_t w = C.lane; w <= nw; w += 32) {
+            uint32_t v[8], nib[4] = {~0u, ~0u, ~0u, ~0u}, d = 0, o = 0, cb = 0, s = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                uint32_t x = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t p = 32u * w + 4u * q + j;
+                    const uint32_t b = p < n ? src[p] : 0u;
+                    x |= b << (8 * j);
+                    const uint32_t bit = 1u << (4 * q + j);
+                    const uint32_t dg = b - '0';
+                    const uint32_t val = dg <= 9u ? dg : (b == '%' ? 10u : 15u);
+                    nib[q >> 1] &= ~(0xFu << (4 * (4 * (q & 1) + j))) | (val << (4 * (4 * (q & 1) + j)));
+                    if (val != 15u) d |= bit;
+                    if (b == '[') o |= bit;
+                    if (b == ']') cb |= bit;
+                    if (b == ' ' || b == '\t') s |= bit;
+                }
+                v[q] = x;
+            }
+            if (w < nw) {
+                uint4 *t4 = reinterpret_cast<uint4 *>(text + 32u * w);
+                t4[0] = make_uint4(v[0], v[1], v[2], v[3]);
+                t4[1] = make_uint4(v[4], v[5], v[6], v[7]);
+                *reinterpret_cast<uint4 *>(masks + 4u * w) = make_uint4(d, o, cb, s);
+            }
+            *reinterpret_cast<uint4 *>(dv + 4u * w) = make_uint4(nib[0], nib[1], nib[2], nib[3]);  // w = nw: all 15
+        }
+    }
+
+    // Pre-processing of the copied line by one lane (Sec. IV-A, the rules of preprocess_slow), visiting only the
+    // bytes the masks mark and reading digit values from the nibbles (the next word's masks and nibbles are
+    // loaded while a word is processed): new labels are written into text in place, and the two digits of each
+    // %nn label become kDel. open_at/open_nl: 100 entries each, in shared memory. Returns 0: done; 1: done, with
+    // %nn digits to squeeze out; 2: the line is left as it is (a bad %, an unclosed ring or atom; text is then
+    // restored by the caller); 3: a label above 9 is needed.
+    static __device__ uint32_t long_relabel(uint8_t *text, const uint32_t *masks, const uint32_t *dv, uint32_t n,
+                                            uint32_t *open_at, uint8_t *open_nl)
+    {
+        // open_at[label]: open token position + 1 of each input label (bit 30: a %nn token), 0: closed;
+        // open_nl[label]: opening order, the new label it took
+        for (int k = 0; k < 100; ++k) open_at[k] = 0;
+        uint32_t lc[10];  // closing order: latest close position + 1 of each new label
+#pragma unroll
+        for (int k = 0; k < 10; ++k) lc[k] = 0;
+        uint32_t held = 0, nopen = 0, skip_to = 0;
+        bool in_br = false, any_pct = false;
+        const uint32_t nw = (n + 31u) >> 5;
+        uint4 mk = *reinterpret_cast<const uint4 *>(masks), nv = *reinterpret_cast<const uint4 *>(dv);
+        for (uint32_t w = 0; w < nw; ++w) {
+            const uint4 mk1 = w + 1 < nw ? *reinterpret_cast<const uint4 *>(masks + 4u * (w + 1)) : make_uint4(0, 0, 0, 0);
+            const uint4 nv1 = *reinterpret_cast<const uint4 *>(dv + 4u * (w + 1));
+            auto nib = [&](uint32_t bit) -> uint32_t {  // digit value of byte bit of this word, bit < 34
+                const uint32_t q = bit >> 3, sh = 4u * (bit & 7u);
+                const uint32_t x = q == 0 ? nv.x : q == 1 ? nv.y : q == 2 ? nv.z : q == 3 ? nv.w : nv1.x;
+                return (x >> sh) & 0xFu;
+            };
+            uint32_t ev = mk.x | mk.y | mk.z | mk.w;
+            bool field_end = false;
+            while (ev) {
+                const uint32_t bit = (uint32_t)(__ffs(ev) - 1), p = 32u * w + bit, m1 = 1u << bit;
+                ev &= ev - 1u;
+                if (mk.w & m1) {  // the SMILES field ends at the first space or tab
+                    field_end = true;
+                    break;
+                }
+                if (in_br) {
+                    if (mk.z & m1) in_br = false;
+                    continue;
+                }
+                if (mk.y & m1) {
+                    in_br = true;
+                    continue;
+                }
+                if (!(mk.x & m1) || p < skip_to) continue;
+                const uint32_t v0 = nib(bit);
+                uint32_t label;
+                bool pct = false;
+                if (v0 == 10u) {  // '%': two digits must follow
+                    if (p + 2 >= n) return 2;
+                    const uint32_t d1 = nib(bit + 1), d2 = nib(bit + 2);
+                    if (d1 > 9 || d2 > 9) return 2;
+                    label = d1 * 10 + d2;
+                    pct = true;
+                    skip_to = p + 3;
+                } else {
+                    label = v0;
+                }
+                const uint32_t op = open_at[label];
+                uint32_t nl;
+                if (op == 0) {  // opens a ring
+                    open_at[label] = (p + 1u) | (pct ? (1u << 30) : 0u);
+                    ++nopen;
+                    if (!OUTER) continue;
+                    const uint32_t fr = ~held & 0x3FFu;
+                    if (fr == 0) return 3;
+                    nl = (uint32_t)__ffs(fr) - 1u;
+                    held |= 1u << nl;
+                    open_nl[label] = (uint8_t)nl;
+                } else {  // closes the ring opened at o
+                    const uint32_t o = (op & 0x3FFFFFFFu) - 1u;
+                    open_at[label] = 0;
+                    --nopen;
+                    if (OUTER) {
+                        nl = open_nl[label];
+                        held &= ~(1u << nl);
+                    } else {
+                        nl = 10;
+#pragma unroll
+                        for (int x = 9; x >= 0; --x)
+                            if (lc[x] <= o) nl = (uint32_t)x;
+                        if (nl == 10) return 3;
+                        text[o] = (uint8_t)('0' + nl);
+                        if (op & (1u << 30)) {
+                            text[o + 1] = kDel;
+                            text[o + 2] = kDel;
+                            any_pct = true;
+                        }
+#pragma unroll
+                        for (int x = 0; x < 10; ++x)
+                            if ((uint32_t)x == nl) lc[x] = p + 1u;
+                    }
+                }
+                text[p] = (uint8_t)('0' + nl);
+                if (pct) {
+                    text[p + 1] = kDel;
+                    text[p + 2] = kDel;
+                    any_pct = true;
+                }
+            }
+            if (field_end) break;
+            mk = mk1;
+            nv = nv1;
+        }
+        if (in_br || nopen != 0) return 2;
+        return any_pct ? 1u : 0u;
+    }
+
+    // Squeezes the kDel bytes out of text[0, n) into out: all lanes, 32 bytes each a round. Returns the length.
+    static __device__ uint32_t long_squeeze(const Ctx &C, const uint8_t *text, uint32_t n, uint8_t *out)
+    {
+        uint32_t base = 0;
+        for (uint32_t r0 = 0; r0 < n; r0 += 1024) {
+            const uint32_t p0 = r0 + 32u * C.lane;
+            uint32_t keep = 0;
+            for (uint32_t j = 0; j < 32; ++j) keep += (p0 + j < n && text[p0 + j] != kDel) ? 1u : 0u;
+            const uint32_t inc = warp_incl_u32(keep);
+            uint32_t o = base + inc - keep;
+            for (uint32_t j = 0; j < 32; ++j) {
+                const uint32_t p = p0 + j;
+                if (p < n && text[p] != kDel) out[o++] = text[p];
+            }
+            base += __shfl_sync(kAll, inc, 31);
+        }
+        return base;
+    }
+
+    // Backward scan of the pre-processed line text[0, m) in 32 chunks, one a lane (Sec. IV-D1): each lane starts
+    // from a read-ahead of the next chunk (16 bytes; exact at the line's end) and keeps the choice and the state
+    // at every byte; a chunk whose entry state was wrong is scanned again from the true one (the next chunk's
+    // state at its start) until the two scans meet. Returns the chunk length.
+    static __device__ uint32_t long_parse(const Ctx &C, const uint8_t *text, uint32_t m, uint8_t *ch, uint8_t *st)
+    {
+        const uint8_t *tab = C.tab;
+        const uint32_t rep = C.P->rep_col, lane = C.lane;
+        auto col = [&](uint32_t b) -> uint32_t { return b >= 0x80u ? rep : (b << 1); };
+        const uint32_t chunk = (((m + 31u) >> 5) + 15u) & ~15u;
+        const uint32_t c0 = min(m, lane * chunk), c1 = min(m, c0 + chunk);
+        uint32_t s = C.P->q0;
+        for (uint32_t p = min(m, c1 + 16u); p-- > c1;) s = look(tab, s, col(text[p]), 0x3204);
+        uint32_t entry = s;
+        if (c0 < c1) {  // 16 bytes a load (chunk starts are 16-aligned; text has 16 bytes of slack)
+            uint4 v = *reinterpret_cast<const uint4 *>(text + ((c1 - 1u) & ~15u));
+            for (uint32_t blk = (c1 - 1u) & ~15u;; blk -= 16u) {
+                const uint4 vn = blk > c0 ? *reinterpret_cast<const uint4 *>(text + blk - 16u) : v;  // the next block
+                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int j = 15; j >= 0; --j) {
+                    const uint32_t p = blk + (uint32_t)j;
+                    if (p < c1) {
+                        s = look(tab, s, col((wv[j >> 2] >> (8 * (j & 3))) & 0xFFu), 0x3204);
+                        ch[p] = (uint8_t)(s >> 8);
+                        st[p] = (uint8_t)s;
+                    }
+                }
+                if (blk == c0) break;
+                v = vn;
+            }
+        }
+        uint32_t exitv = s;
+        for (int it = 0; it < 32; ++it) {
+            const uint32_t T = __shfl_down_sync(kAll, exitv, 1);  // the next chunk's state at its start
+            bool changed = false;
+            if (lane < 31 && c1 < m && c0 < c1 && (T & 0xFFu) != (entry & 0xFFu)) {
+                entry = T;
+                uint32_t x = T;
+                bool met = false;
+                for (uint32_t p = c1; p-- > c0;) {
+                    x = look(tab, x, col(text[p]), 0x3204);
+                    ch[p] = (uint8_t)(x >> 8);
+                    if ((x & 0xFFu) == st[p]) {
+                        met = true;
+                        break;
+                    }
+                    st[p] = (uint8_t)x;
+                }
+                if (!met) {
+                    changed = (x & 0xFFu) != (exitv & 0xFFu);
+                    exitv = x;
+                }
+            }
+            if (!__any_sync(kAll, changed)) break;
+        }
+        return chunk;
+    }
+
+    // Forward byte reader over a buffer in global memory: 16 bytes a load, the next 16 already requested.
+    // Positions only grow; the buffer has 32 bytes of slack past the last position read.
+    struct Fwd {
+        const uint8_t *b;
+        uint32_t blk;
+        uint4 cur, nxt;
+        __device__ __forceinline__ void start(const uint8_t *base, uint32_t p)
+        {
+            b = base;
+            blk = p & ~15u;
+            cur = *reinterpret_cast<const uint4 *>(b + blk);
+            nxt = *reinterpret_cast<const uint4 *>(b + blk + 16u);
+        }
+        __device__ __forceinline__ uint32_t at(uint32_t p)
+        {
+            while (p >= blk + 16u) {
+                blk += 16u;
+                cur = nxt;
+                nxt = *reinterpret_cast<const uint4 *>(b + blk + 16u);
+            }
+            const uint32_t q = (p - blk) >> 2, sh = 8u * (p & 3u);
+            const uint32_t w = q == 0 ? cur.x : q == 1 ? cur.y : q == 2 ? cur.z : cur.w;
+            return (w >> sh) & 0xFFu;
+        }
+    };
+
+    // Emission walks of the coded line, chunk by chunk: each lane walks the pieces that start in its chunk
+    // (Sec. IV-D1), entering at the first piece the previous chunk's walk leaves to it; a lane walks its chunk
+    // speculatively from its start, noting where its first 64 positions start pieces, and joins the true chain
+    // where the two meet (or walks it out exactly), repeated until no chunk's exit moves. Fills the lane table
+    // {first piece, chunk end, output offset} and returns the line's output bytes.
+    static __device__ uint32_t long_walk(const Ctx &C, const uint8_t *ch, uint32_t m, uint32_t chunk, uint32_t *table)
+    {
+        const uint32_t *meta = C.meta, lane = C.lane;
+        const uint32_t c0 = min(m, lane * chunk), c1 = min(m, c0 + chunk);
+        uint64_t V = 0, E2 = 0;
+        uint32_t pos = c0, out = 0;
+        Fwd rd;
+        if (c0 < c1) rd.start(ch, c0);
+        while (pos < c1) {
+            const uint32_t mt = meta[rd.at(pos)];
+            const uint32_t r = pos - c0;
+            if (r < 64u) {
+                V |= 1ull << r;
+                E2 |= (uint64_t)((mt >> kPosBits) == 2u) << r;
+            }
+            out += mt >> kPosBits;
+            pos += mt & kPosMask;
+        }
+        const uint32_t out0 = out, x0 = pos;
+        uint32_t xend = pos, entry = c0, last_in = kNone;
+        for (int it = 0; it < 32; ++it) {
+            uint32_t xin = __shfl_up_sync(kAll, xend, 1);
+            bool changed = false;
+            if (lane > 0 && c0 < c1 && xin != last_in) {
+                last_in = xin;
+                uint32_t p = xin, extra = 0;
+                bool joined = false;
+                Fwd rj;
+                if (p < c1) rj.start(ch, p);
+                while (p < c1) {
+                    const uint32_t r = p - c0;
+                    if (r < 64u && ((V >> r) & 1ull)) {
+                        const uint64_t below = (1ull << r) - 1ull;
+                        out = out0 + extra - (uint32_t)(__popcll(V & below) + __popcll(E2 & below));
+                        joined = true;
+                        break;
+                    }
+                    const uint32_t mt = meta[rj.at(p)];
+                    extra += mt >> kPosBits;
+                    p += mt & kPosMask;
+                }
+                uint32_t nx = x0;
+                if (!joined) {
+                    out = extra;
+                    nx = p;
+                }
+                changed = nx != xend;
+                xend = nx;
+                entry = xin;
+            }
+            if (!__any_sync(kAll, changed)) break;
+        }
+        if (c0 >= c1) out = 0;
+        const uint32_t inc = warp_incl_u32(out);
+        *reinterpret_cast<uint4 *>(table + 4u * lane) = make_uint4(entry, c1, inc - out, 0u);
+        return __shfl_sync(kAll, inc, 31);
+    }
+
+    // Writes the coded line at output offset w: each lane its chunk's pieces at its offset. An escape writes
+    // ' ' and the pre-processed byte (or the escaped digit).
+    template <class Sink>
+    static __device__ void long_emit(const Ctx &C, const uint8_t *ws, uint32_t w, Sink &S)
+    {
+        const uint32_t n = reinterpret_cast<const uint32_t *>(ws)[0];
+        const uint32_t flags = reinterpret_cast<const uint32_t *>(ws)[2];
+        const uint32_t total = reinterpret_cast<const uint32_t *>(ws)[3];
+        const LongLayout L = long_layout(n);
+        const uint8_t *ch = ws + L.ch;
+        const uint8_t *text = ws + ((flags & 2u) ? L.text2 : L.text);
+        const uint4 row = *reinterpret_cast<const uint4 *>(ws + L.table + 16u * C.lane);
+        uint32_t o = w + row.z;
+        Fwd rd;
+        if (row.x < row.y) rd.start(ch, row.x);
+        for (uint32_t p = row.x; p < row.y;) {
+            const uint32_t c = rd.at(p);
+            p += C.meta[c] & kPosMask;
+            if (c > kChEsc) {
+                S.put(o++, (uint8_t)c);
+            } else {
+                S.put(o++, kEsc);
+                S.put(o++, c == kChEsc ? text[p - 1] : (uint8_t)('0' + c - kChEscDigit));
+            }
+        }
+        if (C.lane == 0 && (flags & 1u)) S.put(w + total - 1u, kNl);
+    }
+
+    // Codes one line [gs, gs + n) of the input with all lanes; nl_after: a '\n' follows, coded with the line.
+    // Returns the work space offset (its header holds the output bytes), or ~0 when the scratch is too small
+    // (the host runs the call again with more).
+    static __device__ uint64_t code_long(const Ctx &C, uint64_t gs, uint32_t n, bool nl_after, uint32_t *tabs)
+    {
+        const LongLayout L = long_layout(n);
+        uint64_t off = 0;
+        if (C.lane == 0) off = slow_alloc(C.P, C.status, L.need);
+        off = __shfl_sync(kAll, off, 0);
+        if (off == ~0ull) return ~0ull;
+        uint8_t *ws = C.P->slow + off;
+        uint8_t *text = ws + L.text, *text2 = ws + L.text2;
+        uint32_t *masks = reinterpret_cast<uint32_t *>(ws + L.masks);
+        const uint8_t *src = C.A->in + gs;
+        uint32_t *dv = reinterpret_cast<uint32_t *>(ws + L.dv);
+        long_copy(C, src, n, text, masks, dv);
+        __syncwarp();
+        uint32_t m = n, flags = nl_after ? 1u : 0u;
+        if (C.P->flags & ZS_PREPROCESS) {
+            uint32_t r = 0;
+            if (C.lane == 0)  // its tables in the warp's 512 bytes of shared memory
+                r = long_relabel(text, masks, reinterpret_cast<const uint32_t *>(ws + L.dv), n, tabs,
+                                 reinterpret_cast<uint8_t *>(tabs) + 400);
+            r = __shfl_sync(kAll, r, 0);
+            __syncwarp();
+            if (r == 1) {  // squeeze out the %nn digits
+                m = long_squeeze(C, text, n, text2);
+                flags |= 2u;
+            } else if (r == 2) {  // left as it is: copy it again
+                long_copy(C, src, n, text, masks, dv);
+            } else if (r == 3) {  // a label above 9: the exact pre-processing, one lane
+                if (C.lane == 0)
+                    m = preprocess_slow(src, n, text2, ws + L.tok, reinterpret_cast<int32_t *>(ws + L.tables),
+                                        reinterpret_cast<int32_t *>(ws + L.tables) + 100, OUTER);
+                m = __shfl_sync(kAll, m, 0);
+                flags |= 2u;
+            }
+            __syncwarp();
+        }
+        const uint8_t *tx = (flags & 2u) ? text2 : text;
+        uint8_t *ch = ws + L.ch;
+        const uint32_t chunk = long_parse(C, tx, m, ch, ws + L.st);
+        __syncwarp();
+        const uint32_t total = long_walk(C, ch, m, chunk, reinterpret_cast<uint32_t *>(ws + L.table)) + (nl_after ? 1u : 0u);
+        if (C.lane == 0) {
+            *reinterpret_cast<uint4 *>(ws) = make_uint4(n, m, flags, total);
+            *reinterpret_cast<uint4 *>(ws + 16) = make_uint4(0, 0, 0, 0);  // destination: noted by the span kernel
+        }
+        __syncwarp();
+        return off;
     }
 
     // ---- pre-processing ---------------------------------------------------------------------------------
@@ -1068,6 +1533,7 @@ struct SP {
         *retry = false;
         SL.n = 0;
         SL.past = 0;
+        SL.pre = 0;
         if (a >= b) return b;
         if (!(C.P->flags & ZS_PREPROCESS)) {
             if (last_slow) {  // the last line runs past the staged bytes: coded alone
@@ -1234,6 +1700,7 @@ struct SP {
         uint32_t nidx;
         __device__ __forceinline__ void put(uint32_t w, uint8_t v) { o[w] = v; }
         __device__ __forceinline__ void line(uint32_t r, uint32_t w) { if (r < nidx) idx[r] = w; }
+        __device__ __forceinline__ void long_dst(uint8_t *, uint32_t) {}  // such tiles are never staged
     };
     struct GlobalOut {  // direct writes: output offset ea, lines from eb
         uint8_t *out;
@@ -1248,6 +1715,22 @@ struct SP {
         __device__ __forceinline__ void line(uint32_t r, uint32_t w)
         {
             if (index && r < nlines && eb + r < index_cap) index[eb + r] = ea + w;
+        }
+        // a line coded before the launch: its destination and room, for the patch kernel (header bytes 16-31)
+        __device__ __forceinline__ void long_dst(uint8_t *ws, uint32_t w)
+        {
+            uint64_t *h = reinterpret_cast<uint64_t *>(ws + 16);
+            h[0] = reinterpret_cast<uint64_t>(out + ea + w);
+            h[1] = ea + w < cap ? cap - (ea + w) : 0;
+        }
+    };
+
+    struct LongSink {  // a line coded before the launch, written at dst (room bytes)
+        uint8_t *dst;
+        uint64_t room;
+        __device__ __forceinline__ void put(uint32_t w, uint8_t v)
+        {
+            if (w < room) dst[w] = v;
         }
     };
 
@@ -1331,7 +1814,12 @@ struct SP {
         uint32_t w = E.off, rank = E.rank, p = E.entry;
         for (uint32_t k = 0; k < E.sl.n; ++k) {
             write_out(C, p, E.sl.a[k], w, rank, raw, S);
-            w = emit_slow(C, E.sl.ws[k], w, S);
+            if ((E.sl.pre >> k) & 1u) {
+                S.long_dst(C.P->slow + E.sl.ws[k], w);
+                w += E.sl.out[k];
+            } else {
+                w = emit_slow(C, E.sl.ws[k], w, S);
+            }
             p = E.sl.b[k];
         }
         write_out(C, p, E.e, w, rank, raw, S);
@@ -1459,7 +1947,8 @@ struct SP {
         E.rank = linc - lines - (cutf & 1u);  // a span entered at a cut starts inside the previous lane's line
         E.total = __shfl_sync(kAll, oinc, 31);
         E.lines = __shfl_sync(kAll, linc, 31);
-        const bool staged = !fb && E.total + 16u <= (uint32_t)kOutB && E.lines <= (uint32_t)kMaxL;
+        const bool staged = !fb && E.total + 16u <= (uint32_t)kOutB && E.lines <= (uint32_t)kMaxL &&
+                            !__any_sync(kAll, E.sl.pre != 0);  // a line coded before: written by the patch kernel
         if (staged) {
             SmemOut so{O.out, O.idx, E.lines};
             if (lane == 0) O.idx[0] = 0;
@@ -1525,6 +2014,143 @@ struct SP {
         write_all(C, E, A.in + tile_base(t) - 16, go);
         finish_result(C, t, ea + E.total, eb + E.lines);
         __syncwarp();
+    }
+
+    // ---- lines longer than the stage: coded before the span kernel, written after it ----------------------
+    // The tile slots (one uint32 per tile of the launch, at the start of the scratch) hold the work space (offset
+    // / 16) of the tile's last line when that line runs past the tile's stage: the span kernel takes its size
+    // from there and the patch kernel writes its bytes. Nothing waits on these lines while they are coded.
+    static constexpr int kPreWarps = 8;
+    static constexpr uint32_t kPreTab = 512;  // bytes of relabelling tables per warp
+
+    static __host__ __device__ size_t pre_smem(uint32_t img_bytes)  // called by the launch
+    {
+        return ((img_bytes + 127u) & ~127u) + kPreWarps * (sizeof(ShardView) + kPreTab);
+    }
+
+    // Whether the last line of tile t of shard A runs past the tile's stage, and where that line starts: a '\n'
+    // neither at or after the last owned byte within the stage, nor the stage at the end of the input. The
+    // probe of four tiles at once (each lane 16 bytes of each) is done by precode_run.
+    static __device__ void precode_run(const SpArgs *P)
+    {
+        extern __shared__ __align__(128) uint8_t smem[];
+        __shared__ uint64_t img_bar;
+        const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        uint8_t *img = smem;
+        ShardView *svs = reinterpret_cast<ShardView *>(smem + ((P->img_bytes + 127u) & ~127u));
+        uint32_t *tabs = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(svs + kPreWarps) + wid * kPreTab);
+        Ctx C;
+        C.P = P;
+        C.A = &svs[wid];
+        C.M = nullptr;
+        C.tab = img;
+        C.meta = reinterpret_cast<const uint32_t *>(img + P->meta_off);
+        C.lane = lane;
+        C.status = &P->g->status;
+        if (threadIdx.x == 0) mbar_init(&img_bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_tx(&img_bar, P->img_bytes);
+            bulk_g2s(img, P->bimg, P->img_bytes, &img_bar);
+        }
+        const bool ok = mbar_wait_bounded(&img_bar, 0, P->limit_ns, C.status);
+        if (!__syncthreads_and(ok)) {
+            mbar_wait_bounded(&img_bar, 0, P->limit_ns, C.status);
+            return;
+        }
+        uint32_t *slot = reinterpret_cast<uint32_t *>(P->slow);
+        const uint64_t nwarps = (uint64_t)gridDim.x * kPreWarps;
+        for (uint64_t g0 = ((uint64_t)blockIdx.x * kPreWarps + wid) * 4u; g0 < P->total_tiles; g0 += nwarps * 4u) {
+            // probe: does the window [last owned byte, stage end) of tiles g0 .. g0 + 3 hold a '\n'?
+            uint32_t cand = 0;  // bit j: tile g0 + j may have its last line past the stage
+            uint32_t hit = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                const uint64_t g = g0 + j;
+                bool f = false;
+                if (g < P->total_tiles) {
+                    const uint32_t sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g);
+                    const ShardView &A = P->n_shards == 1 ? P->one : P->shards[sh];
+                    const uint64_t t = g - A.tile0, base = t * (uint64_t)kTB;
+                    const uint64_t own_end = min(A.n, base + kTB), stage_hi = min(A.n, base + kTB + kHB);
+                    if (stage_hi < A.n) {
+                        cand |= 1u << j;
+                        const uint64_t p0 = own_end - 1 + 16u * lane;
+#pragma unroll
+                        for (uint32_t i = 0; i < 16; ++i)
+                            if (p0 + i < stage_hi && A.in[p0 + i] == kNl) f = true;
+                    }
+                }
+                hit |= __any_sync(kAll, f) ? (1u << j) : 0u;
+            }
+            cand &= ~hit;
+            while (cand) {
+                const uint32_t j = (uint32_t)(__ffs(cand) - 1);
+                cand &= cand - 1u;
+                const uint64_t g = g0 + j;
+                const uint32_t sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g);
+                load_shard(&svs[wid], P->one, P->shards, P->n_shards, sh);
+                const ShardView &A = svs[wid];
+                const uint64_t t = g - A.tile0, base = t * (uint64_t)kTB;
+                const uint64_t own_end = min(A.n, base + kTB), stage_hi = min(A.n, base + kTB + kHB);
+                // the tile's last line start: after the last '\n' in [base - 1, own_end - 1) (the input's start
+                // counts as one); none: the tile holds no line start
+                uint64_t ls = ~0ull;
+                const uint64_t lo = base == 0 ? 0 : base - 1;
+                for (uint64_t hi = own_end - 1; hi > lo && ls == ~0ull;) {
+                    const uint64_t w0 = hi > lo + 512 ? hi - 512 : lo;
+                    uint32_t bits = 0;
+                    const uint64_t p0 = w0 + 16u * lane;
+#pragma unroll
+                    for (uint32_t i = 0; i < 16; ++i)
+                        if (p0 + i < hi && A.in[p0 + i] == kNl) bits |= 1u << i;
+                    const uint32_t any = __ballot_sync(kAll, bits != 0);
+                    if (any) {
+                        const int l = 31 - __clz(any);
+                        const uint32_t b = __shfl_sync(kAll, bits, l);
+                        ls = w0 + 16u * (uint32_t)l + (uint32_t)(31 - __clz(b)) + 1u;
+                    }
+                    hi = w0;
+                }
+                if (ls == ~0ull) {
+                    if (base != 0) continue;
+                    ls = 0;
+                }
+                const uint64_t ge = find_nl_warp(C, stage_hi);
+                if (ge - ls >= kLongLine) continue;  // refused by the span kernel
+                const uint64_t off = code_long(C, ls, (uint32_t)(ge - ls), ge < A.n, tabs);
+                if (lane == 0 && off != ~0ull) slot[g] = (uint32_t)(off >> 4);
+            }
+        }
+    }
+
+    // Writes the lines coded before the launch where the span kernel placed them: one warp per slot.
+    static __device__ void patch_run(const SpArgs *P)
+    {
+        const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        Ctx C;
+        C.P = P;
+        C.A = nullptr;
+        C.M = nullptr;
+        C.tab = nullptr;
+        C.meta = reinterpret_cast<const uint32_t *>(P->bimg + P->meta_off);
+        C.lane = lane;
+        C.status = &P->g->status;
+        const uint32_t *slot = reinterpret_cast<const uint32_t *>(P->slow);
+        const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+        for (uint64_t g0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + wid) * 32u; g0 < P->total_tiles;
+             g0 += nwarps * 32u) {
+            const uint64_t g = g0 + lane;
+            uint32_t todo = __ballot_sync(kAll, g < P->total_tiles && slot[g] != 0);
+            while (todo) {
+                const int l = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const uint8_t *ws = P->slow + ((uint64_t)slot[g0 + (uint32_t)l] << 4);
+                const uint64_t *h = reinterpret_cast<const uint64_t *>(ws + 16);
+                LongSink S{reinterpret_cast<uint8_t *>(h[0]), h[1]};
+                if (S.dst) long_emit(C, ws, 0, S);  // no address: the tile was not written (a rerun follows)
+            }
+        }
     }
 
     static __device__ void run(const SpArgs *P)
@@ -1617,6 +2243,18 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) compress_span_kernel(cons
     SP<Geo, OUTER>::run(&P);
 }
 
+template <class Geo, bool OUTER>
+__global__ void __launch_bounds__(SP<Geo, OUTER>::kPreWarps * 32) compress_span_precode_kernel(const SpArgs P)
+{
+    SP<Geo, OUTER>::precode_run(&P);
+}
+
+template <class Geo, bool OUTER>
+__global__ void __launch_bounds__(256) compress_span_patch_kernel(const SpArgs P)
+{
+    SP<Geo, OUTER>::patch_run(&P);
+}
+
 // Compiled geometries: 2048-byte tiles (about 44 lines of 46 bytes, so a lane span holds one or two lines)
 // with 20 warps per SM, the most whose stages fit beside a 170-state table; a variant with 4096-byte tiles
 // (longer spans, better balance across lanes, 11 warps) for long-line mixes.
@@ -1670,12 +2308,37 @@ cudaError_t sp_launch_as(const zs_dict *d, const TiledLaunch &L, unsigned flags,
         if (e != cudaSuccess) return e;
         set_smem = smem;
     }
+    // lines longer than the stage: a slot per tile at the start of the scratch, when it holds them
+    a.slots_need = (L.total_tiles * 4u + 255u) & ~255ull;
+    a.slots_bytes = (L.slow && L.slow_cap >= a.slots_need) ? a.slots_need : 0;
+    if (a.slots_bytes && L.total_tiles) {
+        cudaError_t e = cudaMemsetAsync(L.slow, 0, a.slots_bytes, s);
+        if (e != cudaSuccess) return e;
+        using S = SP<Geo, OUTER>;
+        const int psm = (int)S::pre_smem(d->blayout.img_bytes);
+        static int set_pre = -1;
+        if (set_pre != psm) {
+            e = cudaFuncSetAttribute(compress_span_precode_kernel<Geo, OUTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     psm);
+            if (e != cudaSuccess) return e;
+            set_pre = psm;
+        }
+        const uint64_t pg = std::min<uint64_t>((L.total_tiles + 4 * S::kPreWarps - 1) / (4 * S::kPreWarps),
+                                               (uint64_t)sms * 4u);
+        compress_span_precode_kernel<Geo, OUTER><<<(unsigned)pg, S::kPreWarps * 32, psm, s>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, compress_span_kernel<Geo, OUTER>, SP<Geo, OUTER>::kNT, smem);
     if (per < 1) per = 1;
     uint64_t grid = std::min<uint64_t>((L.total_tiles + Geo::kWarps - 1) / Geo::kWarps, (uint64_t)per * (uint64_t)sms);
     if (grid == 0) grid = 1;
     compress_span_kernel<Geo, OUTER><<<(unsigned)grid, SP<Geo, OUTER>::kNT, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !a.slots_bytes || !L.total_tiles) return e;
+    const uint64_t tg = std::min<uint64_t>((L.total_tiles + 255) / 256, (uint64_t)sms * 2u);
+    compress_span_patch_kernel<Geo, OUTER><<<(unsigned)tg, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

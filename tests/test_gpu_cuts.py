@@ -140,3 +140,47 @@ def test_long_tail_stream_every_cut_threshold(zs, dicts):
             os.environ.pop("ZS_SPAN_CUT_MIN", None)
         else:
             os.environ["ZS_SPAN_CUT_MIN"] = old
+
+
+def _stage_long_lines() -> list[bytes]:
+    """Lines longer than any tile and its halo (4-12 KB), built from long-tail fragments, with the cases the
+    warp-wide line coder must keep exact."""
+    rng = np.random.default_rng(11)
+    frag = [l for l in bytes(synth.generate(synth.CFG3, 0, 6000)).split(b"\n")[:-1] if len(l) >= 150]
+    out = []
+    for k in range(12):
+        target, cur = int(rng.integers(4000, 12001)), b""
+        while len(cur) < target:
+            cur += frag[int(rng.integers(0, len(frag)))]
+        out.append(cur)
+    big = out[0]
+    out.append(big + b"C1CC")                               # unclosed ring: left as it is
+    out.append(big[:3000] + b"C%1xC" + big[3000:])          # a bad %
+    out.append(big[:2000] + _nested(14) + big[2000:])       # labels above 9
+    out.append(big[:2500] + _pct_nested(9) + big[2500:])    # many open %nn
+    out.append(big[:4000] + b" second field 12 %34" + big[4000:6000])
+    out.append(big[:1000] + bytes([0xC3, 0xA9]) + big[1000:])
+    out.append(b"c1ccccc1" * 900)
+    return out
+
+
+@pytest.mark.parametrize("flags", [1, 3, 0])
+def test_lines_longer_than_the_stage(zs, dicts, flags):
+    d, od = dicts
+    longs = _stage_long_lines()
+    rng = np.random.default_rng(5)
+    short = bytes(synth.generate(synth.CFG1, 0, 3000)).split(b"\n")[:-1]
+    lines = []
+    for k, l in enumerate(longs):
+        lines += short[k * 100:(k * 100) + int(rng.integers(0, 60))]
+        lines.append(l)
+    raws = [b"\n".join(lines) + b"\n", b"\n".join(lines), longs[-1], longs[0] + b"\n" + longs[1]]
+    for raw in raws:
+        ec, ei = oracle.compress_stream(od, np.frombuffer(raw, dtype=np.uint8), flags)
+        for v in _span_variants(zs):
+            r, out, idx = _run(zs, d, raw, flags, v)
+            tag = f"variant {v} flags {flags} bytes {len(raw)}"
+            assert r.out_len == ec.size and r.n_lines == ei.size - 1, tag
+            assert np.array_equal(out[: r.out_len].cpu().numpy(), ec), tag
+            assert np.array_equal(idx[: ei.size].cpu().numpy().astype(np.uint64), ei), tag
+            assert torch.all(out[r.out_len:] == 0xEE), tag
