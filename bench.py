@@ -482,6 +482,59 @@ def bench_stream(zs, d, dev, shape, lines: int, peak: float, reps: int, first: i
     return out
 
 
+def long_line_stream(base: np.ndarray, count: int = 50, lo: int = 4096, hi: int = 8192, seed: int = 3) -> np.ndarray:
+    """base with `count` lines of lo..hi bytes spliced in at seeded line boundaries; each long line is made of
+    long-tail lines (ring labels, bracket atoms, %nn) joined without separators, so it stays one valid line."""
+    rng = np.random.default_rng(seed)
+    frag = [l for l in bytes(synth.generate(synth.CFG3, 0, 20000)).split(b"\n")[:-1] if len(l) > 150]
+    longs = []
+    for _ in range(count):
+        target, cur = int(rng.integers(lo, hi + 1)), b""
+        while len(cur) < target:
+            cur += frag[int(rng.integers(0, len(frag)))]
+        longs.append(cur + b"\n")
+    nl = np.flatnonzero(base == 10)
+    at = np.sort(rng.choice(nl.size, count, replace=False))
+    parts, prev = [], 0
+    for k, i in enumerate(at):
+        cut = int(nl[i]) + 1
+        parts.append(base[prev:cut])
+        parts.append(np.frombuffer(longs[k], dtype=np.uint8))
+        prev = cut
+    parts.append(base[prev:])
+    return np.concatenate(parts)
+
+
+def bench_long_lines(zs, d, dev, lines: int, reps: int = 3):
+    """Compression of the drug-like stream with and without 50 lines of 4-8 KB (longer than any tile's stage),
+    each through an autotuned plan: kernel time of both, and their ratio."""
+    import torch
+    nbytes = synth.lines_size(synth.CFG1, 0, lines)
+    base = np.empty(nbytes, dtype=np.uint8)
+    synth.generate_into(synth.CFG1, 0, lines, base.ctypes.data, nbytes)
+    mixed = long_line_stream(base)
+    out = {}
+    for name, host in (("base", base), ("with_long_lines", mixed)):
+        x = torch.from_numpy(host).to(dev)
+        comp = torch.empty(zs.zs_compress_bound(host.size), dtype=torch.uint8, device=dev)
+        idx = torch.empty(int(np.count_nonzero(host == 10)) + 2, dtype=torch.int64, device=dev)
+        pc = zs.Plan(d, zs.OP_COMPRESS, [(x, comp, idx)], flags=zs.PREPROCESS, variant=-1, tune_reps=2)
+        ts = []
+        for k in range(reps + 1):
+            pc.run()
+            if k:
+                ts.append(pc.last_ms)
+        out[name] = {"bytes": int(host.size), "kernel_ms": float(np.median(ts)),
+                     "variant": zs.zs_kernel_variant_name(zs.OP_COMPRESS, pc.variant)}
+        pc.close()
+        del x, comp, idx
+        torch.cuda.empty_cache()
+    out["ratio"] = out["with_long_lines"]["kernel_ms"] / out["base"]["kernel_ms"]
+    out["workload"] = (f"{lines:,} drug-like lines, then the same with 50 lines of 4-8 KB (long-tail lines joined, "
+                       "longer than any tile and its halo) spliced in at seeded line boundaries; autotuned plan each")
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_2404_19391_gb300 import zsmiles as zs
@@ -684,6 +737,7 @@ def run_gpu(args):
             cfg3["workload"] = (f"batched long tail: {args.cfg3_lines:,} synthetic lines ({cfg3['bytes'] / 1e9:.2f} "
                                 "GB), 90% drug-like, 10% of 150-400 chars with bracket atoms, stereo bonds and "
                                 "%nn ring labels; one stream, one autotuned plan (CUDA graph) each way")
+        long_lines = bench_long_lines(zs, d, dev, args.lines) if args.cfg3_lines > 0 else None
         line = {
             "metric": metric_name(), "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
@@ -730,6 +784,8 @@ def run_gpu(args):
         }
         if cfg3 is not None:
             line["config3"] = cfg3
+        if long_lines is not None:
+            line["long_lines"] = long_lines
         if world == 1 and not args.no_serving:
             line["serving"] = bench_serving(zs, d, dev, args.serve_lines, args.serve_requests,
                                             [int(r) for r in args.serve_rates.split(",")])

@@ -1325,10 +1325,10 @@ struct SP {
     // 32-bit word at a time: the prefix XOR of the bracket bits is 1 from a '[' up to its ']'. Space and tab are
     // in both bracket masks, so each one is a '[' inside an atom or a ']' outside one. Digits inside an atom
     // (isotopes, charges, H counts) are not ring labels; the fast relabelling masks them out the same way.
-    static __device__ __forceinline__ bool exception_free(const WarpMem &M, uint32_t a, uint32_t b)
+    static __device__ __forceinline__ bool exception_free(const WarpMem &M, uint32_t a, uint32_t b, bool *dig_in)
     {
         uint32_t in = 0;  // inside a bracket atom at the start of the word
-        uint32_t bad = 0;
+        uint32_t bad = 0, din = 0;
         for (uint32_t w = a >> 5; (w << 5) < b; ++w) {
             uint32_t keep = kAll;
             if ((w << 5) < a) keep &= kAll << (a & 31);
@@ -1341,8 +1341,10 @@ struct SP {
                    | (c & ~before)                           // ']' outside one (space, tab: always one of
                                                              //  the two, being in both masks)
                    | (M.nmask[w] & keep & px);               // a line ending inside one
+            din |= M.dmask[w] & keep & px & ~t;              // a digit inside one (isotope, charge, H count)
             in = (px >> 31) & 1u;
         }
+        *dig_in = din != 0;
         return bad == 0 && in == 0;
     }
 
@@ -1366,6 +1368,7 @@ struct SP {
     // of a line are decided as in relabel_general; the latest close of each new label is kept in 16-bit
     // halves of five registers (label x in register x % 5, high half for x >= 5), so finding the smallest
     // label free since the ring opened is five subtractions and one find-first-set, without branches.
+    template <bool MASK_ATOMS>  // some digit of the span sits inside a bracket atom: mask them out word by word
     static __device__ __forceinline__ uint32_t relabel_fast(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw,
                                                             bool last_slow, Slow &SL, bool *shifted, bool *fallback,
                                                             uint32_t cutf, bool *retry)
@@ -1408,6 +1411,7 @@ struct SP {
         // word's start; the span is exception-free, so the bracket masks hold only '[' and ']')
         uint32_t inb = 0;
         auto word_tokens = [&](uint32_t w, uint32_t keep) -> uint32_t {
+            if (!MASK_ATOMS) return (M.dmask[w] | M.nmask[w]) & keep;
             const uint32_t t = (M.omask[w] | M.cmask[w]) & keep;
             const uint32_t px = prefix_xor(t) ^ (0u - inb);
             inb = px >> 31;
@@ -1527,6 +1531,11 @@ struct SP {
                                                           bool *shifted, Slow &SL, bool *fallback, bool *retry)
     {
         const WarpMem &M = *C.M;
+        // exception test first, by every lane, so that the choice of masking is warp-wide (lanes taking both
+        // forms of the loop would run one after the other)
+        bool dig_in = false, ef = false;
+        if (a < b && (C.P->flags & ZS_PREPROCESS)) ef = exception_free(M, a, b, &dig_in);
+        const bool mask_atoms = __any_sync(kAll, dig_in);
         *lines = a < b ? count_bits(M.nmask, a, b) + (M.text[b - 1] != kNl ? 1u : 0u) - (cutf & 1u) : 0u;
         *shifted = false;
         *fallback = false;
@@ -1543,7 +1552,9 @@ struct SP {
             }
             return b;
         }
-        if (exception_free(M, a, b)) return relabel_fast(C, a, b, raw, last_slow, SL, shifted, fallback, cutf, retry);
+        if (ef)
+            return mask_atoms ? relabel_fast<true>(C, a, b, raw, last_slow, SL, shifted, fallback, cutf, retry)
+                              : relabel_fast<false>(C, a, b, raw, last_slow, SL, shifted, fallback, cutf, retry);
         uint32_t l2 = 0;
         return relabel_general(C, a, b, raw, &l2, shifted, last_slow, SL, fallback, cutf, retry);
     }
@@ -2084,6 +2095,8 @@ struct SP {
                 hit |= __any_sync(kAll, f) ? (1u << j) : 0u;
             }
             cand &= ~hit;
+            if (lane < 4 && g0 + lane < P->total_tiles) slot[g0 + lane] = 0;  // set below if the line is coded
+            __syncwarp();
             while (cand) {
                 const uint32_t j = (uint32_t)(__ffs(cand) - 1);
                 cand &= cand - 1u;
@@ -2312,9 +2325,8 @@ cudaError_t sp_launch_as(const zs_dict *d, const TiledLaunch &L, unsigned flags,
     a.slots_need = (L.total_tiles * 4u + 255u) & ~255ull;
     a.slots_bytes = (L.slow && L.slow_cap >= a.slots_need) ? a.slots_need : 0;
     if (a.slots_bytes && L.total_tiles) {
-        cudaError_t e = cudaMemsetAsync(L.slow, 0, a.slots_bytes, s);
-        if (e != cudaSuccess) return e;
-        using S = SP<Geo, OUTER>;
+        cudaError_t e = cudaSuccess;
+        using S = SP<Geo, OUTER>;  // the precode kernel writes every tile's slot
         const int psm = (int)S::pre_smem(d->blayout.img_bytes);
         static int set_pre = -1;
         if (set_pre != psm) {
