@@ -800,6 +800,20 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_stream(args):
+    """A small case of the two kernels the headline step runs (for a profiler): one drug-like and one long-tail
+    stream of args.profile_stream lines, each compressed and decompressed 4 times by the single-call API."""
+    import torch
+    from paper_2404_19391_gb300 import zsmiles as zs
+    zs.load_library()
+    d = zs.Dictionary()
+    peak, _ = hbm_peak()
+    out = {}
+    for name, shape in (("drug_like", synth.CFG1), ("long_tail", synth.CFG3)):
+        out[name] = bench_stream(zs, d, torch.device("cuda", 0), shape, args.profile_stream, peak, reps=3)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -815,6 +829,9 @@ def main():
     ap.add_argument("--ref-sample-bytes", type=int, default=20_000_000,
                     help="largest per-step sample of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-stream", type=int, default=0,
+                    help="only time one drug-like and one long-tail stream of this many lines through the "
+                         "single-call API (a small case for a profiler capture)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form request replay")
     ap.add_argument("--serve-lines", type=int, default=synth.CFG4_LINES)
     ap.add_argument("--serve-requests", type=int, default=20_000)
@@ -824,6 +841,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_stream:
+        run_profile_stream(args)
     elif args.ablation:
         run_ablation(args)
     else:
