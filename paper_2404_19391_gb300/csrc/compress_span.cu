@@ -1363,6 +1363,97 @@ struct SP {
         }
     }
 
+    // Relabelling of the common span (Sec. IV-A): exception-free, no '%', no cut, no line past the stage, no digit
+    // inside a bracket atom in the warp. Digit labels only, rewritten in place, nothing to squeeze: the ring
+    // opened at o closes at p and takes the smallest label free since o (closing order; five registers hold the
+    // latest closes as in relabel_fast) or keeps the label it took when it opened (opening order). A line left
+    // with an open ring is put back. Returns false, with the span's digits put back, when it meets a '%' or a
+    // line that needs a label above 9: the caller then takes relabel_fast.
+    static __device__ __forceinline__ bool relabel_lean(const Ctx &C, uint32_t a, uint32_t b, const uint8_t *raw)
+    {
+        WarpMem &M = *C.M;
+        uint8_t *text = M.text;
+        uint16_t *openp = M.ring + C.lane;  // open position + 1 of digit label d at openp[32 * d]
+        uint32_t ls = a, dopen = 0, held = 0;
+        uint32_t L0 = 0, L1 = 0, L2 = 0, L3 = 0, L4 = 0;
+        bool give_up = false;
+        uint32_t w = a >> 5;
+        uint32_t bits = (M.dmask[w] | M.nmask[w]) & (kAll << (a & 31));
+        for (;;) {
+            while (bits == 0) {
+                ++w;
+                if ((w << 5) >= b) break;
+                bits = M.dmask[w] | M.nmask[w];
+            }
+            if (bits == 0) break;
+            const uint32_t p = (w << 5) + (uint32_t)(__ffs(bits) - 1);
+            bits &= bits - 1;
+            if (p >= b) break;
+            const uint32_t c = text[p];
+            if (c == kNl) {  // end of a line: one with an unclosed ring stays as it is
+                if (dopen) restore_digits(M, text, raw, ls, p, 0);
+                dopen = held = 0;
+                L0 = L1 = L2 = L3 = L4 = 0;
+                ls = p + 1u;
+                continue;
+            }
+            const uint32_t d = c - '0';
+            if (d > 9u) {  // '%'
+                give_up = true;
+                break;
+            }
+            const uint32_t bit = 1u << d;
+            if (dopen & bit) {  // closes the ring opened at o
+                const uint32_t o = (uint32_t)openp[32 * d] - 1u;
+                uint32_t nl;
+                if (OUTER) {
+                    nl = (uint32_t)text[o] - '0';
+                    held &= ~(1u << nl);
+                } else {
+                    const uint32_t orep = (o * 0x00010001u) | 0x80008000u;
+                    const uint32_t g = (((orep - L0) & 0x80008000u) >> 15) | (((orep - L1) & 0x80008000u) >> 14) |
+                                       (((orep - L2) & 0x80008000u) >> 13) | (((orep - L3) & 0x80008000u) >> 12) |
+                                       (((orep - L4) & 0x80008000u) >> 11);
+                    const uint32_t f = (g & 0x1Fu) | ((g >> 11) & 0x3E0u);  // labels free since o, in order
+                    if (f == 0) {  // would need a two-digit label
+                        give_up = true;
+                        break;
+                    }
+                    nl = (uint32_t)__ffs(f) - 1u;
+                    text[o] = (uint8_t)('0' + nl);
+                    const uint32_t r = nl < 5 ? nl : nl - 5u;
+                    const uint32_t hm = nl < 5 ? 0x0000FFFFu : 0xFFFF0000u;
+                    const uint32_t v = ((p + 1u) * 0x00010001u) & hm;
+                    L0 = r == 0 ? (L0 & ~hm) | v : L0;
+                    L1 = r == 1 ? (L1 & ~hm) | v : L1;
+                    L2 = r == 2 ? (L2 & ~hm) | v : L2;
+                    L3 = r == 3 ? (L3 & ~hm) | v : L3;
+                    L4 = r == 4 ? (L4 & ~hm) | v : L4;
+                }
+                text[p] = (uint8_t)('0' + nl);
+            } else {  // opens a ring
+                openp[32 * d] = (uint16_t)(p + 1u);
+                if (OUTER) {
+                    const uint32_t fr = ~held & 0x3FFu;
+                    if (fr == 0) {
+                        give_up = true;
+                        break;
+                    }
+                    const uint32_t nl = (uint32_t)__ffs(fr) - 1u;
+                    held |= 1u << nl;
+                    text[p] = (uint8_t)('0' + nl);
+                }
+            }
+            dopen ^= bit;
+        }
+        if (give_up) {
+            restore_digits(M, text, raw, a, b, 0);
+            return false;
+        }
+        if (dopen) restore_digits(M, text, raw, ls, b, 0);
+        return true;
+    }
+
     // Relabelling of an exception-free span: only the digit bits outside bracket atoms (all of them ring labels)
     // and the newlines are visited. Labels
     // of a line are decided as in relabel_general; the latest close of each new label is kept in 16-bit
@@ -1552,9 +1643,11 @@ struct SP {
             }
             return b;
         }
-        if (ef)
+        if (ef) {
+            if (!mask_atoms && cutf == 0 && !last_slow && relabel_lean(C, a, b, raw)) return b;
             return mask_atoms ? relabel_fast<true>(C, a, b, raw, last_slow, SL, shifted, fallback, cutf, retry)
                               : relabel_fast<false>(C, a, b, raw, last_slow, SL, shifted, fallback, cutf, retry);
+        }
         uint32_t l2 = 0;
         return relabel_general(C, a, b, raw, &l2, shifted, last_slow, SL, fallback, cutf, retry);
     }
@@ -2071,70 +2164,104 @@ struct SP {
         }
         uint32_t *slot = reinterpret_cast<uint32_t *>(P->slow);
         const uint64_t nwarps = (uint64_t)gridDim.x * kPreWarps;
-        for (uint64_t g0 = ((uint64_t)blockIdx.x * kPreWarps + wid) * 4u; g0 < P->total_tiles; g0 += nwarps * 4u) {
-            // probe: does the window [last owned byte, stage end) of tiles g0 .. g0 + 3 hold a '\n'?
-            uint32_t cand = 0;  // bit j: tile g0 + j may have its last line past the stage
-            uint32_t hit = 0;
-#pragma unroll
-            for (uint32_t j = 0; j < 4; ++j) {
-                const uint64_t g = g0 + j;
-                bool f = false;
-                if (g < P->total_tiles) {
-                    const uint32_t sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g);
-                    const ShardView &A = P->n_shards == 1 ? P->one : P->shards[sh];
-                    const uint64_t t = g - A.tile0, base = t * (uint64_t)kTB;
-                    const uint64_t own_end = min(A.n, base + kTB), stage_hi = min(A.n, base + kTB + kHB);
-                    if (stage_hi < A.n) {
-                        cand |= 1u << j;
-                        const uint64_t p0 = own_end - 1 + 16u * lane;
-#pragma unroll
-                        for (uint32_t i = 0; i < 16; ++i)
-                            if (p0 + i < stage_hi && A.in[p0 + i] == kNl) f = true;
-                    }
-                }
-                hit |= __any_sync(kAll, f) ? (1u << j) : 0u;
+        // each warp a contiguous run of tiles, so that the shard changes rarely; eight tiles a round, four lanes
+        // a tile, each lane 16 of the 64 bytes from the tile's last owned byte (the first '\n' after it is
+        // nearly always there); a tile without one there is probed over its whole stage window on its own
+        const uint64_t per = (P->total_tiles + nwarps - 1) / nwarps;
+        const uint64_t g_begin = ((uint64_t)blockIdx.x * kPreWarps + wid) * per;
+        const uint64_t g_end = min(P->total_tiles, g_begin + per);
+        uint64_t s_t0 = 1, s_t1 = 0;  // tiles [s_t0, s_t1) of the cached shard
+        uint32_t sh = 0;
+        for (uint64_t g0 = g_begin; g0 < g_end; g0 += 8) {
+            if (g0 < s_t0 || g0 >= s_t1) {
+                sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g0);
+                const ShardView &S0 = P->n_shards == 1 ? P->one : P->shards[sh];
+                s_t0 = S0.tile0;
+                s_t1 = S0.tile0 + S0.ntiles;
             }
-            cand &= ~hit;
-            if (lane < 4 && g0 + lane < P->total_tiles) slot[g0 + lane] = 0;  // set below if the line is coded
-            __syncwarp();
-            while (cand) {
-                const uint32_t j = (uint32_t)(__ffs(cand) - 1);
-                cand &= cand - 1u;
-                const uint64_t g = g0 + j;
-                const uint32_t sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g);
-                load_shard(&svs[wid], P->one, P->shards, P->n_shards, sh);
-                const ShardView &A = svs[wid];
-                const uint64_t t = g - A.tile0, base = t * (uint64_t)kTB;
-                const uint64_t own_end = min(A.n, base + kTB), stage_hi = min(A.n, base + kTB + kHB);
-                // the tile's last line start: after the last '\n' in [base - 1, own_end - 1) (the input's start
-                // counts as one); none: the tile holds no line start
-                uint64_t ls = ~0ull;
-                const uint64_t lo = base == 0 ? 0 : base - 1;
-                for (uint64_t hi = own_end - 1; hi > lo && ls == ~0ull;) {
-                    const uint64_t w0 = hi > lo + 512 ? hi - 512 : lo;
-                    uint32_t bits = 0;
-                    const uint64_t p0 = w0 + 16u * lane;
+            const ShardView &A0 = P->n_shards == 1 ? P->one : P->shards[sh];
+            const uint32_t j = C.lane >> 2, q = C.lane & 3u;
+            const uint64_t g = g0 + j;
+            bool mine = false, cand = false, f = false;
+            if (g < g_end && g < s_t1) {  // tiles of the cached shard (the rest are taken next round)
+                mine = true;
+                const uint64_t base = (g - A0.tile0) * (uint64_t)kTB;
+                const uint64_t own_end = min(A0.n, base + kTB), stage_hi = min(A0.n, base + kTB + kHB);
+                cand = stage_hi < A0.n;
+                if (cand) {
+                    const uint64_t p0 = own_end - 1 + 16u * q;
 #pragma unroll
                     for (uint32_t i = 0; i < 16; ++i)
-                        if (p0 + i < hi && A.in[p0 + i] == kNl) bits |= 1u << i;
-                    const uint32_t any = __ballot_sync(kAll, bits != 0);
-                    if (any) {
-                        const int l = 31 - __clz(any);
-                        const uint32_t b = __shfl_sync(kAll, bits, l);
-                        ls = w0 + 16u * (uint32_t)l + (uint32_t)(31 - __clz(b)) + 1u;
-                    }
-                    hi = w0;
+                        if (p0 + i < stage_hi && A0.in[p0 + i] == kNl) f = true;
                 }
-                if (ls == ~0ull) {
-                    if (base != 0) continue;
-                    ls = 0;
-                }
-                const uint64_t ge = find_nl_warp(C, stage_hi);
-                if (ge - ls >= kLongLine) continue;  // refused by the span kernel
-                const uint64_t off = code_long(C, ls, (uint32_t)(ge - ls), ge < A.n, tabs);
-                if (lane == 0 && off != ~0ull) slot[g] = (uint32_t)(off >> 4);
             }
+            if (mine && q == 0) slot[g] = 0;  // set below if the line is coded
+            // a tile is done when one of its four lanes saw a '\n' or it is not a candidate
+            const uint32_t seen = __ballot_sync(kAll, f), cands = __ballot_sync(kAll, cand && q == 0);
+            const uint32_t took = __ballot_sync(kAll, mine && q == 0);
+            uint32_t left = 0;  // tiles (bit j) whose first 64 bytes hold no '\n'
+            for (uint32_t jj = 0; jj < 8; ++jj)
+                if (((cands >> (4 * jj)) & 1u) && !((seen >> (4 * jj)) & 0xFu)) left |= 1u << jj;
+            const uint32_t ntook = __popc(took);
+            __syncwarp();
+            while (left) {
+                const uint32_t jj = (uint32_t)(__ffs(left) - 1);
+                left &= left - 1u;
+                precode_tile(C, g0 + jj, sh, slot, tabs, svs + wid);
+            }
+            if (ntook < 8) g0 -= 8 - ntook;  // the round stopped at the shard's end: resume there
         }
+    }
+
+    // One tile whose first 64 bytes after its last owned byte hold no '\n': probe the rest of its stage window,
+    // and if the last line runs past the stage, find the line and code it (all lanes).
+    static __device__ void precode_tile(Ctx &C, uint64_t g, uint32_t sh, uint32_t *slot, uint32_t *tabs,
+                                        ShardView *sv)
+    {
+        const SpArgs *P = C.P;
+        load_shard(sv, P->one, P->shards, P->n_shards, sh);
+        C.A = sv;
+        const ShardView &A = *sv;
+        const uint32_t lane = C.lane;
+        const uint64_t t = g - A.tile0, base = t * (uint64_t)kTB;
+        const uint64_t own_end = min(A.n, base + kTB), stage_hi = min(A.n, base + kTB + kHB);
+        bool nl = false;
+        for (uint64_t q0 = own_end - 1 + 64; q0 < stage_hi && !nl; q0 += 512) {
+            const uint64_t p0 = q0 + 16u * lane;
+            bool f = false;
+#pragma unroll
+            for (uint32_t i = 0; i < 16; ++i)
+                if (p0 + i < stage_hi && A.in[p0 + i] == kNl) f = true;
+            nl = __any_sync(kAll, f);
+        }
+        if (nl) return;
+        // the tile's last line start: after the last '\n' in [base - 1, own_end - 1) (the input's start counts
+        // as one); none: the tile holds no line start
+        uint64_t ls = ~0ull;
+        const uint64_t lo = base == 0 ? 0 : base - 1;
+        for (uint64_t hi = own_end - 1; hi > lo && ls == ~0ull;) {
+            const uint64_t w0 = hi > lo + 512 ? hi - 512 : lo;
+            uint32_t bits = 0;
+            const uint64_t p0 = w0 + 16u * lane;
+#pragma unroll
+            for (uint32_t i = 0; i < 16; ++i)
+                if (p0 + i < hi && A.in[p0 + i] == kNl) bits |= 1u << i;
+            const uint32_t any = __ballot_sync(kAll, bits != 0);
+            if (any) {
+                const int l = 31 - __clz(any);
+                const uint32_t bb = __shfl_sync(kAll, bits, l);
+                ls = w0 + 16u * (uint32_t)l + (uint32_t)(31 - __clz(bb)) + 1u;
+            }
+            hi = w0;
+        }
+        if (ls == ~0ull) {
+            if (base != 0) return;
+            ls = 0;
+        }
+        const uint64_t ge = find_nl_warp(C, stage_hi);
+        if (ge - ls >= kLongLine) return;  // refused by the span kernel
+        const uint64_t off = code_long(C, ls, (uint32_t)(ge - ls), ge < A.n, tabs);
+        if (lane == 0 && off != ~0ull) slot[g] = (uint32_t)(off >> 4);
     }
 
     // Writes the lines coded before the launch where the span kernel placed them: one warp per slot.
