@@ -1654,10 +1654,12 @@ struct SP {
 
     // ---- parse ------------------------------------------------------------------------------------------
     // Table lookup of the byte transducer: entry (next state | choice << 8) at byte offset
-    // (state << 8) | (2 * byte), built by one byte-permute from the previous entry and the doubled bytes.
+    // (state << 8) | (2 * byte XOR (state mod 32) * 4): one byte-permute builds (state << 8) | 2 * byte from the
+    // previous entry and the doubled bytes, and the swizzle (the state's low five bits, from the same entry)
+    // moves the entry to a bank of its own, so lanes on the same byte in different states do not conflict.
     static __device__ __forceinline__ uint32_t look(const uint8_t *tab, uint32_t prev, uint32_t x2, uint32_t sel)
     {
-        return *reinterpret_cast<const uint16_t *>(tab + __byte_perm(prev, x2, sel));
+        return *reinterpret_cast<const uint16_t *>(tab + (__byte_perm(prev, x2, sel) ^ ((prev << 2) & 0x7Cu)));
     }
 
     // Backward scan of the lane's span [a, e): each byte is replaced by the choice made there. HIGH: the tile

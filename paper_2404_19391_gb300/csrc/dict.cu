@@ -481,7 +481,7 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
                         ch = e2 >> 24;
                         if (ch == zs::kEsc && b >= '0' && b <= '9') ch = 0x10u + (b - '0');
                     }
-                    t16[q * 128 + b] = (uint16_t)(ns | (ch << 8));
+                    t16[q * 128 + (b ^ ((q & 31u) << 1))] = (uint16_t)(ns | (ch << 8));  // bank swizzle
                 }
             uint32_t *meta = reinterpret_cast<uint32_t *>(bimg.data() + BL.meta_off);
             for (uint32_t c = 0; c < 256; ++c) {

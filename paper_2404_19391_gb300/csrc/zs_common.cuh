@@ -79,7 +79,9 @@ constexpr uint32_t kMOffClsRep = 0, kMOffPlen = 8192, kMOffTable = 8448;
 // the raw byte (bytes 0-127; bytes >= 0x80 read the column of a byte below 0x80 in no pattern), so a lookup
 // needs no class table.
 //   [0, 256 * n_states)    table[state][128] (u16): next state | choice << 8, at byte offset state * 256 +
-//                          2 * byte. Choices: a symbol (every symbol is above ' '); ' ' = escape of the input
+//                          (2 * byte XOR (state mod 32) * 4): the swizzle spreads one byte's entries over the 32
+//                          banks, so lanes reading the same byte in different states do not conflict.
+//                          Choices: a symbol (every symbol is above ' '); ' ' = escape of the input
 //                          byte; 0x10 + d = escape of the digit d; '\n' = end of line (next state: the start)
 //   [meta_off, +1024)      meta[256] (u32) per choice: input bytes consumed | output bytes << 13
 struct ByteLayout {
