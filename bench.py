@@ -535,6 +535,41 @@ def bench_long_lines(zs, d, dev, lines: int, reps: int = 3):
     return out
 
 
+def _read_into(path: str, arr: np.ndarray) -> int:
+    """Reads the file into arr (a host buffer), looping over partial reads (one read() stops near 2 GB)."""
+    mv, got = memoryview(arr).cast("B"), 0
+    with open(path, "rb", buffering=0) as f:
+        while got < mv.nbytes:
+            n = f.readinto(mv[got:])
+            if not n:
+                break
+            got += n
+    return got
+
+
+def _write_from(path: str, arr: np.ndarray) -> int:
+    """Writes arr (a host buffer) to the file, looping over partial writes."""
+    mv, put = memoryview(arr).cast("B"), 0
+    with open(path, "wb", buffering=0) as f:
+        while put < mv.nbytes:
+            put += f.write(mv[put:])
+    return put
+
+
+def _storage_dir(need: int):
+    """A scratch directory with `need` bytes free: /dev/shm (memory) if it has room, else the system temporary
+    directory; None if neither does."""
+    import shutil
+    import tempfile
+    for base in ("/dev/shm", tempfile.gettempdir()):
+        try:
+            if os.path.isdir(base) and shutil.disk_usage(base).free > need:
+                return tempfile.mkdtemp(prefix="zs_storage_", dir=base)
+        except OSError:
+            pass
+    return None
+
+
 def run_gpu(args):
     import torch
     from paper_2404_19391_gb300 import zsmiles as zs
@@ -656,6 +691,45 @@ def run_gpu(args):
     e2e_ms = (time.perf_counter() - w0) * 1e3 / e2e_steps
     barrier()
     clocks.stop()
+
+    # ---- storage leg: the step's compression and decompression from and to files. The 64 shards as one text
+    # file (written once, untimed); each timed step reads it into pinned memory, compresses it through the host
+    # pipeline, writes the compressed file and its line index, reads the compressed file back, decompresses it
+    # and writes the decoded text file. The files sit in the box's page cache (or /dev/shm): this measures the
+    # host file path around the GPU, not a storage device ----
+    storage = None
+    sdir = _storage_dir(3 * nbytes + 2 * cbytes + 16 * nlines + (1 << 30))
+    if sdir is not None:
+        import shutil
+        fin, fz, fx, fo = (os.path.join(sdir, f"{k}_{rank}") for k in ("in.smi", "out.zs", "out.idx", "out.smi"))
+        hin_np, hcomp_np, hidx_np, hdec_np = host_in.numpy(), host_comp.numpy(), host_idx.numpy(), host_dec.numpy()
+        _write_from(fin, hin_np)
+        sio = {}
+
+        def storage_step():
+            got = _read_into(fin, hin_np)
+            r = zs.zs_compress_host(d, host_in, zs.PREPROCESS, host_comp, host_idx)
+            w1 = _write_from(fz, hcomp_np[: r.out_len]) + _write_from(fx, hidx_np[: r.n_lines + 1])
+            got2 = _read_into(fz, hcomp_np[: r.out_len])
+            rd = zs.zs_decompress_host(d, host_comp[: r.out_len], host_dec)
+            w2 = _write_from(fo, hdec_np[: rd.out_len])
+            sio.update(read=got + got2, written=w1 + w2,
+                       same=(got == nbytes and r.out_len == cbytes and r.n_lines == nlines and rd.out_len == dbytes))
+
+        storage_step()
+        st_steps = max(1, min(3, e2e_steps))
+        barrier()
+        w0 = time.perf_counter()
+        for _ in range(st_steps):
+            storage_step()
+        st_ms = (time.perf_counter() - w0) * 1e3 / st_steps
+        barrier()
+        shutil.rmtree(sdir, ignore_errors=True)
+        storage = {"value": nbytes / (st_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": st_ms, "steps": st_steps,
+                   "read_bytes_per_step": sio["read"], "written_bytes_per_step": sio["written"],
+                   "same_sizes_as_device_step": sio["same"], "directory": os.path.dirname(sdir),
+                   "leg": "text file -> pinned -> H2D -> compress -> D2H -> compressed + index files; compressed "
+                          "file -> pinned -> H2D -> decompress -> D2H -> text file (page cache or /dev/shm)"}
     del host_in, host_comp, host_idx, host_dec
 
     (ms_step, e2e_ms), (total_bytes,) = reduce_over_ranks([ms_total / args.steps, e2e_ms], [nbytes], dev)
@@ -762,7 +836,10 @@ def run_gpu(args):
                            "memory, to a pinned host stream and index) + zs_decompress_host (that stream to pinned "
                            f"host text) + {RA_IDS:,} random ids H2D, zs_decompress_lines on the device-resident "
                            "largest shard, lines and offsets D2H"},
-            "gpu_launches": 3 * args.steps,
+            # per step: compress (span geometries: a probe for lines longer than the stage, the span kernel and
+            # the patch kernel that writes such lines), decompress, random access
+            "gpu_launches": ((3 if "span" in cvar else 1) + 2) * args.steps,
+            "e2e_storage": storage if storage is not None else {"unavailable": "no scratch directory with room"},
             "roofline": {"bound": "hbm", "achieved": achieved_c, "peak": peak, "unit": "GB/s",
                          "frac": achieved_c / peak, "traffic": traffic, "kernel": ckernel,
                          "peak_kind": f"{peak_kind} (copy, MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
