@@ -246,9 +246,14 @@ zs_status zs_decompress_batch(const zs_dict *d, const zs_shard *shards, size_t n
 typedef struct zs_plan zs_plan; /* opaque, library-owned */
 
 typedef struct zs_plan_options {
-    int variant;   /* -1: autotune (time every variant on this batch, keep the fastest); else a variant */
-    int use_graph; /* nonzero: capture clear + launch + result copy in a CUDA graph, replay it per run */
-    int tune_reps; /* timed runs per variant when autotuning (<= 0: 3) */
+    int variant;    /* -1: autotune (time every variant on this batch, keep the fastest); else a variant */
+    int use_graph;  /* nonzero: capture clear + launch + result copy in a CUDA graph, replay it per run */
+    int tune_reps;  /* timed runs per variant when autotuning (<= 0: 3) */
+    int cut_min;    /* span geometries, fixed variant: shortest line cut between lanes (0: the geometry's
+                       default; < 0: never). Autotuning times the default and its opposite and keeps the faster */
+    int tune_cache; /* nonzero: an autotuned plan first looks up, then records, its choice (variant, cut) under
+                       (GPU model, dictionary digest, operation, flags, log2 of the batch bytes, shard count and
+                       largest shard); the cache lives in the process, and in the file ZS_TUNE_CACHE names */
 } zs_plan_options;
 
 /* Makes a plan for `op` over the shards (host array, copied). opt may be NULL: autotune, with a graph.
@@ -261,6 +266,7 @@ zs_status zs_plan_create(const zs_dict *d, zs_op op, unsigned flags, const zs_sh
  * one plan must not overlap (the plan's scratch is reused). */
 zs_status zs_plan_run(zs_plan *p, zs_result *res, void *stream);
 int zs_plan_variant(const zs_plan *p);             /* the variant the plan runs */
+int zs_plan_cut_min(const zs_plan *p);             /* its span cut threshold in bytes (0: no cuts) */
 double zs_plan_tuned_ms(const zs_plan *p, int v);  /* median kernel ms of variant v when tuned, else -1 */
 double zs_plan_last_ms(const zs_plan *p);          /* kernel ms of the last run */
 void zs_plan_destroy(zs_plan *p);

@@ -8,7 +8,12 @@
 // the line index of empty shards, launch, copy the result records to pinned host memory. With a graph
 // those steps are captured once and replayed by one cudaGraphLaunch.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "zs_common.cuh"
@@ -24,8 +29,9 @@ struct zs_plan {
     int device = -1;
     std::vector<zs_shard> shards;
     int variant = 0;
+    int cut_min = 0;               // span geometries: cut threshold (0: the geometry's default, < 0: never)
     bool use_graph = true;
-    std::vector<double> tuned_ms;  // per variant; < 0: not timed
+    std::vector<double> tuned_ms;  // per variant (its best cut setting); < 0: not timed
 
     // device block: ShardView table[n] | DevResult g | DevResult res[n] | TileState tiles[max_tiles]
     void *dev = nullptr;
@@ -114,6 +120,7 @@ cudaError_t issue(zs_plan *p, cudaStream_t s, bool capturing)
         L.g = p->dres();
         L.slow = p->slow;
         L.slow_cap = p->slow_cap;
+        L.cut_min = p->cut_min;
         // under stream capture a plain record would only order streams: record external event nodes
         const unsigned rf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         e = cudaEventRecordWithFlags(p->ev0, s, rf);
@@ -238,34 +245,59 @@ zs_status collect(zs_plan *p, zs_result *res)
     return first;
 }
 
+// Times `reps` runs of the current layout (after one untimed run that also sizes the long-line scratch);
+// *skip: the batch needs the general kernel (the span geometry cannot run it).
+zs_status time_runs(zs_plan *p, int reps, double *ms, bool *skip)
+{
+    zs_status st = run_once(p, p->cap, false);
+    *skip = st == ZS_OK && (p->host[0].status & zs::kStFallback);
+    std::vector<float> t;
+    for (int k = 0; k < reps && st == ZS_OK && !*skip; ++k) {
+        st = run_once(p, p->cap, false);
+        t.push_back(p->last_ms);
+    }
+    std::sort(t.begin(), t.end());
+    *ms = t.empty() ? 0.0 : t[t.size() / 2];
+    return st;
+}
+
+// Autotuning: every geometry that fits, and for span geometries the long-line cut setting both ways (the
+// geometry's default and its opposite: cuts at 3/64 of a tile, or none); keeps the fastest.
 zs_status tune(zs_plan *p, int reps)
 {
     const int nv = variant_count(p->op);
     p->tuned_ms.assign(nv, -1.0);
-    int best = -1;
+    int best = -1, best_cut = 0;
     double best_ms = 0.0;
     const bool graph = p->use_graph;
     p->use_graph = false;
     for (int v = 0; v < nv; ++v) {
         if (!variant_usable(p, v)) continue;
         zs_status st = layout(p, v);
-        if (st == ZS_OK) st = run_once(p, p->cap, false);  // warm-up (and long-line scratch sizing)
-        if (st == ZS_OK && (p->host[0].status & zs::kStFallback)) continue;  // this batch needs the general kernel
-        std::vector<float> t;
-        for (int k = 0; k < reps && st == ZS_OK; ++k) {
-            st = run_once(p, p->cap, false);
-            t.push_back(p->last_ms);
-        }
         if (st != ZS_OK) {
             p->use_graph = graph;
             return st;
         }
-        std::sort(t.begin(), t.end());
-        const double ms = t.empty() ? 0.0 : t[t.size() / 2];
-        p->tuned_ms[v] = ms;
-        if (best < 0 || ms < best_ms) {
-            best = v;
-            best_ms = ms;
+        const bool span = p->op == ZS_OP_COMPRESS && zs::compress_variant_is_span(v);
+        const int ncut = span ? 2 : 1;
+        for (int c = 0; c < ncut; ++c) {
+            // cut setting c: 0 the geometry's default, 1 the opposite one
+            const uint32_t dflt = span ? zs::span_cut_default(v) : 0u;
+            p->cut_min = c == 0 ? 0 : (dflt ? -1 : (int)(3 * variant_info(p->op, v)->tile_bytes / 64));
+            double ms = 0.0;
+            bool skip = false;
+            st = time_runs(p, reps, &ms, &skip);
+            if (st != ZS_OK) {
+                p->use_graph = graph;
+                return st;
+            }
+            if (skip) break;  // this batch needs the general kernel
+            if (p->tuned_ms[v] < 0 || ms < p->tuned_ms[v]) p->tuned_ms[v] = ms;
+            if (best < 0 || ms < best_ms) {
+                best = v;
+                best_ms = ms;
+                best_cut = p->cut_min;
+            }
         }
     }
     p->use_graph = graph;
@@ -273,7 +305,82 @@ zs_status tune(zs_plan *p, int reps)
         zs::set_error("zs_plan_create: no kernel variant fits this dictionary");
         return ZS_ERR_BAD_DICT;
     }
+    p->cut_min = best_cut;
     return layout(p, best);
+}
+
+// ---- tuning cache: (GPU model, dictionary, operation, flags, batch shape class) -> (variant, cut setting).
+// The shape class is log2 of the batch's bytes, of its shard count and of its largest shard. Kept in the
+// process; with ZS_TUNE_CACHE naming a file, loaded from it once and appended to. Plans use it only when
+// their options ask (tune_cache).
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;
+bool g_tune_loaded = false;
+
+int ilog2(uint64_t x)
+{
+    int k = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++k;
+    }
+    return k;
+}
+
+std::string tune_key(const zs_plan *p)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, p->device);
+    uint64_t total = 0, mx = 0;
+    for (const zs_shard &s : p->shards) {
+        total += s.in_len;
+        mx = std::max<uint64_t>(mx, s.in_len);
+    }
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s/sm%d.%d/x%d|%016llx|%d|%u|%d|%d|%d", prop.name, prop.major, prop.minor,
+             prop.multiProcessorCount, (unsigned long long)p->d->digest, (int)p->op, p->flags, ilog2(total + 1),
+             ilog2(p->shards.size() + 1), ilog2(mx + 1));
+    for (char *c = buf; *c; ++c)
+        if (*c == ' ') *c = '_';
+    return buf;
+}
+
+void tune_cache_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("ZS_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[512];
+    int v = 0, c = 0;
+    while (fscanf(f, "%511s %d %d", key, &v, &c) == 3) g_tune[key] = {v, c};
+    fclose(f);
+}
+
+bool tune_cache_get(const std::string &k, int *v, int *c)
+{
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_cache_load();
+    auto it = g_tune.find(k);
+    if (it == g_tune.end()) return false;
+    *v = it->second.first;
+    *c = it->second.second;
+    return true;
+}
+
+void tune_cache_put(const std::string &k, int v, int c)
+{
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_cache_load();
+    g_tune[k] = {v, c};
+    const char *path = getenv("ZS_TUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE *f = fopen(path, "a")) {
+        fprintf(f, "%s %d %d\n", k.c_str(), v, c);
+        fclose(f);
+    }
 }
 
 }  // namespace
@@ -389,10 +496,21 @@ extern "C" zs_status zs_plan_create(const zs_dict *d, zs_op op, unsigned flags, 
                 st = ZS_ERR_BAD_DICT;
             } else {
                 p->tuned_ms.assign(nv, -1.0);
+                p->cut_min = opt ? opt->cut_min : 0;
                 st = layout(p, want);
             }
         } else {
-            st = tune(p, std::max(1, opt && opt->tune_reps > 0 ? opt->tune_reps : 3));
+            const bool cache = opt && opt->tune_cache;
+            const std::string key = cache ? tune_key(p) : std::string();
+            int cv = -1, cc = 0;
+            if (cache && tune_cache_get(key, &cv, &cc) && cv >= 0 && cv < nv && variant_usable(p, cv)) {
+                p->tuned_ms.assign(nv, -1.0);  // taken from the cache, not timed
+                p->cut_min = cc;
+                st = layout(p, cv);
+            } else {
+                st = tune(p, std::max(1, opt && opt->tune_reps > 0 ? opt->tune_reps : 3));
+                if (st == ZS_OK && cache) tune_cache_put(key, p->variant, p->cut_min);
+            }
         }
     }
     if (st != ZS_OK) {
@@ -422,6 +540,13 @@ extern "C" zs_status zs_plan_run(zs_plan *p, zs_result *res, void *stream)
 }
 
 extern "C" int zs_plan_variant(const zs_plan *p) { return p ? p->variant : -1; }
+
+extern "C" int zs_plan_cut_min(const zs_plan *p)
+{
+    if (!p || p->op != ZS_OP_COMPRESS || !zs::compress_variant_is_span(p->variant)) return 0;
+    if (p->cut_min > 0) return p->cut_min;
+    return p->cut_min < 0 ? 0 : (int)zs::span_cut_default(p->variant);
+}
 
 extern "C" double zs_plan_tuned_ms(const zs_plan *p, int v)
 {

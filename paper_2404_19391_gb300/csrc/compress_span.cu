@@ -2436,8 +2436,10 @@ cudaError_t sp_launch_as(const zs_dict *d, const TiledLaunch &L, unsigned flags,
     a.stall_tile = injected_stall_tile();
     // lines of at least 3/64 of a tile (1.5 lane shares) may be cut, in the geometries where that pays (Geo::kCut);
     // a target within 1/128 of a tile of a line start takes the line start
+    // the caller's threshold (a plan's tuned one), else the geometry's default; the test knob overrides both
     const int64_t cm = span_cut_min_override();
-    a.cut_min = cm >= 0 ? (uint32_t)cm : (Geo::kCut ? (uint32_t)(3 * Geo::kTile / 64) : 0u);
+    a.cut_min = L.cut_min > 0 ? (uint32_t)L.cut_min : (L.cut_min < 0 ? 0u : (Geo::kCut ? (uint32_t)(3 * Geo::kTile / 64) : 0u));
+    if (cm >= 0) a.cut_min = (uint32_t)cm;
     a.cut_slack = Geo::kTile / 128;
     const int smem = (int)sp_smem<Geo>(d);
     int dev = 0, sms = 0;
@@ -2494,12 +2496,14 @@ struct SpEntry {
     KernelVariant info;
     size_t (*smem)(const zs_dict *);
     cudaError_t (*launch)(const zs_dict *, const TiledLaunch &, unsigned, cudaStream_t);
+    uint32_t cut_default;
 };
 
 template <class Geo>
 constexpr SpEntry sp_entry(const char *name)
 {
-    return SpEntry{KernelVariant{name, Geo::kWarps, Geo::kTile}, &sp_smem<Geo>, &sp_launch<Geo>};
+    return SpEntry{KernelVariant{name, Geo::kWarps, Geo::kTile}, &sp_smem<Geo>, &sp_launch<Geo>,
+                   Geo::kCut ? (uint32_t)(3 * Geo::kTile / 64) : 0u};
 }
 
 const SpEntry kSp[] = {
@@ -2513,6 +2517,12 @@ constexpr int kNumSp = (int)(sizeof(kSp) / sizeof(kSp[0]));
 int span_variants() { return kNumSp; }
 
 const KernelVariant *span_variant(int v) { return (v >= 0 && v < kNumSp) ? &kSp[v].info : nullptr; }
+
+uint32_t span_cut_default(int v)
+{
+    if (v < 0 || v >= kNumSp) return 0;
+    return kSp[v].cut_default;
+}
 
 bool span_fits(int v, const zs_dict *d)
 {

@@ -498,6 +498,8 @@ extern "C" zs_status zs_load_dictionary(const uint8_t *file_bytes, size_t len, z
     memcpy(dec.data() + 256, pat, sizeof pat);
 
     zs_dict *d = new zs_dict();
+    d->digest = 1469598103934665603ull;  // FNV-1a, 64-bit
+    for (size_t i = 0; i < len; ++i) d->digest = (d->digest ^ file_bytes[i]) * 1099511628211ull;
     cudaError_t e = cudaGetDevice(&d->device);
     if (e != cudaSuccess) {
         delete d;

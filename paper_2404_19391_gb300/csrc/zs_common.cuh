@@ -194,6 +194,7 @@ struct zs_dict {
     uint8_t *d_dec = nullptr;  // decoder tables (kDecBytes)
     uint8_t plen[256];
     uint8_t pat[256][zs::kMaxPat];
+    uint64_t digest = 0;        // FNV-1a of the dictionary file (the plan tuning cache's key)
     zs::ScratchPool pool;
     struct zs_pipes *pipes = nullptr;  // host-to-host pipelines (pipeline.cu), made on first use
 };
@@ -586,6 +587,7 @@ struct TiledLaunch {
     DevResult *g = nullptr;  // launch-wide counters and status (the shard's own result when n_shards == 1)
     uint8_t *slow = nullptr;  // compression's long-line scratch
     uint64_t slow_cap = 0;
+    int32_t cut_min = 0;      // span kernel: shortest line cut between lanes (0: the geometry's default; < 0: never)
 };
 
 // A compiled geometry of a tiled kernel.
@@ -622,6 +624,7 @@ int span_variants();
 const KernelVariant *span_variant(int v);
 bool span_fits(int v, const zs_dict *d);
 cudaError_t launch_span(int v, const zs_dict *d, const TiledLaunch &L, unsigned flags, cudaStream_t s);
+uint32_t span_cut_default(int v);  // the geometry's default cut threshold (0: cuts off), or 0 for no such geometry
 
 // Compiled variants of the tiled compression (transducer) and decompression kernels.
 int compress_warp_variants();

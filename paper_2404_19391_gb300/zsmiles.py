@@ -41,7 +41,8 @@ class _Shard(ctypes.Structure):
 
 
 class _PlanOptions(ctypes.Structure):
-    _fields_ = [("variant", ctypes.c_int), ("use_graph", ctypes.c_int), ("tune_reps", ctypes.c_int)]
+    _fields_ = [("variant", ctypes.c_int), ("use_graph", ctypes.c_int), ("tune_reps", ctypes.c_int),
+                ("cut_min", ctypes.c_int), ("tune_cache", ctypes.c_int)]
 
 
 class _ServerOptions(ctypes.Structure):
@@ -111,6 +112,7 @@ def load_library(rebuild: bool = False) -> ctypes.CDLL:
                                           ctypes.POINTER(_PlanOptions), ctypes.POINTER(vp)]),
         "zs_plan_run": (ctypes.c_int, [vp, pres, vp]),
         "zs_plan_variant": (ctypes.c_int, [vp]),
+        "zs_plan_cut_min": (ctypes.c_int, [vp]),
         "zs_plan_tuned_ms": (ctypes.c_double, [vp, ctypes.c_int]),
         "zs_plan_last_ms": (ctypes.c_double, [vp]),
         "zs_plan_destroy": (None, [vp]),
@@ -294,11 +296,11 @@ class Plan:
     """zs_plan_create / zs_plan_run / zs_plan_destroy over a fixed list of (in, out, index) tensors."""
 
     def __init__(self, d: Dictionary, op: int, shards, flags: int = PREPROCESS, variant: int = -1,
-                 use_graph: bool = True, tune_reps: int = 3):
+                 use_graph: bool = True, tune_reps: int = 3, cut_min: int = 0, tune_cache: bool = False):
         self._keep = list(shards)  # the tensors must outlive the plan
         self.n = len(shards)
         arr = _shards(shards)
-        opt = _PlanOptions(variant, 1 if use_graph else 0, tune_reps)
+        opt = _PlanOptions(variant, 1 if use_graph else 0, tune_reps, cut_min, 1 if tune_cache else 0)
         h = ctypes.c_void_p()
         _check(_L().zs_plan_create(d.handle, op, flags, arr, self.n, ctypes.byref(opt), ctypes.byref(h)))
         self.handle = h
@@ -313,6 +315,11 @@ class Plan:
     @property
     def variant(self) -> int:
         return int(_L().zs_plan_variant(self.handle))
+
+    @property
+    def cut_min(self) -> int:
+        """The span cut threshold the plan runs with, in bytes (0: no cuts)."""
+        return int(_L().zs_plan_cut_min(self.handle))
 
     def tuned_ms(self, v: int) -> float:
         return float(_L().zs_plan_tuned_ms(self.handle, v))

@@ -238,3 +238,46 @@ def test_plan_argument_errors(zs, dicts):
     assert ei.value.status == zs.ERR_INVALID_ARG
     p = zs.Plan(d, zs.OP_COMPRESS, [], variant=0)
     assert p.run() == []
+
+
+def test_tuned_cut_setting_and_tuning_cache(zs, dicts, tmp_path):
+    """Autotuning also times the span geometries' long-line cut setting both ways; with tune_cache, a second
+    plan of the same shape takes the choice from the cache (untimed) and the cache file records it; a fixed
+    span variant runs with cuts forced off or at a given threshold, all with oracle parity."""
+    import os
+    d, od = dicts
+    raws = [bytes(synth.generate(synth.CFG3, 0, 4000)), bytes(synth.generate(synth.CFG3, 4000, 2500))]
+    exp = [oracle.compress_stream(od, np.frombuffer(b, dtype=np.uint8), 1) for b in raws]
+    path = tmp_path / "tune.txt"
+    old = os.environ.get("ZS_TUNE_CACHE")
+    os.environ["ZS_TUNE_CACHE"] = str(path)
+    try:
+        nv = zs.zs_kernel_variants(zs.OP_COMPRESS)
+        shards, outs, idxs = _compress_shards(zs, raws)
+        p = zs.Plan(d, zs.OP_COMPRESS, shards, flags=1, variant=-1, tune_reps=1, tune_cache=True)
+        v, c = p.variant, p.cut_min
+        assert all(p.tuned_ms(k) > 0 for k in range(nv))
+        _check_compressed(p.run(), shards, outs, idxs, exp)
+        p.close()
+        shards, outs, idxs = _compress_shards(zs, raws)
+        q = zs.Plan(d, zs.OP_COMPRESS, shards, flags=1, variant=-1, tune_cache=True)
+        assert (q.variant, q.cut_min) == (v, c)
+        assert all(q.tuned_ms(k) < 0 for k in range(nv))
+        _check_compressed(q.run(), shards, outs, idxs, exp)
+        q.close()
+        lines = path.read_text().split("\n")
+        assert len([l for l in lines if l.strip()]) == 1 and lines[0].split()[1:] == [str(v), str(c)]
+    finally:
+        if old is None:
+            os.environ.pop("ZS_TUNE_CACHE", None)
+        else:
+            os.environ["ZS_TUNE_CACHE"] = old
+    for sv in range(nv):
+        if "span" not in zs.zs_kernel_variant_name(zs.OP_COMPRESS, sv):
+            continue
+        for cm in (-1, 64):
+            shards, outs, idxs = _compress_shards(zs, raws)
+            r = zs.Plan(d, zs.OP_COMPRESS, shards, flags=1, variant=sv, use_graph=False, cut_min=cm)
+            assert r.cut_min == (0 if cm < 0 else cm)
+            _check_compressed(r.run(), shards, outs, idxs, exp)
+            r.close()
