@@ -36,6 +36,79 @@ struct DxGeom {
 };
 
 constexpr unsigned kAllX = 0xffffffffu;
+
+// Look-back records of this decoder: the first two words of a TileState, each single-copy atomic with its own
+// valid bit: agg_a = the tile's output bytes (its aggregate), agg_b = the output bytes of tiles [0, this] (its
+// inclusive prefix). One 16-byte load reads a record. Newlines are not carried: each tile adds its count to the
+// shard's result with one atomic add.
+__device__ __forceinline__ void dx_publish(TileState *ts, bool inclusive, uint64_t v)
+{
+    unsigned long long *p = inclusive ? &ts->agg_b : &ts->agg_a;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"((unsigned long long)(v | kValidBit)) : "memory");
+}
+
+// Decoupled look-back by a whole warp over these records: each round trip, lane j reads the records of tiles
+// t-1-j-32r for r < R, 32 R predecessors a trip. Sums aggregates from the nearest predecessor back to (and
+// including) the nearest inclusive prefix. Every tile publishes its aggregate before it expands (a size pass),
+// so the walk seldom waits; what it costs is round trips, and with thousands of tiles in flight the nearest
+// inclusive prefix can be hundreds of tiles back. Called by all 32 lanes; all return the same sum. Waits are
+// bounded (kStTimeout on expiry).
+template <int R>
+__device__ __forceinline__ uint64_t dx_lookback(TileState *tiles, uint64_t t, uint64_t limit_ns, uint32_t *status)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint64_t a = 0;
+    int64_t top = (int64_t)t - 1;
+    uint64_t t0 = 0;
+    bool timed = false;
+    while (top >= 0) {
+        uint64_t v[R];
+        uint32_t incl = 0, none = 0;  // bit r: record r holds an inclusive prefix / nothing yet
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t p = top - (int64_t)lane - 32 * r;
+            unsigned long long g = 0, i = kValidBit;  // before tile 0: an inclusive zero
+            if (p >= 0) ld_pair(&tiles[p].agg_a, &g, &i);
+            const bool fi = (i & kValidBit) != 0, fg = (g & kValidBit) != 0;
+            incl |= (fi ? 1u : 0u) << r;
+            none |= (!fi && !fg ? 1u : 0u) << r;
+            v[r] = (fi ? i : g) & ~kValidBit;
+        }
+        // distance (32 r + lane) of the nearest record holding an inclusive prefix
+        int stop = 32 * R;
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r) {
+            const uint32_t b = __ballot_sync(kAllX, (incl >> r) & 1u);
+            if (b) stop = 32 * r + __ffs(b) - 1;
+        }
+        bool missing = false;  // a nearer tile has published nothing
+#pragma unroll
+        for (int r = 0; r < R; ++r) missing |= (32 * r + (int)lane < stop) && ((none >> r) & 1u);
+        if (__any_sync(kAllX, missing)) {
+            if (*((volatile uint32_t *)status) & kStTimeout) break;
+            if (!timed) {
+                t0 = gtime();
+                timed = true;
+            } else if (gtime() - t0 > limit_ns) {
+                if (lane == 0) atomicOr(status, kStTimeout);
+                break;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        timed = false;
+        uint64_t sa = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (32 * r + (int)lane <= stop) sa += v[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(kAllX, sa, o);
+        a += sa;
+        if (stop < 32 * R) break;
+        top -= 32 * R;
+    }
+    return a;
+}
 constexpr uint32_t kCopies = 16;       // replicas of the pattern table
 constexpr uint32_t kFlag = 0x40000000u; // entry flag (top word): ' ' or a byte that is no symbol
 
@@ -58,6 +131,8 @@ struct DX {
     static constexpr int kTB = Geo::kTile;
     static constexpr int kOutB = Geo::kOut;
     static constexpr int kRounds = kTB / 512;
+    // look-back records per lane per round trip: 8 (256 tiles a trip) where registers allow, else 4 or 2
+    static constexpr int kLbR = kW >= 24 ? (Geo::kOr ? 4 : 2) : 8;
     static_assert(kTB % 512 == 0 && kOutB % 16 == 0, "expansion geometry");
 
     struct alignas(16) OutSlot {
@@ -264,6 +339,51 @@ struct DX {
         }
     }
 
+    // Size pass over a staged tile: output bytes and newlines, from the top words of the entries alone (chunks
+    // holding ' ' or a byte that is no symbol take the byte loop, which also notes malformed bytes). Every lane
+    // returns the tile's totals. It runs before the expansion so that the tile's aggregate is published early
+    // and the look-backs of later tiles seldom wait.
+    static __device__ __forceinline__ void tile_sizes(const Ctx &C, uint64_t base, uint32_t nown, uint32_t *total,
+                                                      uint32_t *nls)
+    {
+        const uint8_t *in = C.M->in + 16;
+        uint32_t ob = 0, nl = 0;
+        for (int r = 0; r < kRounds; ++r) {
+            if ((uint32_t)r * 512u >= nown) break;
+            const uint32_t c0 = (uint32_t)r * 512u + C.lane * 16u;
+            const uint32_t p0 = min(c0, nown), p1 = min(c0 + 16u, nown);
+            if (p1 <= p0) continue;
+            bool fast = p1 - p0 == 16 && in[(int32_t)c0 - 1] != kEsc;
+            if (fast) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(in + c0);
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                uint32_t acc = 0, fl = 0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const uint32_t b = (w[k >> 2] >> (8 * (k & 3))) & 255u;
+                    const uint32_t e = *reinterpret_cast<const uint32_t *>(C.tab + ((b << 7) | C.lane8) + 4);
+                    acc += e >> 24;
+                    fl |= e;
+                }
+                if (fl & kFlag) {
+                    fast = false;
+                } else {
+                    ob += acc & 127u;
+                    nl += acc >> 7;
+                }
+            }
+            if (!fast) {
+                bool lit = literal_at(C, base, p0);
+                uint32_t o1 = 0, n1 = 0;
+                slow_size(C, base, p0, p1, &lit, &o1, &n1);
+                ob += o1;
+                nl += n1;
+            }
+        }
+        *total = __reduce_add_sync(kAllX, ob);
+        *nls = __reduce_add_sync(kAllX, nl);
+    }
+
     // Funnel of patterns [k0, k0 + 8) of a fast chunk into aligned words of the stage from byte offset pos:
     // the chunk's two halves are two independent chains, interleaved. A chain's first word may start below
     // its first byte: those bytes (of the chain or lane before) are written as zeros here, or taken from the
@@ -408,12 +528,14 @@ struct DX {
         __syncwarp();
     }
 
-    static __device__ __forceinline__ void finish_result(const Ctx &C, uint64_t t, uint64_t tot_a, uint64_t tot_b)
+    // The shard's last tile writes the output size and counts the unterminated last line (newlines are added
+    // to n_lines tile by tile).
+    static __device__ __forceinline__ void finish_result(const Ctx &C, uint64_t t, uint64_t tot_a)
     {
         const ShardView &A = *C.A;
         if (C.lane == 0 && t == A.ntiles - 1) {
             A.res->out_len = tot_a;
-            A.res->n_lines = tot_b + ((A.in[A.n - 1] != kNl) ? 1u : 0u);
+            if (A.in[A.n - 1] != kNl) atomicAdd(&A.res->n_lines, 1ull);
         }
     }
 
@@ -421,11 +543,10 @@ struct DX {
     {
         const ShardView &A = *C.A;
         const uint64_t t = O.t;
-        uint64_t ea = 0, eb = 0;
-        if (t > 0) lookback_warp(A.tiles, t, &ea, &eb, C.P->limit_ns, C.status);
-        if (C.lane == 0 && t > 0 && (int64_t)t != C.P->stall_tile) publish(&A.tiles[t], 2u, ea + O.total, eb + O.nls);
+        const uint64_t ea = t > 0 ? dx_lookback<kLbR>(A.tiles, t, C.P->limit_ns, C.status) : 0;
+        if (C.lane == 0 && t > 0 && (int64_t)t != C.P->stall_tile) dx_publish(&A.tiles[t], true, ea + O.total);
         if (O.total) warp_copy_realign(O.out, O.total, A.out + ea, A.out_cap > ea ? A.out_cap - ea : 0);
-        finish_result(C, t, ea + O.total, eb + O.nls);
+        finish_result(C, t, ea + O.total);
         __syncwarp();
     }
 
@@ -498,13 +619,18 @@ struct DX {
             ph ^= 1u;
             __syncwarp();
             uint32_t total = 0, nls = 0;
-            const bool fits = expand(Cs, O, t, nown, &total, &nls);
+            tile_sizes(Cs, base, nown, &total, &nls);
+            if (lane == 0) {
+                if ((int64_t)t != P->stall_tile) dx_publish(&O.sv.tiles[t], t == 0, total);
+                if (nls) atomicAdd(&O.sv.res->n_lines, (unsigned long long)nls);
+            }
+            uint32_t etotal = 0, enls = 0;
+            const bool fits = expand(Cs, O, t, nown, &etotal, &enls);
             if (lane == 0) {
                 O.t = t;
                 O.total = total;
                 O.nls = nls;
                 O.direct = fits ? 0u : 1u;
-                if ((int64_t)t != P->stall_tile) publish(&O.sv.tiles[t], t == 0 ? 2u : 1u, total, nls);
             }
             __syncwarp();
             if (pending) {
@@ -518,11 +644,10 @@ struct DX {
                 continue;
             }
             if (!fits) {  // look back first, then write straight to memory
-                uint64_t ea = 0, eb = 0;
-                if (t > 0) lookback_warp(O.sv.tiles, t, &ea, &eb, P->limit_ns, C.status);
-                if (lane == 0 && t > 0 && (int64_t)t != P->stall_tile) publish(&O.sv.tiles[t], 2u, ea + total, eb + nls);
+                const uint64_t ea = t > 0 ? dx_lookback<kLbR>(O.sv.tiles, t, P->limit_ns, C.status) : 0;
+                if (lane == 0 && t > 0 && (int64_t)t != P->stall_tile) dx_publish(&O.sv.tiles[t], true, ea + total);
                 expand_direct(Cs, t, nown, ea);
-                finish_result(Cs, t, ea + total, eb + nls);
+                finish_result(Cs, t, ea + total);
                 __syncwarp();
             } else {
                 pending = true;
@@ -546,13 +671,16 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) decompress_expand_kernel(
 
 // Compiled geometries, all with 2048-byte tiles (four rounds) and stages of 2.25 x the tile beside the 36 KB of
 // tables: one stage and 24 warps per SM (more warps to hide latency, the look-back not pipelined), patterns
-// ORed in or funnelled; and two stages (pipelined look-back) with 16 warps, ORed in.
+// ORed in or funnelled; two stages (pipelined look-back) with 16 warps, ORed in; one stage with 20 warps
+// (registers for the widest look-back), ORed in.
 using DxV0 = DxGeom<24, 2048, 4608, 1, true>;
 using DxV1 = DxGeom<24, 2048, 4608, 1, false>;
 using DxV2 = DxGeom<16, 2048, 4608, 2, true>;
+using DxV3 = DxGeom<20, 2048, 4608, 1, true>;
 static_assert(DxV0::kWarps * sizeof(DX<DxV0>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
 static_assert(DxV1::kWarps * sizeof(DX<DxV1>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
 static_assert(DxV2::kWarps * sizeof(DX<DxV2>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
+static_assert(DxV3::kWarps * sizeof(DX<DxV3>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
 
 template <class Geo>
 size_t dx_smem()
@@ -606,6 +734,7 @@ const DxEntry kDx[] = {
     dx_entry<DxV0>("decompress expand w24 t2048 or"),
     dx_entry<DxV1>("decompress expand w24 t2048 funnel"),
     dx_entry<DxV2>("decompress expand w16 t2048 or 2-stage"),
+    dx_entry<DxV3>("decompress expand w20 t2048 or"),
 };
 constexpr int kNumDx = (int)(sizeof(kDx) / sizeof(kDx[0]));
 
