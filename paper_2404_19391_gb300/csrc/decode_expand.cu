@@ -2,16 +2,16 @@
 //
 //   - Tiles and look-back as in the other tiled kernels: each warp of a persistent CTA claims tiles in
 //     launch order, stages one (and the 16 bytes before it) with one bulk (TMA) copy, and resolves its
-//     output offset by a warp-wide decoupled look-back one tile behind the one it expands (software
-//     pipeline: two output stages per warp).
+//     output offset by a warp-wide decoupled look-back. The next tile is claimed and its copy issued as soon
+//     as the current one has expanded, so the copy lands while the warp looks back and copies out.
 //   - Rounds: lane l takes the 16 bytes at 16 l of each 512-byte round (conflict-free 16-byte loads) and
 //     looks up the 16 patterns at once. Each 64-bit entry holds the pattern (up to 7 bytes) and, in its top
 //     byte, its length plus 128 for '\n', so one sum gives the lane's output bytes and newlines; ' ' and
 //     bytes that are no symbol carry a flag instead, and such chunks (rare in SMILES text) take a byte loop.
 //     The table is replicated 16 times so that the 16 lanes of each half-warp read 16 different bank pairs.
-//   - A warp scan places the lanes; each lane funnels its patterns from registers into aligned 32-bit
-//     stores of the tile's output stage. A lane's first word may hold bytes of the lane before it, which
-//     that lane writes byte by byte after the warp's word stores.
+//   - A size pass over the entries' top words gives each lane's output bytes per round, a warp scan per
+//     round places the lanes, and the tile publishes its size before it expands; the expansion then ORs
+//     each pattern into a cleared stage at its own offset (no chain from one pattern to the next).
 //   - Escapes need no sequential scan: a byte is verbatim exactly when the run of ' ' before it has odd
 //     length (every unescaped ' ' escapes the next byte, and a run starts unescaped).
 //   - The stage leaves with aligned 16-byte stores once the look-back has given the tile's offset; a tile
@@ -23,19 +23,24 @@
 namespace zs {
 namespace {
 
-template <int W, int TB, int OUTB, int SLOTS, bool ORW>
+template <int W, int TB, int OUTB, int SLOTS>
 struct DxGeom {
     static constexpr int kWarps = W;    // warps per CTA (one CTA per SM)
     static constexpr int kTile = TB;    // compressed bytes per warp tile
     static constexpr int kOut = OUTB;   // staged output bytes per tile
     static constexpr int kSlots = SLOTS;  // 2: a tile's look-back and copy-out wait until the next tile is
                                           // expanded (software pipeline); 1: they follow at once
-    static constexpr bool kOr = ORW;    // patterns land by shared-memory atomic OR into a cleared stage, each at
-                                        // its own offset (no chain from one pattern to the next); else by
-                                        // a funnel of aligned word stores
 };
 
 constexpr unsigned kAllX = 0xffffffffu;
+
+// *[addr] |= v in shared memory (32-bit shared-window address) when p holds: one predicated reduction, no branch.
+__device__ __forceinline__ void red_or_shared(uint32_t addr, uint32_t v, bool p)
+{
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q red.shared.or.b32 [%0], %1; }" ::"r"(addr), "r"(v),
+                 "r"((uint32_t)p)
+                 : "memory");
+}
 
 // Look-back records of this decoder: the first two words of a TileState, each single-copy atomic with its own
 // valid bit: agg_a = the tile's output bytes (its aggregate), agg_b = the output bytes of tiles [0, this] (its
@@ -131,23 +136,24 @@ struct DX {
     static constexpr int kTB = Geo::kTile;
     static constexpr int kOutB = Geo::kOut;
     static constexpr int kRounds = kTB / 512;
-    // look-back records per lane per round trip: 8 (256 tiles a trip) where registers allow, else 4 or 2
-    static constexpr int kLbR = kW >= 24 ? (Geo::kOr ? 4 : 2) : 8;
+    // look-back records per lane per round trip: 8 (256 tiles a trip) where registers allow, else 4
+    static constexpr int kLbR = kW >= 24 ? 4 : 8;
     static_assert(kTB % 512 == 0 && kOutB % 16 == 0, "expansion geometry");
 
     struct alignas(16) OutSlot {
-        uint8_t out[kOutB + 32];
-        uint64_t t;
-        uint32_t total, nls;
-        uint32_t direct, _pad;
+        uint8_t out[kOutB + 32];  // the tile's output at stage offset o = (destination address mod 16)
         ShardView sv;
     };
 
     struct alignas(16) WarpMem {
         uint8_t in[16 + kTB + 16];  // the 16 bytes before the tile, the tile
         OutSlot os[Geo::kSlots];
+        ShardView nsv;              // shard of the staged tile (copied to its output slot when it expands)
+        uint32_t pw[kRounds][32];   // from the size pass: lane's output offset in the round | kSlowChunk
+        uint32_t run[kRounds];      // from the size pass: the round's output offset in the tile
         uint64_t bar;
     };
+    static constexpr uint32_t kSlowChunk = 0x80000000u;
 
     struct Ctx {
         const DxArgs *P;
@@ -290,69 +296,22 @@ struct DX {
         }
     }
 
-    // One round's lanes: the chunk of lane `lane`, its 16 entries (fast path) or the byte-loop sizes.
-    struct Chunk {
-        uint32_t lo[16], hi[16];
-        uint32_t p0, p1;   // tile offsets of the chunk's valid bytes
-        uint32_t outb, nls;
-        bool fast, lit;
-    };
-
-    static __device__ __forceinline__ void load_chunk(const Ctx &C, uint64_t base, uint32_t nown, uint32_t r, Chunk &K)
-    {
-        const uint32_t c0 = (uint32_t)r * 512u + C.lane * 16u;
-        K.p0 = min(c0, nown);
-        K.p1 = min(c0 + 16u, nown);
-        K.outb = K.nls = 0;
-        K.lit = false;
-        K.fast = false;
-        if (K.p1 <= K.p0) return;
-        const uint8_t *in = C.M->in + 16;
-        K.fast = K.p1 - K.p0 == 16 && in[(int32_t)c0 - 1] != kEsc;
-        if (K.fast) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(in + c0);
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-            uint32_t acc = 0, fl = 0;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint32_t b = (w[k >> 2] >> (8 * (k & 3))) & 255u;
-                const uint2 e = *reinterpret_cast<const uint2 *>(C.tab + ((b << 7) | C.lane8));
-                K.lo[k] = e.x;
-                K.hi[k] = e.y;
-                acc += e.y >> 24;
-                fl |= e.y;
-            }
-            if (fl & kFlag) {
-                K.fast = false;
-            } else {
-                K.outb = acc & 127u;
-                K.nls = acc >> 7;
-                return;
-            }
-        }
-        K.lit = literal_at(C, base, K.p0);
-        bool lit = K.lit;
-        slow_size(C, base, K.p0, K.p1, &lit, &K.outb, &K.nls);
-        if (lit && base + K.p1 == C.A->n) {  // the stream ends in an unpaired escape
-            note_error_offset(C.A->res, C.A->n - 1);
-            atomicOr(C.status, kStMalformed);
-        }
-    }
-
-    // Size pass over a staged tile: output bytes and newlines, from the top words of the entries alone (chunks
-    // holding ' ' or a byte that is no symbol take the byte loop, which also notes malformed bytes). Every lane
-    // returns the tile's totals. It runs before the expansion so that the tile's aggregate is published early
-    // and the look-backs of later tiles seldom wait.
+    // Size pass over a staged tile, from the top words of the entries alone (chunks holding ' ' or a byte that
+    // is no symbol take the byte loop, which also notes malformed bytes): each lane's output offset in each
+    // round (warp scan) into pw, each round's offset in the tile into run; every lane returns the tile's
+    // totals. It runs before the expansion so that the tile's size is published early and the look-backs of
+    // later tiles seldom wait.
     static __device__ __forceinline__ void tile_sizes(const Ctx &C, uint64_t base, uint32_t nown, uint32_t *total,
                                                       uint32_t *nls)
     {
-        const uint8_t *in = C.M->in + 16;
-        uint32_t ob = 0, nl = 0;
+        WarpMem &M = *C.M;
+        const uint8_t *in = M.in + 16;
+        uint32_t run = 0, nl = 0;
         for (int r = 0; r < kRounds; ++r) {
             if ((uint32_t)r * 512u >= nown) break;
             const uint32_t c0 = (uint32_t)r * 512u + C.lane * 16u;
             const uint32_t p0 = min(c0, nown), p1 = min(c0 + 16u, nown);
-            if (p1 <= p0) continue;
+            uint32_t ob = 0;
             bool fast = p1 - p0 == 16 && in[(int32_t)c0 - 1] != kEsc;
             if (fast) {
                 const uint4 v = *reinterpret_cast<const uint4 *>(in + c0);
@@ -368,162 +327,103 @@ struct DX {
                 if (fl & kFlag) {
                     fast = false;
                 } else {
-                    ob += acc & 127u;
+                    ob = acc & 127u;
                     nl += acc >> 7;
                 }
             }
-            if (!fast) {
+            if (!fast && p1 > p0) {
                 bool lit = literal_at(C, base, p0);
-                uint32_t o1 = 0, n1 = 0;
-                slow_size(C, base, p0, p1, &lit, &o1, &n1);
-                ob += o1;
+                uint32_t n1 = 0;
+                slow_size(C, base, p0, p1, &lit, &ob, &n1);
                 nl += n1;
+                if (lit && base + p1 == C.A->n) {  // the stream ends in an unpaired escape
+                    note_error_offset(C.A->res, C.A->n - 1);
+                    atomicOr(C.status, kStMalformed);
+                }
             }
+            const uint32_t inc = warp_incl_u32(ob);
+            M.pw[r][C.lane] = (inc - ob) | (fast ? 0u : kSlowChunk);
+            if (C.lane == 31) M.run[r] = run;
+            run += __shfl_sync(kAllX, inc, 31);
         }
-        *total = __reduce_add_sync(kAllX, ob);
+        __syncwarp();
+        *total = run;
         *nls = __reduce_add_sync(kAllX, nl);
     }
 
-    // Funnel of patterns [k0, k0 + 8) of a fast chunk into aligned words of the stage from byte offset pos:
-    // the chunk's two halves are two independent chains, interleaved. A chain's first word may start below
-    // its first byte: those bytes (of the chain or lane before) are written as zeros here, or taken from the
-    // stage when `first` (the round's first byte: the previous round's bytes are already there). Each chain's
-    // last partial word is left in *a, *wpos, *n for the second phase.
-    struct Funnel {
-        uint32_t a, wpos, n, p0;
-    };
-
-    static __device__ __forceinline__ void funnel2(const Chunk &K, uint8_t *stg, uint32_t pos, bool first,
-                                                   Funnel &F0, Funnel &F1)
-    {
-        uint32_t half = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) half += (K.hi[k] >> 24) & 7u;
-        F0.p0 = pos;
-        F1.p0 = pos + half;
-        F0.wpos = pos & ~3u;
-        F0.n = pos & 3u;
-        F1.wpos = F1.p0 & ~3u;
-        F1.n = F1.p0 & 3u;
-        F0.a = (first && F0.n) ? *reinterpret_cast<const uint32_t *>(stg + F0.wpos) & ((1u << (8 * F0.n)) - 1u) : 0u;
-        F1.a = 0;
-        auto push = [&](Funnel &F, uint32_t lo, uint32_t hi) {
-            const uint32_t len = (hi >> 24) & 7u;
-            const uint32_t h = hi & 0x00FFFFFFu;
-            const uint32_t sh = 8u * F.n;
-            const uint32_t w0 = F.a | (lo << sh);
-            const uint32_t w1 = __funnelshift_l(lo, h, sh);
-            const uint32_t w2 = __funnelshift_l(h, 0u, sh);
-            const uint32_t tot = F.n + len;
-            if (tot >= 4) *reinterpret_cast<uint32_t *>(stg + F.wpos) = w0;
-            if (tot >= 8) *reinterpret_cast<uint32_t *>(stg + F.wpos + 4) = w1;
-            F.a = tot >= 8 ? w2 : (tot >= 4 ? w1 : w0);
-            F.n = tot & 3u;
-            F.wpos += tot & ~3u;
-        };
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            push(F0, K.lo[k], K.hi[k]);
-            push(F1, K.lo[8 + k], K.hi[8 + k]);
-        }
-    }
-
     // Each pattern of a fast chunk ORed into the (cleared) stage at its own offset: the offsets are a prefix of
-    // the lengths, so the 16 patterns are independent; a pattern's up to 7 bytes touch at most three words.
-    static __device__ __forceinline__ void or_patterns(const Chunk &K, uint8_t *stg, uint32_t pos)
+    // the lengths, so the 16 patterns are independent. A pattern's up to 7 bytes touch two words, or three when
+    // it starts late in a word and is 6 or 7 bytes long; the second word takes an OR of zero when the pattern
+    // ends in the first (no branch), the third a predicated one.
+    static __device__ __forceinline__ void or_patterns(const uint32_t (&lo)[16], const uint32_t (&hi)[16],
+                                                       uint32_t q)
     {
-        uint32_t *w32 = reinterpret_cast<uint32_t *>(stg);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const uint32_t len = (K.hi[k] >> 24) & 7u;
-            const uint32_t h = K.hi[k] & 0x00FFFFFFu;
-            const uint32_t sh = 8u * (pos & 3u);
-            uint32_t *q = w32 + (pos >> 2);
-            atomicOr(q, K.lo[k] << sh);
-            const uint32_t end = (pos & 3u) + len;  // bytes from the first word's start
-            if (end > 4) atomicOr(q + 1, __funnelshift_l(K.lo[k], h, sh));
-            if (end > 8) atomicOr(q + 2, __funnelshift_l(h, 0u, sh));
-            pos += len;
+            const uint32_t len = (hi[k] >> 24) & 7u;
+            const uint32_t h = hi[k] & 0x00FFFFFFu;
+            const uint32_t o = q & 3u;
+            const uint32_t sh = 8u * o;
+            const uint32_t w = q & ~3u;
+            red_or_shared(w, lo[k] << sh, true);
+            red_or_shared(w + 4u, __funnelshift_l(lo[k], h, sh), true);
+            red_or_shared(w + 8u, __funnelshift_l(h, 0u, sh), o + len > 8u);
+            q += len;
         }
     }
 
-    // Second phase: a chain's last partial word, byte by byte, never below the chain's first byte.
-    static __device__ __forceinline__ void funnel_tail(uint8_t *stg, const Funnel &F)
+    // Expansion of a sized tile into slot O's stage (which must hold total + 32 bytes): per round, each lane
+    // looks up its 16 patterns and ORs them in at the offset the size pass gave it.
+    static __device__ __forceinline__ void expand(const Ctx &C, OutSlot &O, uint64_t base, uint32_t nown,
+                                                  uint32_t total)
     {
-        const uint32_t j0 = F.wpos == (F.p0 & ~3u) ? (F.p0 & 3u) : 0u;
-        for (uint32_t j = j0; j < F.n; ++j) stg[F.wpos + j] = (uint8_t)(F.a >> (8 * j));
-    }
-
-    // Sizes of one round, warp scan; returns the round's total; *pos = the lane's output offset in the round.
-    static __device__ __forceinline__ uint32_t place(const Ctx &C, const Chunk &K, uint32_t *pos)
-    {
-        const uint32_t inc = warp_incl_u32(K.outb);
-        *pos = inc - K.outb;
-        return __shfl_sync(kAllX, inc, 31);
-    }
-
-    // Expansion of a tile into slot O's stage. Returns false (nothing more written) once the tile outgrows
-    // the stage; *total and *nls are the tile's totals either way.
-    static __device__ bool expand(const Ctx &C, OutSlot &O, uint64_t t, uint32_t nown, uint32_t *total_out,
-                                  uint32_t *nls_out)
-    {
-        const uint64_t base = t * (uint64_t)kTB;
+        const WarpMem &M = *C.M;
+        const uint8_t *in = M.in + 16;
         uint8_t *stg = O.out;
-        uint32_t run = 0, nls = 0;
-        bool fits = true;
-        if (Geo::kOr) {  // patterns are ORed in: the stage starts at zero
-            uint4 *s16 = reinterpret_cast<uint4 *>(stg);
-            for (uint32_t j = C.lane; j < (uint32_t)(kOutB + 32) / 16; j += 32) s16[j] = make_uint4(0, 0, 0, 0);
-            __syncwarp();
-        }
+        uint4 *s16 = reinterpret_cast<uint4 *>(stg);
+        const uint32_t nclear = (total + 12u + 15u) / 16u;  // patterns OR zeros up to 12 bytes past the end
+        for (uint32_t j = C.lane; j < nclear; j += 32) s16[j] = make_uint4(0, 0, 0, 0);
+        __syncwarp();
+        const uint32_t sbase = smem_u32(stg);
         for (int r = 0; r < kRounds; ++r) {
             if ((uint32_t)r * 512u >= nown) break;
-            Chunk K;
-            load_chunk(C, base, nown, (uint32_t)r, K);
-            uint32_t pos;
-            const uint32_t rt = place(C, K, &pos);
-            nls += K.nls;
-            if (fits && run + rt + 32u > (uint32_t)kOutB) fits = false;
-            if (fits && Geo::kOr) {
-                if (K.fast) or_patterns(K, stg, run + pos);
-                else if (K.p1 > K.p0) slow_or(C, K.p0, K.p1, K.lit, run + pos, stg);
-                __syncwarp();
-            } else if (fits) {
-                Funnel F0, F1;
-                if (K.fast) funnel2(K, stg, run + pos, pos == 0, F0, F1);
-                __syncwarp();
-                if (K.fast) {  // the chains' pending partial words
-                    funnel_tail(stg, F0);
-                    funnel_tail(stg, F1);
-                } else if (K.p1 > K.p0) {
-                    slow_write<true>(C, K.p0, K.p1, K.lit, run + pos, stg, 0);
+            const uint32_t c0 = (uint32_t)r * 512u + C.lane * 16u;
+            const uint32_t p0 = min(c0, nown), p1 = min(c0 + 16u, nown);
+            if (p1 <= p0) continue;
+            const uint32_t pw = M.pw[r][C.lane];
+            const uint32_t pos = M.run[r] + (pw & ~kSlowChunk);
+            if (!(pw & kSlowChunk)) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(in + c0);
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                uint32_t lo[16], hi[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const uint32_t b = (w[k >> 2] >> (8 * (k & 3))) & 255u;
+                    const uint2 e = *reinterpret_cast<const uint2 *>(C.tab + ((b << 7) | C.lane8));
+                    lo[k] = e.x;
+                    hi[k] = e.y;
                 }
-                __syncwarp();
+                or_patterns(lo, hi, sbase + pos);
+            } else {
+                slow_or(C, p0, p1, literal_at(C, base, p0), pos, stg);
             }
-            run += rt;
         }
-        *total_out = run;
-        *nls_out = __reduce_add_sync(kAllX, nls);
-        return fits;
+        __syncwarp();
     }
 
-    // A tile that outgrew its stage: sizes again round by round, bytes straight to out[ea + ...].
-    static __device__ void expand_direct(const Ctx &C, uint64_t t, uint32_t nown, uint64_t ea)
+    // A tile that outgrew its stage: the byte loop of every chunk, at the offsets of the size pass, straight to
+    // out[ea + ...].
+    static __device__ void expand_direct(const Ctx &C, uint64_t base, uint32_t nown, uint64_t ea)
     {
-        const uint64_t base = t * (uint64_t)kTB;
-        uint32_t run = 0;
+        const WarpMem &M = *C.M;
         for (int r = 0; r < kRounds; ++r) {
             if ((uint32_t)r * 512u >= nown) break;
-            Chunk K;
-            load_chunk(C, base, nown, (uint32_t)r, K);
-            uint32_t pos;
-            const uint32_t rt = place(C, K, &pos);
-            if (K.p1 > K.p0) {
-                bool lit = K.fast ? false : K.lit;
-                if (K.fast) lit = false;
-                slow_write<false>(C, K.p0, K.p1, lit, run + pos, nullptr, ea);
-            }
-            run += rt;
+            const uint32_t c0 = (uint32_t)r * 512u + C.lane * 16u;
+            const uint32_t p0 = min(c0, nown), p1 = min(c0 + 16u, nown);
+            if (p1 <= p0) continue;
+            const uint32_t pw = M.pw[r][C.lane];
+            const bool lit = (pw & kSlowChunk) ? literal_at(C, base, p0) : false;
+            slow_write<false>(C, p0, p1, lit, M.run[r] + (pw & ~kSlowChunk), nullptr, ea);
         }
         __syncwarp();
     }
@@ -539,14 +439,14 @@ struct DX {
         }
     }
 
-    static __device__ void finish_staged(const Ctx &C, OutSlot &O)
+    // Look-back, inclusive prefix, copy-out of a staged tile.
+    static __device__ void finish_staged(const Ctx &C, OutSlot &O, uint64_t t, uint32_t total)
     {
         const ShardView &A = *C.A;
-        const uint64_t t = O.t;
         const uint64_t ea = t > 0 ? dx_lookback<kLbR>(A.tiles, t, C.P->limit_ns, C.status) : 0;
-        if (C.lane == 0 && t > 0 && (int64_t)t != C.P->stall_tile) dx_publish(&A.tiles[t], true, ea + O.total);
-        if (O.total) warp_copy_realign(O.out, O.total, A.out + ea, A.out_cap > ea ? A.out_cap - ea : 0);
-        finish_result(C, t, ea + O.total);
+        if (C.lane == 0 && t > 0 && (int64_t)t != C.P->stall_tile) dx_publish(&A.tiles[t], true, ea + total);
+        if (total) warp_copy_realign(O.out, total, A.out + ea, A.out_cap > ea ? A.out_cap - ea : 0);
+        finish_result(C, t, ea + total);
         __syncwarp();
     }
 
@@ -596,69 +496,70 @@ struct DX {
             reinterpret_cast<uint64_t *>(tab)[i] = e;
         }
         __syncthreads();
-        uint32_t ph = 0, s = 0;
-        bool pending = false;
-        for (;;) {
-            unsigned long long tt = 0;
-            if (lane == 0) tt = atomicAdd(&P->g->tile_counter, 1ull);
-            const uint64_t g = __shfl_sync(kAllX, tt, 0);
-            if (g >= P->total_tiles) break;
-            OutSlot &O = M.os[s];
-            const uint32_t sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g);
-            load_shard(&O.sv, P->one, P->shards, P->n_shards, sh);
-            const uint64_t t = g - O.sv.tile0;
+        uint32_t ph = 0;
+        constexpr uint32_t kWords = sizeof(ShardView) / 8;
+        // Shard lookup (only when g leaves the shard of the last tile) and the bulk copy of launch-wide tile g.
+        auto stage_tile = [&](uint64_t g) {
+            if (g < M.nsv.tile0 || g >= M.nsv.tile0 + M.nsv.ntiles) {
+                const uint32_t sh = P->n_shards == 1 ? 0u : find_shard(P->shards, P->n_shards, g);
+                load_shard(&M.nsv, P->one, P->shards, P->n_shards, sh);
+            }
+            const uint64_t t = g - M.nsv.tile0;
+            const uint64_t base = t * (uint64_t)kTB;
+            Ctx Cn = C;
+            Cn.A = &M.nsv;
+            stage(Cn, t, (uint32_t)(min(M.nsv.n, base + kTB) - base));
+        };
+        if (lane == 0) {
+            M.nsv.tile0 = 0;
+            M.nsv.ntiles = 0;  // no shard loaded yet
+        }
+        __syncwarp();
+        unsigned long long tt = 0;
+        if (lane == 0) tt = atomicAdd(&P->g->tile_counter, 1ull);
+        uint64_t g = __shfl_sync(kAllX, tt, 0);
+        bool have = g < P->total_tiles;
+        if (have) stage_tile(g);
+        OutSlot &O = M.os[0];
+        while (have) {
+            if (lane < kWords) reinterpret_cast<uint64_t *>(&O.sv)[lane] = reinterpret_cast<const uint64_t *>(&M.nsv)[lane];
+            __syncwarp();
+            const ShardView &A = O.sv;
+            const uint64_t t = g - A.tile0;
             Ctx Cs = C;
             Cs.A = &O.sv;
             const uint64_t base = t * (uint64_t)kTB;
-            const uint32_t nown = (uint32_t)(min(O.sv.n, base + kTB) - base);
-            stage(Cs, t, nown);
+            const uint32_t nown = (uint32_t)(min(A.n, base + kTB) - base);
             if (!mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status)) {
                 mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status);
                 return;
             }
             ph ^= 1u;
             __syncwarp();
+            // size pass: the tile's size is published before it expands
             uint32_t total = 0, nls = 0;
             tile_sizes(Cs, base, nown, &total, &nls);
             if (lane == 0) {
-                if ((int64_t)t != P->stall_tile) dx_publish(&O.sv.tiles[t], t == 0, total);
-                if (nls) atomicAdd(&O.sv.res->n_lines, (unsigned long long)nls);
+                if ((int64_t)t != P->stall_tile) dx_publish(&A.tiles[t], t == 0, total);
+                if (nls) atomicAdd(&A.res->n_lines, (unsigned long long)nls);
             }
-            uint32_t etotal = 0, enls = 0;
-            const bool fits = expand(Cs, O, t, nown, &etotal, &enls);
-            if (lane == 0) {
-                O.t = t;
-                O.total = total;
-                O.nls = nls;
-                O.direct = fits ? 0u : 1u;
-            }
-            __syncwarp();
-            if (pending) {
-                Ctx Cp = C;
-                Cp.A = &M.os[s ^ 1u].sv;
-                finish_staged(Cp, M.os[s ^ 1u]);
-                pending = false;
-            }
-            if (Geo::kSlots == 1 && fits) {  // no pipeline: finish this tile now
-                finish_staged(Cs, O);
-                continue;
-            }
-            if (!fits) {  // look back first, then write straight to memory
-                const uint64_t ea = t > 0 ? dx_lookback<kLbR>(O.sv.tiles, t, P->limit_ns, C.status) : 0;
-                if (lane == 0 && t > 0 && (int64_t)t != P->stall_tile) dx_publish(&O.sv.tiles[t], true, ea + total);
-                expand_direct(Cs, t, nown, ea);
+            const bool fits = total + 32u <= (uint32_t)kOutB;
+            if (fits) {
+                expand(Cs, O, base, nown, total);
+            } else {  // a tile that outgrows the stage looks back first and writes straight to memory
+                const uint64_t ea = t > 0 ? dx_lookback<kLbR>(A.tiles, t, P->limit_ns, C.status) : 0;
+                if (lane == 0 && t > 0 && (int64_t)t != P->stall_tile) dx_publish(&A.tiles[t], true, ea + total);
+                expand_direct(Cs, base, nown, ea);
                 finish_result(Cs, t, ea + total);
                 __syncwarp();
-            } else {
-                pending = true;
-                s ^= 1u;
             }
-            if (Geo::kSlots == 1) s = 0;
-        }
-        if (pending) {
-            Ctx Cp = C;
-            Cp.A = &M.os[s ^ 1u].sv;
-            finish_staged(Cp, M.os[s ^ 1u]);
+            // the staged bytes of this tile are dead from here on: the next tile's copy lands during the look-back
+            // and copy-out of this one
+            if (lane == 0) tt = atomicAdd(&P->g->tile_counter, 1ull);
+            g = __shfl_sync(kAllX, tt, 0);
+            have = g < P->total_tiles;
+            if (have) stage_tile(g);
+            if (fits) finish_staged(Cs, O, t, total);
         }
     }
 };
@@ -669,18 +570,12 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) decompress_expand_kernel(
     DX<Geo>::run(&P);
 }
 
-// Compiled geometries, all with 2048-byte tiles (four rounds) and stages of 2.25 x the tile beside the 36 KB of
-// tables: one stage and 24 warps per SM (more warps to hide latency, the look-back not pipelined), patterns
-// ORed in or funnelled; two stages (pipelined look-back) with 16 warps, ORed in; one stage with 20 warps
-// (registers for the widest look-back), ORed in.
-using DxV0 = DxGeom<24, 2048, 4608, 1, true>;
-using DxV1 = DxGeom<24, 2048, 4608, 1, false>;
-using DxV2 = DxGeom<16, 2048, 4608, 2, true>;
-using DxV3 = DxGeom<20, 2048, 4608, 1, true>;
+// Compiled geometries, both with 2048-byte tiles (four rounds), one stage of 2.25 x the tile beside the 36 KB of
+// tables: 24 warps per SM (80 registers), or 20 warps (96 registers: the widest look-back).
+using DxV0 = DxGeom<24, 2048, 4608, 1>;
+using DxV1 = DxGeom<20, 2048, 4608, 1>;
 static_assert(DxV0::kWarps * sizeof(DX<DxV0>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
 static_assert(DxV1::kWarps * sizeof(DX<DxV1>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
-static_assert(DxV2::kWarps * sizeof(DX<DxV2>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
-static_assert(DxV3::kWarps * sizeof(DX<DxV3>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
 
 template <class Geo>
 size_t dx_smem()
@@ -731,10 +626,8 @@ constexpr DxEntry dx_entry(const char *name)
 }
 
 const DxEntry kDx[] = {
-    dx_entry<DxV0>("decompress expand w24 t2048 or"),
-    dx_entry<DxV1>("decompress expand w24 t2048 funnel"),
-    dx_entry<DxV2>("decompress expand w16 t2048 or 2-stage"),
-    dx_entry<DxV3>("decompress expand w20 t2048 or"),
+    dx_entry<DxV0>("decompress expand w24 t2048"),
+    dx_entry<DxV1>("decompress expand w20 t2048"),
 };
 constexpr int kNumDx = (int)(sizeof(kDx) / sizeof(kDx[0]));
 
