@@ -13,6 +13,11 @@
 //     and streams those bytes into the host arena with coalesced 16-byte stores, so one launch sequence
 //     and one event complete a batch (no host round trip to learn the size). The device reservation is
 //     released when the batch completes; the host bytes stay until the result is fetched or released.
+//   - The batch's output offsets land in its host region too, behind its bytes, and stay there until its
+//     last request is fetched or released: completing a batch costs O(1) host work per request (no per-id
+//     copy); zs_server_fetch rebases a request's offsets as it copies them out.
+//   - A request that arrives while no batch is in flight is launched by the submitting thread itself (no
+//     hand-off to the scheduler); under load, requests queue and the scheduler batches them.
 //   - Completion is observed by polling CUDA events (the scheduler yields between polls while work is
 //     in flight); latency is arrival to the completion of the batch's host copy.
 #include <algorithm>
@@ -98,11 +103,13 @@ struct Request {
     std::shared_ptr<Batch> batch;
     size_t first = 0;  // index of its first id in the batch
     uint64_t byte_off = 0, byte_len = 0;
-    std::vector<uint64_t> off;  // k + 1 offsets, from 0
+    const uint64_t *off = nullptr;  // its k + 1 offsets in the batch's host region (relative to byte_off's base)
 };
 
 struct Batch {
     size_t dev_off = 0, host_off = 0, bound = 0;
+    size_t host_bound = 0;  // host region: the bytes (bound, rounded to 8) then the K + 1 offsets
+    size_t slot = 0;        // the in-flight slot running it
     std::vector<Request *> reqs;
     size_t unfetched = 0;
 };
@@ -110,9 +117,9 @@ struct Batch {
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    // h_ids, h_off and h_res are pinned and mapped: the kernels read the ids and write the offsets and the
-    // result record through their device addresses (d_ids, h_off_dev, h_res_dev), with no copy calls
-    uint64_t *h_ids = nullptr, *d_ids = nullptr, *h_off = nullptr, *h_off_dev = nullptr, *d_off = nullptr;
+    // h_ids and h_res are pinned and mapped: the kernels read the ids and write the result record through
+    // their device addresses (d_ids, h_res_dev), with no copy calls; the offsets go to the batch's host region
+    uint64_t *h_ids = nullptr, *d_ids = nullptr, *d_off = nullptr;
     void *d_scratch = nullptr;
     zs::DevResult *h_res = nullptr, *h_res_dev = nullptr;
     int state = 0;  // 0 free, 1 batch in flight
@@ -122,7 +129,8 @@ struct Slot {
 
 // Copies the r->out_len decoded bytes of a batch from the device arena to the mapped host arena (both
 // regions 256-byte aligned) with 16-byte loads and stores, grid-stride, and the batch's K + 1 output offsets
-// and its result record to their mapped host copies, so the batch needs no copy calls of its own.
+// (to the host region behind the bytes) and its result record to their mapped host copies, so the batch needs
+// no copy calls of its own.
 __global__ void copy_out_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst, const zs::DevResult *r,
                                 uint64_t cap, const uint64_t *__restrict__ off, uint64_t *__restrict__ h_off,
                                 uint64_t n_off, zs::DevResult *h_res)
@@ -173,6 +181,10 @@ __global__ void line_max_kernel(const uint8_t *__restrict__ comp, uint64_t comp_
     if (mx) atomicMax(out, mx);
     if (bad) atomicAdd(out + 1, bad);
 }
+
+// Host region of a batch whose bytes take `bound`: the bytes, then the K + 1 offsets (8-byte aligned).
+size_t offsets_at(size_t bound) { return (bound + 7) & ~(size_t)7; }
+size_t host_bound(size_t bound, size_t K) { return offsets_at(bound) + (K + 1) * sizeof(uint64_t); }
 
 double ms_between(Clock::time_point a, Clock::time_point b)
 {
@@ -227,6 +239,7 @@ struct zs_server {
 
     void loop();
     bool admit(Slot &s);
+    void await(std::unique_lock<std::mutex> &lk, Request *r);
     void finish(Slot &s);
     void fail_batch(Slot &s, zs_status st, const std::string &msg);
 };
@@ -280,9 +293,10 @@ cudaError_t issue_batch(zs_server *S, Slot &s)
         e = zs::launch_lines(S->d, S->comp, S->comp_len, S->index, S->n_lines, s.d_ids, K,
                              S->d_arena + s.batch->dev_off, s.batch->bound, s.d_off, dr, tiles, s.st);
     if (e == cudaSuccess) {
+        uint8_t *h = S->h_arena_dev + s.batch->host_off;
         copy_out_kernel<<<copy_blocks(s.batch->bound), 256, 0, s.st>>>(
-            S->d_arena + s.batch->dev_off, S->h_arena_dev + s.batch->host_off, dr, s.batch->bound, s.d_off,
-            s.h_off_dev, K + 1, s.h_res_dev);
+            S->d_arena + s.batch->dev_off, h, dr, s.batch->bound, s.d_off,
+            reinterpret_cast<uint64_t *>(h + offsets_at(s.batch->bound)), K + 1, s.h_res_dev);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
@@ -295,21 +309,22 @@ cudaError_t issue_batch(zs_server *S, Slot &s)
 bool zs_server::admit(Slot &s)
 {
     if (queue.empty()) return false;
-    const size_t room = std::min(dev_alloc.largest(), host_alloc.largest());
+    const size_t droom = dev_alloc.largest(), hroom = host_alloc.largest();
     size_t K = 0, bound = 0;
     std::vector<Request *> take;
     for (Request *r : queue) {
-        const size_t nb = RangeAlloc::round(bound + r->bound);
-        if (K + r->ids.size() > opt.max_batch_ids || nb > room) break;
-        K += r->ids.size();
+        const size_t nb = RangeAlloc::round(bound + r->bound), nk = K + r->ids.size();
+        if (nk > opt.max_batch_ids || nb > droom || RangeAlloc::round(host_bound(nb, nk)) > hroom) break;
+        K = nk;
         bound = nb;
         take.push_back(r);
     }
     if (take.empty()) return false;  // the head waits for memory (no overtaking)
     auto b = std::make_shared<Batch>();
     b->bound = bound;
+    b->host_bound = host_bound(bound, K);
     if (!dev_alloc.alloc(bound, &b->dev_off)) return false;
-    if (!host_alloc.alloc(bound, &b->host_off)) {
+    if (!host_alloc.alloc(b->host_bound, &b->host_off)) {
         dev_alloc.release(b->dev_off, bound);
         return false;
     }
@@ -324,6 +339,7 @@ bool zs_server::admit(Slot &s)
         queue.pop_front();
     }
     b->unfetched = take.size();
+    b->slot = (size_t)(&s - slots.data());
     s.batch = b;
     s.K = K;
     s.state = 1;
@@ -374,13 +390,12 @@ void zs_server::finish(Slot &s)
         return;
     }
     const Clock::time_point now = Clock::now();
+    const uint64_t *offs = reinterpret_cast<const uint64_t *>(h_arena + b->host_off + offsets_at(b->bound));
     for (Request *q : b->reqs) {
         const size_t k = q->ids.size();
-        const uint64_t base = s.h_off[q->first];
-        q->off.resize(k + 1);
-        for (size_t j = 0; j <= k; ++j) q->off[j] = s.h_off[q->first + j] - base;
-        q->byte_off = base;
-        q->byte_len = q->off[k];
+        q->off = offs + q->first;
+        q->byte_off = q->off[0];
+        q->byte_len = q->off[k] - q->off[0];
         q->state = 2;
         q->done_at = now;
         lat_ms.push_back(ms_between(q->arrival, now));
@@ -390,6 +405,37 @@ void zs_server::finish(Slot &s)
     s.state = 0;
     s.batch.reset();
     done_cv.notify_all();
+}
+
+// Waits (lk held on mu) until request r is done. While its batch is on the GPU the waiting thread polls the
+// batch's event itself and completes the batch when it is done, so a result is seen without a hand-off
+// through the scheduler thread (which polls the same events; whichever sees the event first finishes the batch).
+void zs_server::await(std::unique_lock<std::mutex> &lk, Request *r)
+{
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != device) cudaSetDevice(device);
+    while (r->state < 2) {
+        if (r->state == 1) {
+            Slot &s = slots[r->batch->slot];
+            const cudaError_t q = cudaEventQuery(s.ev);
+            if (q == cudaSuccess) {
+                finish(s);
+                continue;
+            }
+            if (q != cudaErrorNotReady) {
+                cudaGetLastError();
+                fail_batch(s, ZS_ERR_CUDA, std::string("zs_server: ") + cudaGetErrorString(q));
+                continue;
+            }
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        } else {
+            done_cv.wait(lk, [&] { return r->state != 0; });
+        }
+    }
+    if (cur >= 0 && cur != device) cudaSetDevice(cur);
 }
 
 void zs_server::loop()
@@ -472,11 +518,8 @@ extern "C" zs_status zs_server_create(const zs_dict *d, const uint8_t *d_comp, s
         if (e == cudaSuccess)
             e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_ids), K * sizeof(uint64_t), cudaHostAllocMapped);
         if (e == cudaSuccess)
-            e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_off), (K + 1) * sizeof(uint64_t), cudaHostAllocMapped);
-        if (e == cudaSuccess)
             e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_res), sizeof(zs::DevResult), cudaHostAllocMapped);
         if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s.d_ids), s.h_ids, 0);
-        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s.h_off_dev), s.h_off, 0);
         if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s.h_res_dev), s.h_res, 0);
         if (e == cudaSuccess) e = cudaMalloc(&s.d_off, (K + 1) * sizeof(uint64_t));
         if (e == cudaSuccess)
@@ -522,7 +565,6 @@ extern "C" void zs_server_destroy(zs_server *S)
         if (s.ev) cudaEventDestroy(s.ev);
         if (s.st) cudaStreamDestroy(s.st);
         if (s.h_ids) cudaFreeHost(s.h_ids);
-        if (s.h_off) cudaFreeHost(s.h_off);
         if (s.h_res) cudaFreeHost(s.h_res);
         if (s.d_off) cudaFree(s.d_off);
         if (s.d_scratch) cudaFree(s.d_scratch);
@@ -556,7 +598,7 @@ extern "C" zs_status zs_server_submit(zs_server *S, const uint64_t *ids, size_t 
     }
     const size_t bound = k * S->max_line;
     r->bound = bound;
-    if (RangeAlloc::round(bound) > S->opt.arena_bytes) {
+    if (RangeAlloc::round(host_bound(bound, k)) > S->opt.arena_bytes) {
         zs::set_error("zs_server_submit: the request's output bound exceeds the arena");
         return ZS_ERR_CAPACITY;
     }
@@ -573,7 +615,6 @@ extern "C" zs_status zs_server_submit(zs_server *S, const uint64_t *ids, size_t 
     if (k == 0) {
         p->state = 2;
         p->done_at = now;
-        p->off.assign(1, 0);
         ++S->n_completed;
         S->lat_ms.push_back(0.0);
         S->done_cv.notify_all();
@@ -581,15 +622,16 @@ extern "C" zs_status zs_server_submit(zs_server *S, const uint64_t *ids, size_t 
     }
     S->queue.push_back(p);
     ++S->changes;
-    // a free slot takes the request at once, from this thread: no hand-off to the scheduler at low load
-    for (Slot &s : S->slots) {
-        if (s.state != 0 || S->fatal != ZS_OK) continue;
+    // an idle server (nothing in flight, nothing queued before this request) launches it at once from this
+    // thread: no hand-off to the scheduler at low load; under load the scheduler batches the queue
+    bool idle = S->fatal == ZS_OK && S->queue.size() == 1;
+    for (const Slot &s : S->slots) idle &= s.state == 0;
+    if (idle) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (cur != S->device) cudaSetDevice(S->device);
-        S->admit(s);
+        S->admit(S->slots[0]);
         if (cur >= 0 && cur != S->device) cudaSetDevice(cur);
-        break;
     }
     S->cv.notify_all();
     return ZS_OK;
@@ -611,7 +653,7 @@ extern "C" zs_status zs_server_wait(zs_server *S, uint64_t ticket, double timeou
     Request *r = it->second.get();
     auto ready = [&] { return r->state >= 2; };
     if (timeout_s < 0) {
-        S->done_cv.wait(lk, ready);
+        S->await(lk, r);
     } else if (!S->done_cv.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) {
         zs::set_error("zs_server_wait: timed out");
         return ZS_ERR_TIMEOUT;
@@ -635,7 +677,7 @@ void drop(zs_server *S, std::unordered_map<uint64_t, std::unique_ptr<Request>>::
 {
     Request *r = it->second.get();
     if (auto b = r->batch) {
-        if (--b->unfetched == 0) S->host_alloc.release(b->host_off, b->bound);
+        if (--b->unfetched == 0) S->host_alloc.release(b->host_off, b->host_bound);
         r->batch.reset();
     }
     S->reqs.erase(it);
@@ -650,7 +692,7 @@ zs_status wait_release(zs_server *S, uint64_t ticket, Clock::time_point *done_at
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return ZS_ERR_INVALID_ARG;
     Request *r = it->second.get();
-    S->done_cv.wait(lk, [&] { return r->state >= 2; });
+    S->await(lk, r);
     const zs_status st = r->state == 3 ? r->err : ZS_OK;
     *done_at = r->done_at;
     drop(S, it);
@@ -694,7 +736,11 @@ extern "C" zs_status zs_server_fetch(zs_server *S, uint64_t ticket, uint8_t *out
         return ZS_ERR_CAPACITY;
     }
     if (r->byte_len) std::memcpy(out, S->h_arena + r->batch->host_off + r->byte_off, r->byte_len);
-    if (off) std::memcpy(off, r->off.data(), r->off.size() * sizeof(uint64_t));
+    if (off) {
+        const size_t k = r->ids.size();
+        if (!r->off) off[0] = 0;  // an empty request
+        for (size_t j = 0; r->off && j <= k; ++j) off[j] = r->off[j] - r->byte_off;
+    }
     drop(S, it);
     return ZS_OK;
 }
