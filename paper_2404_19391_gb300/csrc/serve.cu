@@ -21,6 +21,7 @@
 //   - Completion is observed by polling CUDA events (the scheduler yields between polls while work is
 //     in flight); latency is arrival to the completion of the batch's host copy.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -95,7 +96,10 @@ struct Batch;
 
 struct Request {
     uint64_t ticket = 0;
-    std::vector<uint64_t> ids;
+    size_t k = 0;                     // ids
+    const uint64_t *hid = nullptr;    // its ids: in the pinned ids arena (ids_off) or in heap_ids
+    size_t ids_off = SIZE_MAX;        // byte offset in the ids arena, SIZE_MAX: heap_ids
+    std::vector<uint64_t> heap_ids;   // used when the ids arena is full
     size_t bound = 0;
     Clock::time_point arrival, done_at;
     int state = 0;  // 0 queued, 1 on the GPU, 2 done, 3 failed
@@ -108,6 +112,7 @@ struct Request {
 
 struct Batch {
     size_t dev_off = 0, host_off = 0, bound = 0;
+    const uint64_t *d_ids = nullptr;  // the ids the launch reads (device address of pinned memory)
     size_t host_bound = 0;  // host region: the bytes (bound, rounded to 8) then the K + 1 offsets
     size_t slot = 0;        // the in-flight slot running it
     std::vector<Request *> reqs;
@@ -215,6 +220,10 @@ struct zs_server {
 
     uint8_t *d_arena = nullptr;
     uint8_t *h_arena = nullptr;     // pinned, mapped
+    // pinned, mapped ids arena: submit copies a request's ids here (no heap allocation, no page faults), and a
+    // batch of one request is launched on them where they lie
+    uint64_t *h_idsa = nullptr, *d_idsa = nullptr;
+    RangeAlloc ids_alloc;
     uint8_t *h_arena_dev = nullptr;  // its device address
     RangeAlloc dev_alloc, host_alloc;
     std::vector<Slot> slots;
@@ -226,7 +235,9 @@ struct zs_server {
     std::deque<Request *> queue;
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     uint64_t next_ticket = 1;
-    uint64_t changes = 0;  // bumped by submit, fetch/release and stop: the idle scheduler waits on it
+    // bumped (under mu) by submit, fetch/release and stop: the idle scheduler waits on it, the polling one
+    // reads it without the lock to see that there is new work
+    std::atomic<uint64_t> changes{0};
     bool stop = false;
     zs_status fatal = ZS_OK;
     std::string fatal_msg;
@@ -239,6 +250,7 @@ struct zs_server {
 
     void loop();
     bool admit(Slot &s);
+    void release_ids(Batch &b);
     void await(std::unique_lock<std::mutex> &lk, Request *r);
     void finish(Slot &s);
     void fail_batch(Slot &s, zs_status st, const std::string &msg);
@@ -290,7 +302,7 @@ cudaError_t issue_batch(zs_server *S, Slot &s)
     zs::DevResult *dr = reinterpret_cast<zs::DevResult *>(s.d_scratch);
     zs::TileState *tiles = reinterpret_cast<zs::TileState *>(dr + 1);
     if (e == cudaSuccess)
-        e = zs::launch_lines(S->d, S->comp, S->comp_len, S->index, S->n_lines, s.d_ids, K,
+        e = zs::launch_lines(S->d, S->comp, S->comp_len, S->index, S->n_lines, s.batch->d_ids, K,
                              S->d_arena + s.batch->dev_off, s.batch->bound, s.d_off, dr, tiles, s.st);
     if (e == cudaSuccess) {
         uint8_t *h = S->h_arena_dev + s.batch->host_off;
@@ -313,7 +325,7 @@ bool zs_server::admit(Slot &s)
     size_t K = 0, bound = 0;
     std::vector<Request *> take;
     for (Request *r : queue) {
-        const size_t nb = RangeAlloc::round(bound + r->bound), nk = K + r->ids.size();
+        const size_t nb = RangeAlloc::round(bound + r->bound), nk = K + r->k;
         if (nk > opt.max_batch_ids || nb > droom || RangeAlloc::round(host_bound(nb, nk)) > hroom) break;
         K = nk;
         bound = nb;
@@ -329,15 +341,17 @@ bool zs_server::admit(Slot &s)
         return false;
     }
     size_t at = 0;
+    const bool in_place = take.size() == 1 && take[0]->ids_off != SIZE_MAX;  // launched on the arena copy
     for (Request *r : take) {
-        std::memcpy(s.h_ids + at, r->ids.data(), r->ids.size() * sizeof(uint64_t));
+        if (!in_place) std::memcpy(s.h_ids + at, r->hid, r->k * sizeof(uint64_t));
         r->first = at;
         r->state = 1;
         r->batch = b;
-        at += r->ids.size();
+        at += r->k;
         b->reqs.push_back(r);
         queue.pop_front();
     }
+    b->d_ids = in_place ? d_idsa + take[0]->ids_off / sizeof(uint64_t) : s.d_ids;
     b->unfetched = take.size();
     b->slot = (size_t)(&s - slots.data());
     s.batch = b;
@@ -354,9 +368,21 @@ bool zs_server::admit(Slot &s)
     return true;
 }
 
+// The batch's launch has read its requests' ids: their arena space is free again. Holds mu.
+void zs_server::release_ids(Batch &b)
+{
+    for (Request *r : b.reqs) {
+        if (r->ids_off != SIZE_MAX) ids_alloc.release(r->ids_off, r->k * sizeof(uint64_t));
+        r->ids_off = SIZE_MAX;
+        r->hid = nullptr;
+        r->heap_ids = std::vector<uint64_t>();
+    }
+}
+
 void zs_server::fail_batch(Slot &s, zs_status st, const std::string &msg)
 {
     auto b = s.batch;
+    release_ids(*b);
     const Clock::time_point now = Clock::now();
     for (Request *r : b->reqs) {
         r->state = 3;
@@ -371,6 +397,8 @@ void zs_server::fail_batch(Slot &s, zs_status st, const std::string &msg)
             r->state = 3;
             r->err = st;
             r->done_at = now;
+            if (r->ids_off != SIZE_MAX) ids_alloc.release(r->ids_off, r->k * sizeof(uint64_t));
+            r->ids_off = SIZE_MAX;
         }
         queue.clear();
     }
@@ -390,9 +418,10 @@ void zs_server::finish(Slot &s)
         return;
     }
     const Clock::time_point now = Clock::now();
+    release_ids(*b);
     const uint64_t *offs = reinterpret_cast<const uint64_t *>(h_arena + b->host_off + offsets_at(b->bound));
     for (Request *q : b->reqs) {
-        const size_t k = q->ids.size();
+        const size_t k = q->k;
         q->off = offs + q->first;
         q->byte_off = q->off[0];
         q->byte_len = q->off[k] - q->off[0];
@@ -418,19 +447,24 @@ void zs_server::await(std::unique_lock<std::mutex> &lk, Request *r)
     while (r->state < 2) {
         if (r->state == 1) {
             Slot &s = slots[r->batch->slot];
-            const cudaError_t q = cudaEventQuery(s.ev);
+            const cudaEvent_t ev = s.ev;
+            // poll without the lock for a while (the submitter and the scheduler need it), then look again
+            lk.unlock();
+            cudaError_t q = cudaErrorNotReady;
+            for (int i = 0; i < 64 && q == cudaErrorNotReady; ++i) {
+                q = cudaEventQuery(ev);
+                if (q == cudaErrorNotReady) std::this_thread::yield();
+            }
+            lk.lock();
+            if (r->state != 1 || s.batch != r->batch) continue;  // finished (or failed) meanwhile
+            if (q == cudaErrorNotReady) continue;
+            q = cudaEventQuery(ev);
             if (q == cudaSuccess) {
                 finish(s);
-                continue;
-            }
-            if (q != cudaErrorNotReady) {
+            } else if (q != cudaErrorNotReady) {
                 cudaGetLastError();
                 fail_batch(s, ZS_ERR_CUDA, std::string("zs_server: ") + cudaGetErrorString(q));
-                continue;
             }
-            lk.unlock();
-            std::this_thread::yield();
-            lk.lock();
         } else {
             done_cv.wait(lk, [&] { return r->state != 0; });
         }
@@ -442,6 +476,7 @@ void zs_server::loop()
 {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
+    std::vector<cudaEvent_t> polled;
     for (;;) {
         bool busy = false, progressed = false;
         for (Slot &s : slots) {
@@ -458,20 +493,33 @@ void zs_server::loop()
             progressed = true;
         }
         int inflight = 0;
+        bool free_slot = false;
         for (Slot &s : slots) {
             if (s.state == 0 && fatal == ZS_OK && admit(s)) progressed = true;
             inflight += s.state != 0;
+            free_slot |= s.state == 0;
         }
         max_inflight_seen = std::max(max_inflight_seen, inflight);
         if (stop && inflight == 0) break;
         if (progressed) continue;
-        if (busy || inflight) {  // poll the in-flight events; let submitters in between polls
+        if (busy || inflight) {
+            // poll the in-flight events without the lock (submitters and waiters take it meanwhile) until one
+            // completes, or new work arrives while a slot is free
+            polled.clear();
+            for (Slot &s : slots)
+                if (s.state != 0) polled.push_back(s.ev);
+            const uint64_t seen = changes.load();
             lk.unlock();
-            std::this_thread::yield();
+            for (bool go = true; go;) {
+                for (cudaEvent_t ev : polled)
+                    if (cudaEventQuery(ev) != cudaErrorNotReady) go = false;
+                if (free_slot && changes.load() != seen) go = false;
+                if (go) std::this_thread::yield();
+            }
             lk.lock();
         } else {
-            const uint64_t seen = changes;  // the queue head waits for arena room or a new request
-            cv.wait(lk, [&] { return stop || changes != seen; });
+            const uint64_t seen = changes.load();  // the queue head waits for arena room or a new request
+            cv.wait(lk, [&] { return stop || changes.load() != seen; });
         }
     }
 }
@@ -507,7 +555,11 @@ extern "C" zs_status zs_server_create(const zs_dict *d, const uint8_t *d_comp, s
     if (st != ZS_OK) return st;
     const size_t K = S->opt.max_batch_ids;
     S->scratch_tiles = zs::lines_tiles(K);
+    const size_t ids_bytes = 4 * K * sizeof(uint64_t);
     e = cudaMalloc(&S->d_arena, S->opt.arena_bytes);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void **>(&S->h_idsa), ids_bytes, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&S->d_idsa), S->h_idsa, 0);
     if (e == cudaSuccess)
         e = cudaHostAlloc(reinterpret_cast<void **>(&S->h_arena), S->opt.arena_bytes, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&S->h_arena_dev), S->h_arena, 0);
@@ -533,6 +585,7 @@ extern "C" zs_status zs_server_create(const zs_dict *d, const uint8_t *d_comp, s
     }
     S->dev_alloc.reset(S->opt.arena_bytes);
     S->host_alloc.reset(S->opt.arena_bytes);
+    S->ids_alloc.reset(ids_bytes);
     zs_server *raw = S.release();
     raw->worker = std::thread([raw] { raw->loop(); });
     *out = raw;
@@ -571,6 +624,7 @@ extern "C" void zs_server_destroy(zs_server *S)
     }
     if (S->d_arena) cudaFree(S->d_arena);
     if (S->h_arena) cudaFreeHost(S->h_arena);
+    if (S->h_idsa) cudaFreeHost(S->h_idsa);
     if (cur >= 0) cudaSetDevice(cur);
     delete S;
 }
@@ -588,7 +642,7 @@ extern "C" zs_status zs_server_submit(zs_server *S, const uint64_t *ids, size_t 
         return ZS_ERR_INVALID_ARG;
     }
     auto r = std::make_unique<Request>();
-    r->ids.assign(ids, ids + k);
+    r->k = k;
     r->arrival = now;
     uint64_t top = 0;
     for (size_t j = 0; j < k; ++j) top = std::max(top, ids[j]);
@@ -602,8 +656,26 @@ extern "C" zs_status zs_server_submit(zs_server *S, const uint64_t *ids, size_t 
         zs::set_error("zs_server_submit: the request's output bound exceeds the arena");
         return ZS_ERR_CAPACITY;
     }
+    // the ids are copied into the pinned ids arena (space reserved under the lock, copied outside it), or into
+    // the heap when the arena is full
+    if (k) {
+        {
+            std::lock_guard<std::mutex> g(S->mu);
+            size_t off = 0;
+            if (S->ids_alloc.alloc(k * sizeof(uint64_t), &off)) r->ids_off = off;
+        }
+        if (r->ids_off != SIZE_MAX) {
+            uint64_t *dst = S->h_idsa + r->ids_off / sizeof(uint64_t);
+            std::memcpy(dst, ids, k * sizeof(uint64_t));
+            r->hid = dst;
+        } else {
+            r->heap_ids.assign(ids, ids + k);
+            r->hid = r->heap_ids.data();
+        }
+    }
     std::lock_guard<std::mutex> g(S->mu);
     if (S->fatal != ZS_OK) {
+        if (r->ids_off != SIZE_MAX) S->ids_alloc.release(r->ids_off, k * sizeof(uint64_t));
         zs::set_error(S->fatal_msg);
         return S->fatal;
     }
@@ -660,7 +732,7 @@ extern "C" zs_status zs_server_wait(zs_server *S, uint64_t ticket, double timeou
     }
     if (res) {
         res->out_len = r->byte_len;
-        res->n_lines = r->ids.size();
+        res->n_lines = r->k;
         res->err_offset = 0;
     }
     if (r->state == 3) {
@@ -737,7 +809,7 @@ extern "C" zs_status zs_server_fetch(zs_server *S, uint64_t ticket, uint8_t *out
     }
     if (r->byte_len) std::memcpy(out, S->h_arena + r->batch->host_off + r->byte_off, r->byte_len);
     if (off) {
-        const size_t k = r->ids.size();
+        const size_t k = r->k;
         if (!r->off) off[0] = 0;  // an empty request
         for (size_t j = 0; r->off && j <= k; ++j) off[j] = r->off[j] - r->byte_off;
     }
