@@ -278,6 +278,33 @@ def test_escape_runs(zs, dicts):
     check_decompress(zs, dicts, exp_comp, expect=np.frombuffer(raw, dtype=np.uint8))
 
 
+def test_tiles_that_outgrow_the_decoder_stage(zs, dicts):
+    """Compressed stretches made of the dictionary's longer patterns (3 bytes and more) expand more than the
+    decoder stages per tile (2.25x): those tiles write straight to memory after their look-back, between ordinary
+    tiles whose output is staged, and the whole output must still equal the oracle's."""
+    d, od = dicts
+    longer = []
+    for s in range(33, 256):  # one-symbol lines through the oracle decoder give each symbol's pattern length
+        try:
+            n = oracle.decompress_stream(od, np.array([s, 10], dtype=np.uint8)).size - 1
+        except oracle.OracleError:
+            continue
+        if n >= 3:
+            longer.append(s)
+    assert len(longer) >= 8
+    rng = np.random.default_rng(11)
+    ordinary = oracle.compress_stream(od, synth.generate(synth.CFG0, 0, 2000), 1)[0]
+    parts = []
+    for k in range(5):
+        lines = rng.choice(longer, size=(int(rng.integers(60, 160)), 40)).astype(np.uint8)
+        stretch = np.concatenate([lines, np.full((lines.shape[0], 1), 10, dtype=np.uint8)], axis=1).ravel()
+        cut = int(rng.integers(1, ordinary.size))
+        cut = int(np.flatnonzero(ordinary[cut:] == 10)[0]) + cut + 1 if (ordinary[cut:] == 10).any() else ordinary.size
+        parts += [ordinary[:cut], stretch]
+    comp = np.concatenate(parts)
+    check_decompress(zs, dicts, comp)
+
+
 # ---- line index and random access ---------------------------------------------------------------------
 
 @pytest.mark.parametrize("data", [b"\n", b"a", b"a\n", b"a\nb", b"a\nb\n", b"\n\n\nx", b"xy\n\nz\n"])
