@@ -351,25 +351,33 @@ struct DX {
         *nls = __reduce_add_sync(kAllX, nl);
     }
 
-    // Each pattern of a fast chunk ORed into the (cleared) stage at its own offset: the offsets are a prefix of
-    // the lengths, so the 16 patterns are independent. A pattern's up to 7 bytes touch two words, or three when
-    // it starts late in a word and is 6 or 7 bytes long; the second word takes an OR of zero when the pattern
-    // ends in the first (no branch), the third a predicated one.
+    // The 16 patterns of a fast chunk ORed into the (cleared) stage from shared address q on. The lane builds
+    // each 32-bit word of its output in a register (a funnel of the patterns) and ORs a word into the stage once
+    // it is complete, and the last, partial one at the end: about one reduction per two patterns, each with the
+    // lanes that complete a word at that step, so the 32 lanes' random banks collide far less than with one
+    // reduction per word a pattern touches. A lane's first and last words may hold bytes of its neighbours
+    // (the OR keeps them).
     static __device__ __forceinline__ void or_patterns(const uint32_t (&lo)[16], const uint32_t (&hi)[16],
                                                        uint32_t q)
     {
+        uint32_t w = q & ~3u;         // the word being filled
+        uint32_t n8 = 8u * (q & 3u);  // its bits below this lane's next byte
+        uint32_t acc = 0;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const uint32_t len = (hi[k] >> 24) & 7u;
+            const uint32_t len8 = (hi[k] >> 21) & 56u;  // 8 x the pattern's length
             const uint32_t h = hi[k] & 0x00FFFFFFu;
-            const uint32_t o = q & 3u;
-            const uint32_t sh = 8u * o;
-            const uint32_t w = q & ~3u;
-            red_or_shared(w, lo[k] << sh, true);
-            red_or_shared(w + 4u, __funnelshift_l(lo[k], h, sh), true);
-            red_or_shared(w + 8u, __funnelshift_l(h, 0u, sh), o + len > 8u);
-            q += len;
+            const uint32_t w0 = acc | (lo[k] << n8);
+            const uint32_t w1 = __funnelshift_l(lo[k], h, n8);
+            const uint32_t w2 = __funnelshift_l(h, 0u, n8);
+            const uint32_t t8 = n8 + len8;  // below 88: the word and at most two more
+            red_or_shared(w, w0, t8 >= 32u);
+            red_or_shared(w + 4u, w1, t8 >= 64u);
+            acc = t8 >= 64u ? w2 : (t8 >= 32u ? w1 : w0);
+            w += (t8 >> 5) << 2;
+            n8 = t8 & 31u;
         }
+        red_or_shared(w, acc, n8 != 0u);
     }
 
     // Expansion of a sized tile into slot O's stage (which must hold total + 32 bytes): per round, each lane
