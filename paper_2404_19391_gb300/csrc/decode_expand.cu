@@ -136,8 +136,8 @@ struct DX {
     static constexpr int kTB = Geo::kTile;
     static constexpr int kOutB = Geo::kOut;
     static constexpr int kRounds = kTB / 512;
-    // look-back records per lane per round trip: 8 (256 tiles a trip) where registers allow, else 4
-    static constexpr int kLbR = kW >= 24 ? 4 : 8;
+    // look-back records per lane per round trip (64 tiles a trip: measured best against 1, 4 and 8)
+    static constexpr int kLbR = 2;
     static_assert(kTB % 512 == 0 && kOutB % 16 == 0, "expansion geometry");
 
     struct alignas(16) OutSlot {
