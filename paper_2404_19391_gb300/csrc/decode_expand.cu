@@ -453,7 +453,7 @@ struct DX {
         const ShardView &A = *C.A;
         const uint64_t ea = t > 0 ? dx_lookback<kLbR>(A.tiles, t, C.P->limit_ns, C.status) : 0;
         if (C.lane == 0 && t > 0 && (int64_t)t != C.P->stall_tile) dx_publish(&A.tiles[t], true, ea + total);
-        if (total) warp_copy_realign(O.out, total, A.out + ea, A.out_cap > ea ? A.out_cap - ea : 0);
+        if (total) warp_copy_realign<true>(O.out, total, A.out + ea, A.out_cap > ea ? A.out_cap - ea : 0);
         finish_result(C, t, ea + total);
         __syncwarp();
     }

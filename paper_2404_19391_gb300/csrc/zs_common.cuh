@@ -524,6 +524,15 @@ __device__ __forceinline__ uint4 shift_chunk(const uint4 A, const uint4 B, uint3
                       __funnelshift_r(v[Q + 2], v[Q + 3], sh), __funnelshift_r(v[Q + 3], v[Q + 4], sh));
 }
 
+template <int Q>
+__device__ __forceinline__ void realign_loop(const uint4 *s16, uint4 *g, uint32_t j, uint32_t j1, uint32_t sh)
+{
+    for (; j < j1; j += 32) g[j] = shift_chunk<Q>(s16[j - 1], s16[j], sh);
+}
+
+// HOIST: the word offset's four cases are separate loops (the decoder), else one loop that switches per chunk
+// (the span kernel, whose register allocation is tuned around it).
+template <bool HOIST = false>
 __device__ __forceinline__ void warp_copy_realign(const uint8_t *stg, uint64_t len64, uint8_t *dst, uint64_t cap)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -537,16 +546,25 @@ __device__ __forceinline__ void warp_copy_realign(const uint8_t *stg, uint64_t l
     } else {
         // destination chunk j = stage bytes [16 j - so, 16 j - so + 16): chunk j - 1 from byte r = 16 - so on
         const uint32_t r = 16u - so, q = r >> 2, sh = 8u * (r & 3u);
-        for (uint32_t j = j0 + lane; j < j1; j += 32) {
-            const uint4 A = s16[j - 1], B = s16[j];
-            uint4 o;
+        if constexpr (HOIST) {  // the word offset q is the same for every chunk: choose the loop once
             switch (q) {
-                case 0: o = shift_chunk<0>(A, B, sh); break;
-                case 1: o = shift_chunk<1>(A, B, sh); break;
-                case 2: o = shift_chunk<2>(A, B, sh); break;
-                default: o = shift_chunk<3>(A, B, sh); break;
+                case 0: realign_loop<0>(s16, g, j0 + lane, j1, sh); break;
+                case 1: realign_loop<1>(s16, g, j0 + lane, j1, sh); break;
+                case 2: realign_loop<2>(s16, g, j0 + lane, j1, sh); break;
+                default: realign_loop<3>(s16, g, j0 + lane, j1, sh); break;
             }
-            g[j] = o;
+        } else {
+            for (uint32_t j = j0 + lane; j < j1; j += 32) {
+                const uint4 A = s16[j - 1], B = s16[j];
+                uint4 o;
+                switch (q) {
+                    case 0: o = shift_chunk<0>(A, B, sh); break;
+                    case 1: o = shift_chunk<1>(A, B, sh); break;
+                    case 2: o = shift_chunk<2>(A, B, sh); break;
+                    default: o = shift_chunk<3>(A, B, sh); break;
+                }
+                g[j] = o;
+            }
         }
     }
     const uint32_t h1 = min(len, j0 * 16u - so);  // head bytes [0, h1)
