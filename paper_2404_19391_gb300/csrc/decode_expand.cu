@@ -10,8 +10,9 @@
 //     bytes that are no symbol carry a flag instead, and such chunks (rare in SMILES text) take a byte loop.
 //     The table is replicated 16 times so that the 16 lanes of each half-warp read 16 different bank pairs.
 //   - A size pass over the entries' top words gives each lane's output bytes per round, a warp scan per
-//     round places the lanes, and the tile publishes its size before it expands; the expansion then ORs
-//     each pattern into a cleared stage at its own offset (no chain from one pattern to the next).
+//     round places the lanes, and the tile publishes its size before it expands; the expansion then funnels
+//     each lane's patterns into 32-bit words in a register and ORs each finished word into a cleared stage
+//     (the first and last words of a lane may hold bytes of its neighbours, which the OR keeps).
 //   - Escapes need no sequential scan: a byte is verbatim exactly when the run of ' ' before it has odd
 //     length (every unescaped ' ' escapes the next byte, and a run starts unescaped).
 //   - The stage leaves with aligned 16-byte stores once the look-back has given the tile's offset; a tile
@@ -244,16 +245,14 @@ struct DX {
         *nls = nl;
     }
 
-    // The same walk writing the bytes: into the stage at pos (STAGED) or to out[ea + pos] below cap.
-    template <bool STAGED>
+    // The same walk writing the bytes to out[ea + pos] (those below the capacity): a tile that outgrew its stage.
     static __device__ __forceinline__ void slow_write(const Ctx &C, uint32_t p0, uint32_t p1, bool lit, uint32_t pos,
-                                                      uint8_t *stg, uint64_t ea)
+                                                      uint64_t ea)
     {
         const ShardView &A = *C.A;
         const uint8_t *in = C.M->in + 16;
         auto put = [&](uint32_t w, uint8_t v) {
-            if (STAGED) stg[w] = v;
-            else if (ea + w < A.out_cap) A.out[ea + w] = v;
+            if (ea + w < A.out_cap) A.out[ea + w] = v;
         };
         for (uint32_t p = p0; p < p1; ++p) {
             const uint8_t b = in[p];
@@ -431,7 +430,7 @@ struct DX {
             if (p1 <= p0) continue;
             const uint32_t pw = M.pw[r][C.lane];
             const bool lit = (pw & kSlowChunk) ? literal_at(C, base, p0) : false;
-            slow_write<false>(C, p0, p1, lit, M.run[r] + (pw & ~kSlowChunk), nullptr, ea);
+            slow_write(C, p0, p1, lit, M.run[r] + (pw & ~kSlowChunk), ea);
         }
         __syncwarp();
     }
