@@ -24,13 +24,15 @@
 namespace zs {
 namespace {
 
-template <int W, int TB, int OUTB, int SLOTS>
+template <int W, int TB, int OUTB, int SLOTS, bool GIN = false>
 struct DxGeom {
     static constexpr int kWarps = W;    // warps per CTA (one CTA per SM)
     static constexpr int kTile = TB;    // compressed bytes per warp tile
     static constexpr int kOut = OUTB;   // staged output bytes per tile
     static constexpr int kSlots = SLOTS;  // 2: a tile's look-back and copy-out wait until the next tile is
                                           // expanded (software pipeline); 1: they follow at once
+    static constexpr bool kGlobalIn = GIN;  // the tile's compressed bytes are read from global memory (through
+                                            // L1) instead of a staged copy: shared memory for more warps
 };
 
 constexpr unsigned kAllX = 0xffffffffu;
@@ -147,7 +149,7 @@ struct DX {
     };
 
     struct alignas(16) WarpMem {
-        uint8_t in[16 + kTB + 16];  // the 16 bytes before the tile, the tile
+        uint8_t in[Geo::kGlobalIn ? 16 : 16 + kTB + 16];  // the 16 bytes before the tile, the tile (staged)
         OutSlot os[Geo::kSlots];
         ShardView nsv;              // shard of the staged tile (copied to its output slot when it expands)
         uint32_t pw[kRounds][32];   // from the size pass: lane's output offset in the round | kSlowChunk
@@ -160,6 +162,7 @@ struct DX {
         const DxArgs *P;
         const ShardView *A;
         WarpMem *M;
+        const uint8_t *tin;  // the tile's first compressed byte: in the stage, or in global memory
         const uint8_t *tab;  // pat8[256][kCopies]
         const uint8_t *plen;
         const uint8_t *pat;
@@ -190,9 +193,17 @@ struct DX {
     // first, then global memory for a run that reaches past the stage).
     static __device__ __forceinline__ bool literal_at(const Ctx &C, uint64_t base, uint32_t c0)
     {
+        uint32_t run = 0;
+        if constexpr (Geo::kGlobalIn) {
+            int64_t g = (int64_t)(base + c0) - 1;
+            while (g >= 0 && C.A->in[g] == kEsc) {
+                ++run;
+                --g;
+            }
+            return (run & 1u) != 0;
+        }
         const WarpMem &M = *C.M;
         int32_t q = 15 + (int32_t)c0;  // staged position of the byte before
-        uint32_t run = 0;
         while (q >= 0 && M.in[q] == kEsc && base + (uint64_t)q >= 16) {
             ++run;
             --q;
@@ -207,13 +218,37 @@ struct DX {
         return (run & 1u) != 0;
     }
 
+    // The byte before tile offset c0 (0 before the stream's first byte).
+    static __device__ __forceinline__ uint32_t byte_before(const Ctx &C, uint64_t base, uint32_t c0)
+    {
+        if (Geo::kGlobalIn && base + c0 == 0) return 0u;
+        return C.tin[(int32_t)c0 - 1];
+    }
+
+    // The 16 compressed bytes at tile offset c0 (16-byte aligned in the stage; from global memory only when
+    // the shard's input is 16-byte aligned, else byte by byte).
+    static __device__ __forceinline__ uint4 load16(const Ctx &C, uint32_t c0)
+    {
+        if constexpr (!Geo::kGlobalIn) {
+            return *reinterpret_cast<const uint4 *>(C.tin + c0);
+        } else {
+            if (C.A->in_aligned) return *reinterpret_cast<const uint4 *>(C.tin + c0);
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                w[k] = (uint32_t)C.tin[c0 + 4 * k] | ((uint32_t)C.tin[c0 + 4 * k + 1] << 8) |
+                       ((uint32_t)C.tin[c0 + 4 * k + 2] << 16) | ((uint32_t)C.tin[c0 + 4 * k + 3] << 24);
+            return make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+
     // Byte loop over the staged bytes [p0, p1) (tile offsets): output bytes and newlines, noting malformed
     // bytes. *lit: in, the first byte is verbatim; out, the last byte was an unpaired ' '.
     static __device__ __forceinline__ void slow_size(const Ctx &C, uint64_t base, uint32_t p0, uint32_t p1, bool *lit,
                                                      uint32_t *outb, uint32_t *nls)
     {
         const ShardView &A = *C.A;
-        const uint8_t *in = C.M->in + 16;
+        const uint8_t *in = C.tin;
         uint32_t ob = 0, nl = 0;
         bool l = *lit;
         for (uint32_t p = p0; p < p1; ++p) {
@@ -250,7 +285,7 @@ struct DX {
                                                       uint64_t ea)
     {
         const ShardView &A = *C.A;
-        const uint8_t *in = C.M->in + 16;
+        const uint8_t *in = C.tin;
         auto put = [&](uint32_t w, uint8_t v) {
             if (ea + w < A.out_cap) A.out[ea + w] = v;
         };
@@ -275,7 +310,7 @@ struct DX {
     static __device__ __forceinline__ void slow_or(const Ctx &C, uint32_t p0, uint32_t p1, bool lit, uint32_t pos,
                                                    uint8_t *stg)
     {
-        const uint8_t *in = C.M->in + 16;
+        const uint8_t *in = C.tin;
         uint32_t *w32 = reinterpret_cast<uint32_t *>(stg);
         auto put = [&](uint32_t w, uint8_t v) { atomicOr(w32 + (w >> 2), (uint32_t)v << (8 * (w & 3u))); };
         for (uint32_t p = p0; p < p1; ++p) {
@@ -304,16 +339,15 @@ struct DX {
                                                       uint32_t *nls)
     {
         WarpMem &M = *C.M;
-        const uint8_t *in = M.in + 16;
         uint32_t run = 0, nl = 0;
         for (int r = 0; r < kRounds; ++r) {
             if ((uint32_t)r * 512u >= nown) break;
             const uint32_t c0 = (uint32_t)r * 512u + C.lane * 16u;
             const uint32_t p0 = min(c0, nown), p1 = min(c0 + 16u, nown);
             uint32_t ob = 0;
-            bool fast = p1 - p0 == 16 && in[(int32_t)c0 - 1] != kEsc;
+            bool fast = p1 - p0 == 16 && byte_before(C, base, c0) != kEsc;
             if (fast) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(in + c0);
+                const uint4 v = load16(C, c0);
                 const uint32_t w[4] = {v.x, v.y, v.z, v.w};
                 uint32_t acc = 0, fl = 0;
 #pragma unroll
@@ -385,7 +419,6 @@ struct DX {
                                                   uint32_t total)
     {
         const WarpMem &M = *C.M;
-        const uint8_t *in = M.in + 16;
         uint8_t *stg = O.out;
         uint4 *s16 = reinterpret_cast<uint4 *>(stg);
         const uint32_t nclear = (total + 12u + 15u) / 16u;  // patterns OR zeros up to 12 bytes past the end
@@ -400,7 +433,7 @@ struct DX {
             const uint32_t pw = M.pw[r][C.lane];
             const uint32_t pos = M.run[r] + (pw & ~kSlowChunk);
             if (!(pw & kSlowChunk)) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(in + c0);
+                const uint4 v = load16(C, c0);
                 const uint32_t w[4] = {v.x, v.y, v.z, v.w};
                 uint32_t lo[16], hi[16];
 #pragma unroll
@@ -469,6 +502,7 @@ struct DX {
         C.P = P;
         C.A = nullptr;
         C.M = &M;
+        C.tin = nullptr;
         C.tab = tab;
         C.plen = dec;
         C.pat = dec + 256;
@@ -513,9 +547,11 @@ struct DX {
             }
             const uint64_t t = g - M.nsv.tile0;
             const uint64_t base = t * (uint64_t)kTB;
-            Ctx Cn = C;
-            Cn.A = &M.nsv;
-            stage(Cn, t, (uint32_t)(min(M.nsv.n, base + kTB) - base));
+            if constexpr (!Geo::kGlobalIn) {  // else the bytes are read where they lie
+                Ctx Cn = C;
+                Cn.A = &M.nsv;
+                stage(Cn, t, (uint32_t)(min(M.nsv.n, base + kTB) - base));
+            }
         };
         if (lane == 0) {
             M.nsv.tile0 = 0;
@@ -537,11 +573,16 @@ struct DX {
             Cs.A = &O.sv;
             const uint64_t base = t * (uint64_t)kTB;
             const uint32_t nown = (uint32_t)(min(A.n, base + kTB) - base);
-            if (!mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status)) {
-                mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status);
-                return;
+            if constexpr (Geo::kGlobalIn) {
+                Cs.tin = A.in + base;
+            } else {
+                Cs.tin = M.in + 16;
+                if (!mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status)) {
+                    mbar_wait_bounded(&M.bar, ph, P->limit_ns, C.status);
+                    return;
+                }
+                ph ^= 1u;
             }
-            ph ^= 1u;
             __syncwarp();
             // size pass: the tile's size is published before it expands
             uint32_t total = 0, nls = 0;
@@ -581,8 +622,12 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) decompress_expand_kernel(
 // tables: 24 warps per SM (80 registers), or 20 warps (96 registers: the widest look-back).
 using DxV0 = DxGeom<24, 2048, 4608, 1>;
 using DxV1 = DxGeom<20, 2048, 4608, 1>;
+using DxV2 = DxGeom<28, 2048, 4608, 1, true>;
+using DxV3 = DxGeom<32, 2048, 4608, 1, true>;
 static_assert(DxV0::kWarps * sizeof(DX<DxV0>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
 static_assert(DxV1::kWarps * sizeof(DX<DxV1>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
+static_assert(DxV2::kWarps * sizeof(DX<DxV2>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
+static_assert(DxV3::kWarps * sizeof(DX<DxV3>::WarpMem) + 256 * kCopies * 8 + kDecBytes <= 227 * 1024, "smem");
 
 template <class Geo>
 size_t dx_smem()
@@ -635,6 +680,8 @@ constexpr DxEntry dx_entry(const char *name)
 const DxEntry kDx[] = {
     dx_entry<DxV0>("decompress expand w24 t2048"),
     dx_entry<DxV1>("decompress expand w20 t2048"),
+    dx_entry<DxV2>("decompress expand w28 t2048 global"),
+    dx_entry<DxV3>("decompress expand w32 t2048 global"),
 };
 constexpr int kNumDx = (int)(sizeof(kDx) / sizeof(kDx[0]));
 
