@@ -618,8 +618,9 @@ __global__ void __launch_bounds__(Geo::kWarps * 32, 1) decompress_expand_kernel(
     DX<Geo>::run(&P);
 }
 
-// Compiled geometries, both with 2048-byte tiles (four rounds), one stage of 2.25 x the tile beside the 36 KB of
-// tables: 24 warps per SM (80 registers), or 20 warps (96 registers: the widest look-back).
+// Compiled geometries, all with 2048-byte tiles (four rounds) and one stage of 2.25 x the tile beside the 36 KB
+// of tables: the input staged by a bulk copy with 24 warps per SM (72 registers) or 20 warps (96), or read from
+// global memory with 28 or 32 warps (the shared memory of the staged input left to more warps).
 using DxV0 = DxGeom<24, 2048, 4608, 1>;
 using DxV1 = DxGeom<20, 2048, 4608, 1>;
 using DxV2 = DxGeom<28, 2048, 4608, 1, true>;
