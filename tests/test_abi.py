@@ -44,3 +44,18 @@ def test_product_path_does_not_reference_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 text = open(os.path.join(dirpath, f), errors="replace").read()
                 assert "import oracle" not in text and "from oracle" not in text and "zs_oracle" not in text, f
+
+
+def test_no_cpu_fallback():
+    """Without a CUDA device the binding refuses to work: a dictionary cannot be loaded and host tensors are
+    rejected, so no call can quietly run anywhere but the GPU kernels."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2404_19391_gb300 import zsmiles as zs
+    zs.load_library()
+    with pytest.raises(Exception):
+        zs.Dictionary()
+    with pytest.raises(ValueError):
+        zs._ptr(torch.zeros(16, dtype=torch.uint8))
